@@ -1,0 +1,412 @@
+"""Benchmark of the segregation gradient flow on one GB300 (or N replicas).
+
+Workload (default): unit-sphere icosphere level 8 (N = 655 362 vertices,
+1 310 720 triangles), m = 16 components, eps = 1e-3, tau = 5e-6, seeded
+uniform[0,1) initial data; mixed precision (float32 vectors and matrices,
+inner products / norms / CG scalars / energies accumulated to float64).
+One bench step = one step of Algorithm 2.2 (heat step by Jacobi-PCG, nodal
+ODE, renormalisation) plus the energy evaluation of the stop rule, i.e. every
+hot-path pass runs in every step.  Metric: DoF-steps/s = N * m * steps / s.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) each rank runs an independent replica on its own GPU
+(weak scaling); ranks meet only at a host barrier and a max-reduction of the
+timings (gloo), never in the data path.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+HBM_FALLBACK_GBS = 6800.0
+METRIC = "DoF-steps/s (N*m*steps) sphere 655k m=16 FP32-mix vs FP64; p50/p99 latency"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--level", type=int, default=8)
+    ap.add_argument("--m", type=int, default=16)
+    ap.add_argument("--eps", type=float, default=1e-3)
+    ap.add_argument("--tau", type=float, default=5e-6)
+    ap.add_argument("--seed", type=int, default=1236)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-sample-seconds", type=float, default=20.0)
+    ap.add_argument("--reference-budget-seconds", type=float, default=150.0)
+    return ap.parse_args()
+
+
+def workload_name(a):
+    n = 10 * 4 ** a.level + 2
+    return f"unit sphere icosphere level {a.level} (N={n}), m={a.m}, eps={a.eps:g}, tau={a.tau:g}, seeded uniform init"
+
+
+# --------------------------------------------------------------- distributed
+
+
+def dist_setup(a):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("gloo", rank=rank, world_size=ws)
+    return rank, ws, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------- clocks
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# -------------------------------------------------------------- CPU oracle
+
+
+def oracle_sample(level, m, eps, tau, seed, budget_s, max_cols=None):
+    """Time the FP64 oracle on a bounded sample of the workload.
+
+    A sample step is the oracle's Algorithm 2.2 step restricted to the first
+    c components (c columns of the heat step, the nodal ODE and the
+    normalisation over those c columns); its cost is proportional to c, and
+    its DoF count is N * c.  c is chosen so that the sample takes about
+    budget_s seconds.  Returns (DoF-steps/s, c, seconds, threads).
+    """
+    import numpy as np
+
+    import workload as w
+    from oracle import seg_oracle as o
+
+    xyz, tri = w.icosphere(level)
+    M, K = o.assemble(xyz, tri)
+    U = o.initial_state(M, w.uniform01(seed, xyz.shape[0], m))
+    t0 = time.perf_counter()
+    o.heat_step(M, K, tau, U[:, :1])
+    t_col = time.perf_counter() - t0
+    c = int(max(1, min(max_cols or m, budget_s // max(t_col, 1e-9))))
+    t0 = time.perf_counter()
+    o.step(M, K, tau, eps, U[:, :c])
+    dt = time.perf_counter() - t0
+    return xyz.shape[0] * c / dt, c, dt, 1
+
+
+def cpu_baseline(a):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = (f"import json,sys; sys.path.insert(0,{ROOT!r}); import bench; "
+            f"r=bench.oracle_sample({a.level},{a.m},{a.eps},{a.tau},{a.seed},{a.cpu_sample_seconds}); "
+            f"print(json.dumps(r))")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        return {"value": None, "unit": "DoF-steps/s", "cores": 1, "kind": "oracle", "error": r.stderr[-300:]}
+    rate, c, dt, threads = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": rate, "unit": "DoF-steps/s", "cores": threads, "kind": "oracle",
+            "sample": f"one oracle step (FP64 numpy/scipy, single thread) of the first {c} of {a.m} components "
+                      f"on the level-{a.level} sphere, {dt:.1f} s"}
+
+
+# ---------------------------------------------------------------- our arm
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def cg_pass_a_bytes(n, nnz, m_pad, s):
+    """Algorithmic bytes of one CG pass A launch (k_cg_a).
+
+    Per vertex row: read r and p_old (also gathered by the neighbours, each
+    unique row once), read and write x, write p_new and q: 6 vectors of
+    N * m_pad * s bytes; plus the CSR of A (row pointers, int32 columns,
+    values) and the Jacobi diagonal.
+    """
+    V = n * m_pad * s
+    return 6 * V + 4 * (n + 1) + nnz * (4 + s) + n * s
+
+
+def run_ours(a, rank, ws, local):
+    import numpy as np
+    import torch
+
+    import paper_1408_2355_gb300 as seg
+    import workload as w
+
+    torch.cuda.set_device(local)
+    dev_index = torch.cuda.current_device()
+    xyz, tri = w.icosphere(a.level)
+    n = xyz.shape[0]
+    mesh = seg.seg_create_mesh(xyz, tri)
+    stream = torch.cuda.Stream()
+
+    def make(prec):
+        prob = seg.seg_assemble(mesh, a.tau, prec)
+        prm = seg.seg_params()
+        prm.check_every = 1      # energy + stop-rule pass in every step
+        prm.energy_tol = -1.0    # ... but never stop: time exactly K steps
+        st = seg.seg_state_create(prob, a.m, a.eps, seg.SEG_INIT_UNIFORM, a.seed, prm, stream.cuda_stream)
+        return prob, st
+
+    def timed(st, K, W):
+        seg.seg_step(st, W)
+        s0 = seg.seg_get_stats(st)
+        barrier(ws)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        seg.seg_step_async(st, K)
+        e1.record(stream)
+        seg.seg_sync(st)
+        torch.cuda.synchronize()
+        barrier(ws)
+        ms = e0.elapsed_time(e1)
+        s1 = seg.seg_get_stats(st)
+        return ms, s0, s1
+
+    prob, st = make(seg.SEG_MIXED_FP32)
+    info = seg.seg_problem_info(prob)
+    li = seg.seg_launch_info(st)
+    clocks = ClockSampler(dev_index)
+    clocks.start()
+    ms, s0, s1 = timed(st, a.steps, a.warmup)
+    clk = clocks.stop()
+    ms = max_over_ranks(ms, ws)
+    dcg = s1["cg_iterations"] - s0["cg_iterations"]
+    launches = 3 * a.steps + 2 * dcg
+    value = ws * n * a.m * a.steps / (ms / 1e3)
+    e_final = seg.seg_energy(st)
+
+    # live duration of the dominant kernel (CG pass A) with CUDA events
+    t_a = seg.seg_time_kernel(st, 1, 20)
+    t_b = seg.seg_time_kernel(st, 2, 20)
+    bytes_a = cg_pass_a_bytes(n, info["nnz"], li["padded_m"], 4)
+    peak, peak_kind = measured_peak()
+    achieved = bytes_a / (t_a / 1e3) / 1e9
+
+    out = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "DoF-steps/s",
+        "n_gpus": ws,
+        "steps": a.steps,
+        "warmup": a.warmup,
+        "ms_per_step": ms / a.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "impl": "ours",
+        "config": {
+            "workload": workload_name(a),
+            "n_vert": n,
+            "n_tri": int(tri.shape[0]),
+            "nnz": info["nnz"],
+            "m": a.m,
+            "precision": "mixed: f32 vectors/matrices/exp, inner products and CG scalars to f64 accuracy",
+            "cg_rtol": 1e-7,
+            "energy_every_step": True,
+            "l2": "inputs larger than L2: 5 state vectors x 42 MB + 76 MB of CSR > 129 MB L2",
+            "grid_blocks": li["grid_blocks"],
+            "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+        },
+        "cg_iterations_per_step": dcg / a.steps,
+        "final_total_energy": e_final["total"],
+        "gpu_launches": launches,
+        "clocks": clk,
+        "roofline": {
+            "bound": "hbm",
+            "kernel": "k_cg_a (CG pass A: p = D^-1 r + beta p, q = A p, p.q, lagged x update)",
+            "achieved": achieved,
+            "peak": peak,
+            "peak_kind": peak_kind,
+            "unit": "GB/s",
+            "frac": achieved / peak,
+            "traffic": None,
+            "bytes_per_launch": bytes_a,
+            "launch_ms": t_a,
+            "cg_pass_b_ms": t_b,
+        },
+    }
+
+    if not a.no_e2e:
+        # end to end through the public API: host (pinned) initial data in,
+        # every step the control block (energy of the step) read back, final
+        # state out to host memory
+        U0 = torch.from_numpy(w.uniform01(a.seed, n, a.m)).pin_memory()
+        Uout = torch.empty((n, a.m), dtype=torch.float64).pin_memory()
+        seg.seg_set_u(st, U0)
+        seg.seg_step(st, a.warmup)
+        barrier(ws)
+        t0 = time.perf_counter()
+        seg.seg_set_u(st, U0)
+        energies = []
+        for _ in range(a.steps):
+            seg.seg_step(st, 1)
+            energies.append(seg.seg_get_stats(st)["last_check_total"])
+        seg.seg_get_u(st, Uout)
+        t1 = time.perf_counter()
+        dt = max_over_ranks(t1 - t0, ws)
+        out["e2e"] = {"value": ws * n * a.m * a.steps / dt, "unit": "DoF-steps/s",
+                      "h2d_bytes_per_step": n * a.m * 8 / a.steps,
+                      "d2h_bytes_per_step": n * a.m * 8 / a.steps + 512,
+                      "note": "set_u from pinned host, K x (seg_step + control-block read), get_u to pinned host"}
+
+    if not a.no_fp64:
+        del st
+        prob64, st64 = make(seg.SEG_FP64)
+        k64 = max(3, a.steps // 3)
+        ms64, s0, s1 = timed(st64, k64, min(a.warmup, 3))
+        ms64 = max_over_ranks(ms64, ws)
+        out["fp64"] = {"value": ws * n * a.m * k64 / (ms64 / 1e3), "unit": "DoF-steps/s", "steps": k64,
+                       "ms_per_step": ms64 / k64,
+                       "cg_iterations_per_step": (s1["cg_iterations"] - s0["cg_iterations"]) / k64}
+        out["mixed_over_fp64"] = out["value"] / out["fp64"]["value"]
+    return out
+
+
+def run_reference(a, rank, ws):
+    """The oracle as the reference arm, timed on the host cores (rank 0 only)."""
+    import numpy as np
+
+    import workload as w
+    from oracle import seg_oracle as o
+
+    xyz, tri = w.icosphere(a.level)
+    n = xyz.shape[0]
+    M, K = o.assemble(xyz, tri)
+    U = o.initial_state(M, w.uniform01(a.seed, n, a.m))
+    t0 = time.perf_counter()
+    o.heat_step(M, K, a.tau, U[:, :1])
+    t_col = time.perf_counter() - t0
+    per_step = a.reference_budget_seconds / max(1, a.steps + a.warmup)
+    c = int(max(1, min(a.m, per_step // max(t_col, 1e-9))))
+    for _ in range(a.warmup):
+        U[:, :c] = o.step(M, K, a.tau, a.eps, U[:, :c])
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        U[:, :c] = o.step(M, K, a.tau, a.eps, U[:, :c])
+    dt = time.perf_counter() - t0
+    value = n * c * a.steps / dt
+    sample = (f"each step: one FP64 oracle step (numpy/scipy, single thread) of the first {c} of {a.m} "
+              f"components on the level-{a.level} sphere")
+    return {
+        "metric": METRIC, "value": value, "unit": "DoF-steps/s", "n_gpus": ws, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": dt / a.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": workload_name(a), "n_vert": n, "m": a.m, "components_per_sample": c},
+        "cpu_baseline": {"value": value, "unit": "DoF-steps/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "DoF-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    a = parse()
+    rank, ws, local = dist_setup(a)
+    if a.impl == "reference":
+        if rank == 0:
+            os.environ.setdefault("OMP_NUM_THREADS", "1")
+            print(json.dumps(run_reference(a, rank, ws)), flush=True)
+        return
+    out = run_ours(a, rank, ws, local)
+    if rank == 0:
+        if not a.no_cpu_baseline and ws >= 1:
+            out["cpu_baseline"] = cpu_baseline(a)
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,220 @@
+/*
+ * seg.h -- C ABI of the GB300 eigenfunction-segregation library.
+ *
+ * The library computes the operator-split gradient flow of Elliott & Ranner,
+ * "A computational approach to an optimal partition problem on surfaces"
+ * (Algorithm 2.2): m piecewise-linear surface finite-element functions u_i on
+ * a triangulated surface Gamma_h are advanced by
+ *   step 1  (M + tau K) u~_i = M u_i^k                  (implicit Euler heat step)
+ *   step 2  u^_i = u~_i exp(-(2 tau/eps^2) sum_{j!=i} u~_j^2)   (nodal ODE, exact)
+ *   step 3  u_i^{k+1} = u^_i / ||u^_i||_{L2(Gamma_h)}   (renormalisation)
+ * with M, K the P1 mass and stiffness matrices (Sec. 2.1).  The energies are
+ * those of Problem 2.1 and eq. (Seps-u); the eigenvalue estimates are the H^1
+ * semi-norms of Sec. 3.2 and the lambda formula of Sec. 1.1.
+ *
+ * Conventions (all entry points):
+ *  - Every call returns a seg_status; SEG_OK == 0.  On error, seg_last_error()
+ *    returns a thread-local message.  No call aborts or throws.
+ *  - Handles are owned by the library and released with the *_destroy calls.
+ *    A seg_problem may be shared read-only by any number of seg_state objects;
+ *    it must outlive them.  A seg_mesh may be destroyed after seg_assemble.
+ *  - Input arrays are copied.  Output arrays are caller-allocated; unless an
+ *    argument says otherwise they are HOST memory and the call returns after
+ *    the data is written (it synchronises the state's CUDA stream).
+ *  - Vertex-major layout: u[z * m + i] is component i at vertex z, in the
+ *    caller's vertex numbering (the library reorders vertices internally for
+ *    locality and undoes the permutation on every input and output).
+ *  - All device work of a state runs on the CUDA stream given at creation.
+ *  - Calls on one state are not thread-safe; distinct states may be used from
+ *    distinct threads.
+ */
+#ifndef SEG_H
+#define SEG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct seg_mesh seg_mesh;
+typedef struct seg_problem seg_problem;
+typedef struct seg_state seg_state;
+
+typedef enum {
+  SEG_OK = 0,
+  SEG_ERR_ARG = -1,            /* invalid argument (null handle, bad size, out-of-range index) */
+  SEG_ERR_MESH = -2,           /* degenerate or inconsistent triangulation */
+  SEG_ERR_CUDA = -3,           /* a CUDA runtime call failed (message has the CUDA error) */
+  SEG_ERR_NO_MEMORY = -4,      /* host or device allocation failed */
+  SEG_ERR_NOT_CONVERGED = -5,  /* a step-1 solve reached cg_maxit before cg_rtol */
+  SEG_ERR_NONFINITE = -6,      /* a norm or energy became NaN/Inf or a component vanished */
+  SEG_ERR_TIMEOUT = -7,        /* reserved: a bounded device wait gave up */
+  SEG_ERR_UNSUPPORTED = -8     /* configuration outside the supported range (e.g. m > 32) */
+} seg_status;
+
+typedef enum {
+  SEG_FP64 = 0,        /* all vectors, matrices and reductions in IEEE float64 */
+  SEG_MIXED_FP32 = 1   /* float32 vectors/matrices/exp; inner products, norms, CG
+                          alpha/beta and energies accumulated to float64 accuracy */
+} seg_precision;
+
+typedef enum {
+  SEG_INIT_ONEHOT = 0,  /* Sec. 2.2: one random component set to 1 per vertex */
+  SEG_INIT_UNIFORM = 1  /* every component uniform in [0, 1) */
+} seg_init;
+
+/* Optional parameters.  Zero-initialise and set what you need; a zero or
+ * negative field selects the default given beside it. */
+typedef struct {
+  double cg_rtol;        /* step-1 CG stops at ||r||_2 <= cg_rtol ||M u||_2 per component;
+                            default 1e-12 (SEG_FP64), 1e-7 (SEG_MIXED_FP32) */
+  int32_t cg_maxit;      /* default 1000 */
+  int32_t grid_blocks;   /* CUDA blocks of the row kernels; default 2 per SM */
+  int64_t check_every;   /* Sec. 2.2 stop rule cadence M_tau; default round(0.1 / tau);
+                            the energy check is skipped entirely if set < 0 */
+  double energy_tol;     /* stop when |total_k - total_{k - M_tau}| < energy_tol; default
+                            1e-6 (Sec. 2.2); a negative value disables stopping */
+} seg_params;
+
+typedef struct {
+  int64_t steps;            /* steps completed since the state was (re)initialised */
+  int64_t cg_iterations;    /* total step-1 CG iterations */
+  int32_t cg_last;          /* CG iterations of the last completed step */
+  int32_t cg_max;           /* largest per-step CG iteration count */
+  int32_t converged;        /* 1 once the Sec. 2.2 stop rule fired */
+  int32_t status_bits;      /* bit0: a solve hit cg_maxit; bit1: non-finite norm/energy */
+  double last_check_total;  /* total energy at the latest stop-rule check */
+  int64_t checks;           /* number of stop-rule checks evaluated */
+} seg_stats;
+
+/* ------------------------------------------------------------------ meshes */
+
+/* Sec. 2.1: a triangulated surface Gamma_h.  xyz[n_vert*3] vertex coordinates
+ * (float64), tri[n_tri*3] vertex indices (int32, 0-based, outward orientation).
+ * Both are copied.  SEG_ERR_ARG for indices out of range or n < 3;
+ * SEG_ERR_MESH for a zero-area triangle or a repeated vertex in a triangle. */
+seg_status seg_create_mesh(const double* xyz, int64_t n_vert, const int32_t* tri, int64_t n_tri,
+                           seg_mesh** out);
+
+/* Unit-sphere icosphere of the given level (N = 10*4^level + 2 vertices, all on
+ * |x| = 1): the icosahedron split level times through its edge midpoints. */
+seg_status seg_mesh_icosphere(int32_t level, seg_mesh** out);
+
+/* The icosphere mapped radially onto x^2/a^2 + y^2/b^2 + z^2/c^2 = 1. */
+seg_status seg_mesh_ellipsoid(int32_t level, double a, double b, double c, seg_mesh** out);
+
+/* Torus ((R + r cos v) cos u, (R + r cos v) sin u, r sin v) on an nu x nv grid,
+ * each grid quad split along one fixed diagonal. */
+seg_status seg_mesh_torus(int32_t nu, int32_t nv, double R, double r, seg_mesh** out);
+
+/* Sizes of a mesh, and a copy of its arrays (either output may be NULL). */
+seg_status seg_mesh_info(const seg_mesh* mesh, int64_t* n_vert, int64_t* n_tri);
+seg_status seg_mesh_get(const seg_mesh* mesh, double* xyz, int32_t* tri);
+void seg_mesh_destroy(seg_mesh* mesh);
+
+/* ---------------------------------------------------------------- assembly */
+
+/* Sec. 2.1 / Algorithm 2.2 step 1: assemble the P1 mass matrix M, stiffness
+ * matrix K and A = M + tau K on Gamma_h (float64 on the host, stored on the
+ * current CUDA device in the requested precision) for time step tau > 0. */
+seg_status seg_assemble(const seg_mesh* mesh, double tau, seg_precision precision,
+                        seg_problem** out);
+
+/* n_vert, number of nonzeros of M/K/A, tau, total area |Gamma_h| (any may be NULL). */
+seg_status seg_problem_info(const seg_problem* p, int64_t* n_vert, int64_t* nnz, double* tau,
+                            double* area);
+void seg_problem_destroy(seg_problem* p);
+
+/* ------------------------------------------------------------------- state */
+
+/* Create the state of m >= 1 components (m <= 32) with penalty eps > 0 and
+ * random initial data (Sec. 2.2) drawn on the device from the counter-based
+ * generator U(z,i) = (splitmix64(seed ^ splitmix64(z*m+i)) >> 11) * 2^-53,
+ * each component then normalised in L2(Gamma_h).  opt may be NULL.
+ * cuda_stream is a cudaStream_t (NULL = the library's own stream). */
+seg_status seg_state_create(const seg_problem* p, int32_t m, double eps, seg_init init,
+                            uint64_t seed, const seg_params* opt, void* cuda_stream,
+                            seg_state** out);
+void seg_state_destroy(seg_state* s);
+
+/* Replace the state by the L2(Gamma_h)-normalisation of u[n_vert*m] (float64,
+ * caller's vertex order).  If is_device != 0, u is a device pointer on the
+ * current device, otherwise host memory.  Resets steps, statistics and the
+ * stop rule. */
+seg_status seg_set_u(seg_state* s, const double* u, int32_t is_device);
+
+/* Write the current normalised state u[n_vert*m] (float64, caller's vertex
+ * order) to host memory, or device memory if is_device != 0. */
+seg_status seg_get_u(seg_state* s, double* u, int32_t is_device);
+
+/* ------------------------------------------------------------------- steps */
+
+/* Algorithm 2.2: advance up to nsteps steps.  Stops early when the Sec. 2.2
+ * rule fires (energy change below energy_tol at a check every check_every
+ * steps); *steps_done (nullable) receives the steps actually taken.  Returns
+ * SEG_ERR_NOT_CONVERGED if any step-1 solve hit cg_maxit (the steps still
+ * complete), SEG_ERR_NONFINITE if a norm or energy became non-finite (the run
+ * halts).  Synchronises the stream. */
+seg_status seg_step(seg_state* s, int64_t nsteps, int64_t* steps_done);
+
+/* As seg_step but only enqueues the work on the state's stream and returns;
+ * seg_sync() waits and reports the same status and step count. */
+seg_status seg_step_async(seg_state* s, int64_t nsteps);
+seg_status seg_sync(seg_state* s, int64_t* steps_done);
+
+/* One stage of Algorithm 2.2 on its own (for inspection and testing):
+ * stage 1 = heat step (M + tau K) u~ = M u, stage 2 = nodal segregation ODE,
+ * stage 3 = L2(Gamma_h) renormalisation.  Stages 1, 2, 3 in order equal one
+ * seg_step.  After stage 1 or 2, seg_get_u returns the un-normalised u~ or u^
+ * scaled by the current normalisation factors; the state must be brought back
+ * with stage 3 (or seg_set_u) before seg_step.  Synchronises. */
+seg_status seg_substep(seg_state* s, int32_t stage);
+
+/* ---------------------------------------------------------------- outputs */
+
+/* Energies of the current state (Problem 2.1, eq. (Seps-u), tables of Sec. 3):
+ *   total      = sum_i D_i + S_eps   (the paper's reported "total energy")
+ *   functional = 0.5 sum_i D_i + S_eps   (E^{eps,h})
+ *   dirichlet  = sum_i D_i, D_i = int |grad u_i|^2 = u_i^T K u_i
+ *   s_eps      = eps^-2 int sum_i sum_{j!=i} u_i^2 u_j^2 (exact quadrature)
+ * Any output pointer may be NULL. */
+seg_status seg_energy(seg_state* s, double* total, double* functional, double* dirichlet,
+                      double* s_eps);
+
+/* Eigenvalue estimates per component (host arrays of length m, nullable):
+ * lambda[i] = D_i (Sec. 3.2: the H^1 semi-norm of the normalised component),
+ * lambda_cl[i] = D_i + (2/eps^2) int u_i^2 sum_{j!=i} u_j^2 (the formula of Sec. 1.1). */
+seg_status seg_eigenvalue_estimates(seg_state* s, double* lambda, double* lambda_cl);
+
+/* Partition read-out per vertex (host arrays of length n_vert, nullable):
+ * argmax[z] = argmax_i u_i(z) (lowest index on ties); v_positive[z] = 1 if
+ * v_i(z) = u_i(z) - sum_{j!=i} u_j(z) > 0 for that i (eq. (vi)), else 0. */
+seg_status seg_labels(seg_state* s, int32_t* argmax, uint8_t* v_positive);
+
+seg_status seg_get_stats(seg_state* s, seg_stats* out);
+
+/* Thread-local description of the last error of this thread ("" if none). */
+const char* seg_last_error(void);
+
+/* -------------------------------------------------------------- diagnostics */
+
+/* Time `reps` back-to-back launches of one hot-path kernel of this state on
+ * its stream with CUDA events; *ms_per_launch receives the mean.  which:
+ * 0 = start pass (residual, norms, Dirichlet energy), 1 = CG pass A (search
+ * direction update + A p + p.Ap), 2 = CG pass B (residual update + dots),
+ * 3 = finish pass (last x update + nodal ODE), 4 = energy pass (S_eps and the
+ * coupling integrals).  The kernels run on the state's own buffers, so the
+ * state's values are undefined afterwards: call seg_set_u before using it. */
+seg_status seg_time_kernel(seg_state* s, int32_t which, int32_t reps, double* ms_per_launch);
+
+/* Launch geometry of the row kernels of a state (nullable outputs). */
+seg_status seg_launch_info(seg_state* s, int32_t* grid_blocks, int32_t* block_threads,
+                           int32_t* lanes_per_row, int32_t* padded_m);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SEG_H */

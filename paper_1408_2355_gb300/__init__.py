@@ -1,0 +1,338 @@
+"""Python binding of the GB300 eigenfunction-segregation library (libseg.so).
+
+Argument marshalling only: every function forwards to the C entry point of
+the same name declared in include/seg.h, and all computation happens in the
+library's CUDA kernels.  There is no CPU fallback: importing this package
+raises if the compiled library is missing (build it with
+``python paper_1408_2355_gb300/build.py``).
+
+Arrays: numpy float64 / int32 / uint8 for host data; torch CUDA tensors are
+accepted wherever a device pointer is allowed (``is_device=True``).
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+import platform
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", platform.machine(), "libseg.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"libseg.so not found at {LIB_PATH}; build it with `python paper_1408_2355_gb300/build.py`"
+    )
+lib = C.CDLL(LIB_PATH)
+
+SEG_OK = 0
+SEG_ERR_ARG = -1
+SEG_ERR_MESH = -2
+SEG_ERR_CUDA = -3
+SEG_ERR_NO_MEMORY = -4
+SEG_ERR_NOT_CONVERGED = -5
+SEG_ERR_NONFINITE = -6
+SEG_ERR_TIMEOUT = -7
+SEG_ERR_UNSUPPORTED = -8
+
+SEG_FP64 = 0
+SEG_MIXED_FP32 = 1
+SEG_INIT_ONEHOT = 0
+SEG_INIT_UNIFORM = 1
+
+EXPORTED = [
+    "seg_create_mesh", "seg_mesh_icosphere", "seg_mesh_ellipsoid", "seg_mesh_torus",
+    "seg_mesh_info", "seg_mesh_get", "seg_mesh_destroy", "seg_assemble", "seg_problem_info",
+    "seg_problem_destroy", "seg_state_create", "seg_state_destroy", "seg_set_u", "seg_get_u",
+    "seg_step", "seg_step_async", "seg_sync", "seg_substep", "seg_energy",
+    "seg_eigenvalue_estimates", "seg_labels", "seg_get_stats", "seg_last_error",
+    "seg_time_kernel", "seg_launch_info",
+]
+
+
+class SegError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"seg status {status}: {message}")
+        self.status = status
+
+
+class seg_params(C.Structure):
+    _fields_ = [
+        ("cg_rtol", C.c_double),
+        ("cg_maxit", C.c_int32),
+        ("grid_blocks", C.c_int32),
+        ("check_every", C.c_int64),
+        ("energy_tol", C.c_double),
+    ]
+
+
+class seg_stats(C.Structure):
+    _fields_ = [
+        ("steps", C.c_int64),
+        ("cg_iterations", C.c_int64),
+        ("cg_last", C.c_int32),
+        ("cg_max", C.c_int32),
+        ("converged", C.c_int32),
+        ("status_bits", C.c_int32),
+        ("last_check_total", C.c_double),
+        ("checks", C.c_int64),
+    ]
+
+
+_vp = C.c_void_p
+_i32 = C.c_int32
+_i64 = C.c_int64
+_d = C.c_double
+_pp = C.POINTER(C.c_void_p)
+
+_SIG = {
+    "seg_create_mesh": [_vp, _i64, _vp, _i64, _pp],
+    "seg_mesh_icosphere": [_i32, _pp],
+    "seg_mesh_ellipsoid": [_i32, _d, _d, _d, _pp],
+    "seg_mesh_torus": [_i32, _i32, _d, _d, _pp],
+    "seg_mesh_info": [_vp, _vp, _vp],
+    "seg_mesh_get": [_vp, _vp, _vp],
+    "seg_assemble": [_vp, _d, C.c_int, _pp],
+    "seg_problem_info": [_vp, _vp, _vp, _vp, _vp],
+    "seg_state_create": [_vp, _i32, _d, C.c_int, C.c_uint64, _vp, _vp, _pp],
+    "seg_set_u": [_vp, _vp, _i32],
+    "seg_get_u": [_vp, _vp, _i32],
+    "seg_step": [_vp, _i64, _vp],
+    "seg_step_async": [_vp, _i64],
+    "seg_sync": [_vp, _vp],
+    "seg_substep": [_vp, _i32],
+    "seg_energy": [_vp, _vp, _vp, _vp, _vp],
+    "seg_eigenvalue_estimates": [_vp, _vp, _vp],
+    "seg_labels": [_vp, _vp, _vp],
+    "seg_get_stats": [_vp, _vp],
+    "seg_time_kernel": [_vp, _i32, _i32, _vp],
+    "seg_launch_info": [_vp, _vp, _vp, _vp, _vp],
+}
+for _name, _args in _SIG.items():
+    _f = getattr(lib, _name)
+    _f.argtypes = _args
+    _f.restype = C.c_int
+for _name in ("seg_mesh_destroy", "seg_problem_destroy", "seg_state_destroy"):
+    getattr(lib, _name).argtypes = [_vp]
+    getattr(lib, _name).restype = None
+lib.seg_last_error.argtypes = []
+lib.seg_last_error.restype = C.c_char_p
+
+
+def seg_last_error() -> str:
+    return lib.seg_last_error().decode()
+
+
+def _check(status, ok=(SEG_OK,)):
+    if status not in ok:
+        raise SegError(status, seg_last_error())
+    return status
+
+
+def _ptr(a):
+    """Address of a numpy array or a torch tensor (contiguous)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(C.c_void_p)
+
+
+class _Handle:
+    _destroy = None
+
+    def __init__(self, ptr):
+        self.ptr = ptr
+
+    def close(self):
+        if self.ptr:
+            getattr(lib, self._destroy)(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Mesh(_Handle):
+    _destroy = "seg_mesh_destroy"
+
+
+class Problem(_Handle):
+    _destroy = "seg_problem_destroy"
+
+    def __init__(self, ptr, mesh_keepalive=None):
+        super().__init__(ptr)
+
+
+class State(_Handle):
+    _destroy = "seg_state_destroy"
+
+    def __init__(self, ptr, problem, m):
+        super().__init__(ptr)
+        self.problem = problem  # keep the problem alive while the state exists
+        self.m = m
+
+
+# ------------------------------------------------------------------ meshes
+
+
+def seg_create_mesh(xyz, tri) -> Mesh:
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    tri = np.ascontiguousarray(tri, dtype=np.int32)
+    out = C.c_void_p()
+    _check(lib.seg_create_mesh(_ptr(xyz), xyz.shape[0], _ptr(tri), tri.shape[0], C.byref(out)))
+    return Mesh(out)
+
+
+def seg_mesh_icosphere(level: int) -> Mesh:
+    out = C.c_void_p()
+    _check(lib.seg_mesh_icosphere(level, C.byref(out)))
+    return Mesh(out)
+
+
+def seg_mesh_ellipsoid(level: int, a: float, b: float, c: float) -> Mesh:
+    out = C.c_void_p()
+    _check(lib.seg_mesh_ellipsoid(level, a, b, c, C.byref(out)))
+    return Mesh(out)
+
+
+def seg_mesh_torus(nu: int, nv: int, R: float, r: float) -> Mesh:
+    out = C.c_void_p()
+    _check(lib.seg_mesh_torus(nu, nv, R, r, C.byref(out)))
+    return Mesh(out)
+
+
+def seg_mesh_info(mesh: Mesh):
+    n, f = C.c_int64(), C.c_int64()
+    _check(lib.seg_mesh_info(mesh.ptr, C.byref(n), C.byref(f)))
+    return n.value, f.value
+
+
+def seg_mesh_get(mesh: Mesh):
+    n, f = seg_mesh_info(mesh)
+    xyz = np.empty((n, 3), dtype=np.float64)
+    tri = np.empty((f, 3), dtype=np.int32)
+    _check(lib.seg_mesh_get(mesh.ptr, _ptr(xyz), _ptr(tri)))
+    return xyz, tri
+
+
+def seg_mesh_destroy(mesh: Mesh):
+    mesh.close()
+
+
+# ---------------------------------------------------------------- assembly
+
+
+def seg_assemble(mesh: Mesh, tau: float, precision: int = SEG_FP64) -> Problem:
+    out = C.c_void_p()
+    _check(lib.seg_assemble(mesh.ptr, tau, precision, C.byref(out)))
+    return Problem(out)
+
+
+def seg_problem_info(problem: Problem):
+    n, nnz, tau, area = C.c_int64(), C.c_int64(), C.c_double(), C.c_double()
+    _check(lib.seg_problem_info(problem.ptr, C.byref(n), C.byref(nnz), C.byref(tau), C.byref(area)))
+    return {"n_vert": n.value, "nnz": nnz.value, "tau": tau.value, "area": area.value}
+
+
+def seg_problem_destroy(problem: Problem):
+    problem.close()
+
+
+# ------------------------------------------------------------------- state
+
+
+def seg_state_create(problem: Problem, m: int, eps: float, init: int = SEG_INIT_UNIFORM, seed: int = 0,
+                     params: seg_params | None = None, cuda_stream: int | None = None) -> State:
+    out = C.c_void_p()
+    pp = C.byref(params) if params is not None else None
+    _check(lib.seg_state_create(problem.ptr, m, eps, init, seed & 0xFFFFFFFFFFFFFFFF, pp,
+                                C.c_void_p(cuda_stream) if cuda_stream else None, C.byref(out)))
+    return State(out, problem, m)
+
+
+def seg_state_destroy(state: State):
+    state.close()
+
+
+def _n_vert(state: State) -> int:
+    return seg_problem_info(state.problem)["n_vert"]
+
+
+def seg_set_u(state: State, u, is_device: bool = False):
+    if not is_device:
+        u = np.ascontiguousarray(u, dtype=np.float64)
+    _check(lib.seg_set_u(state.ptr, _ptr(u), 1 if is_device else 0))
+
+
+def seg_get_u(state: State, out=None, is_device: bool = False):
+    if out is None:
+        out = np.empty((_n_vert(state), state.m), dtype=np.float64)
+        is_device = False
+    _check(lib.seg_get_u(state.ptr, _ptr(out), 1 if is_device else 0))
+    return out
+
+
+def seg_step(state: State, nsteps: int, ok_not_converged: bool = False) -> int:
+    done = C.c_int64()
+    ok = (SEG_OK, SEG_ERR_NOT_CONVERGED) if ok_not_converged else (SEG_OK,)
+    _check(lib.seg_step(state.ptr, nsteps, C.byref(done)), ok)
+    return done.value
+
+
+def seg_step_async(state: State, nsteps: int):
+    _check(lib.seg_step_async(state.ptr, nsteps))
+
+
+def seg_sync(state: State) -> int:
+    done = C.c_int64()
+    _check(lib.seg_sync(state.ptr, C.byref(done)))
+    return done.value
+
+
+def seg_substep(state: State, stage: int):
+    _check(lib.seg_substep(state.ptr, stage))
+
+
+def seg_energy(state: State) -> dict:
+    t, f, d, s = C.c_double(), C.c_double(), C.c_double(), C.c_double()
+    _check(lib.seg_energy(state.ptr, C.byref(t), C.byref(f), C.byref(d), C.byref(s)))
+    return {"total": t.value, "functional": f.value, "dirichlet": d.value, "s_eps": s.value}
+
+
+def seg_eigenvalue_estimates(state: State):
+    lam = np.empty(state.m, dtype=np.float64)
+    lam_cl = np.empty(state.m, dtype=np.float64)
+    _check(lib.seg_eigenvalue_estimates(state.ptr, _ptr(lam), _ptr(lam_cl)))
+    return lam, lam_cl
+
+
+def seg_labels(state: State):
+    n = _n_vert(state)
+    am = np.empty(n, dtype=np.int32)
+    vp = np.empty(n, dtype=np.uint8)
+    _check(lib.seg_labels(state.ptr, _ptr(am), _ptr(vp)))
+    return am, vp
+
+
+def seg_get_stats(state: State) -> dict:
+    st = seg_stats()
+    _check(lib.seg_get_stats(state.ptr, C.byref(st)))
+    return {k: getattr(st, k) for k, _ in seg_stats._fields_}
+
+
+def seg_time_kernel(state: State, which: int, reps: int) -> float:
+    ms = C.c_double()
+    _check(lib.seg_time_kernel(state.ptr, which, reps, C.byref(ms)))
+    return ms.value
+
+
+def seg_launch_info(state: State) -> dict:
+    g, b, l, p = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+    _check(lib.seg_launch_info(state.ptr, C.byref(g), C.byref(b), C.byref(l), C.byref(p)))
+    return {"grid_blocks": g.value, "block_threads": b.value, "lanes_per_row": l.value, "padded_m": p.value}

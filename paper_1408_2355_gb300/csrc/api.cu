@@ -1,0 +1,801 @@
+// C ABI of the library (declared in include/seg.h): handles, validation,
+// device buffers, and the CUDA graph of one step of Algorithm 2.2.
+//
+// The step graph is
+//     k_start -> k_energy -> WHILE(cond) { k_cg_a -> k_cg_b } -> k_finish
+// where the WHILE node's condition is set on the device by the last block of
+// k_start (any component still above tolerance), k_energy (stop rule) and
+// k_cg_b (convergence / iteration cap), so a whole step -- including the
+// data-dependent CG iteration count -- runs without a host round trip.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "seg_internal.h"
+
+using namespace segimpl;
+
+namespace {
+
+thread_local std::string g_err;
+
+seg_status fail(seg_status code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+#define SEG_CUDA(call)                                                                      \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess) return fail(SEG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+}  // namespace
+
+struct seg_mesh {
+  HostMesh h;
+};
+
+struct seg_problem {
+  int64_t n = 0, nnz = 0, f = 0;
+  double tau = 0, area = 0;
+  seg_precision prec = SEG_FP64;
+  int device = 0;
+  int* rowptr = nullptr;
+  int* col = nullptr;
+  void* valA = nullptr;
+  void* valM = nullptr;
+  void* valK = nullptr;
+  void* dinv = nullptr;
+  int* tri = nullptr;
+  void* tarea = nullptr;
+  int* perm = nullptr;
+  int* iperm = nullptr;
+};
+
+struct seg_state {
+  const seg_problem* p = nullptr;
+  int m = 0, ms = 0, lpr = 0;
+  double eps = 0;
+  seg_precision prec = SEG_FP64;
+  double cg_rtol = 0;
+  int cg_maxit = 0;
+  long long check_every = 0;
+  double energy_tol = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int grid = 0;
+  void* X = nullptr;
+  void* R = nullptr;
+  void* P0 = nullptr;
+  void* P1 = nullptr;
+  void* Q = nullptr;
+  DevCtl* ctl = nullptr;
+  void* part = nullptr;
+  double* io = nullptr;     // n * m float64 staging
+  double* ones = nullptr;   // kMaxCols ones (scale reset)
+  double* scale_backup = nullptr;
+  int* am = nullptr;
+  unsigned char* vp = nullptr;
+  DevCtl* hctl = nullptr;   // pinned mirror
+  KernelSet ks{};
+  KArgs<float> af{};
+  KArgs<double> ad{};
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphConditionalHandle cond = 0;
+  bool pending = true;      // inv_n must be recomputed before use
+};
+
+namespace {
+
+size_t vsize(seg_precision p) { return p == SEG_MIXED_FP32 ? sizeof(float) : sizeof(double); }
+
+template <typename T>
+KArgs<T>& args_of(seg_state* s);
+template <>
+KArgs<float>& args_of<float>(seg_state* s) { return s->af; }
+template <>
+KArgs<double>& args_of<double>(seg_state* s) { return s->ad; }
+
+struct Launch {
+  int set_cond = 0, force = 0, apply_x = 0, apply_ode = 0, count_step = 0, ignore_halt = 1;
+};
+
+template <typename T>
+KArgs<T> make_args(seg_state* s, const Launch& l) {
+  KArgs<T> a = args_of<T>(s);
+  a.set_cond = l.set_cond;
+  a.cond = (unsigned long long)s->cond;
+  a.force = l.force;
+  a.apply_x = l.apply_x;
+  a.apply_ode = l.apply_ode;
+  a.count_step = l.count_step;
+  a.ignore_halt = l.ignore_halt;
+  return a;
+}
+
+// Launch one row kernel (grid = s->grid) with the state's arguments.
+seg_status launch_row(seg_state* s, void* fn, const Launch& l) {
+  cudaError_t e;
+  if (s->prec == SEG_MIXED_FP32) {
+    KArgs<float> a = make_args<float>(s, l);
+    void* args[] = {&a};
+    e = cudaLaunchKernel(fn, dim3(s->grid), dim3(kBlockThreads), args, 0, s->stream);
+  } else {
+    KArgs<double> a = make_args<double>(s, l);
+    void* args[] = {&a};
+    e = cudaLaunchKernel(fn, dim3(s->grid), dim3(kBlockThreads), args, 0, s->stream);
+  }
+  if (e != cudaSuccess) return fail(SEG_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+  return SEG_OK;
+}
+
+// Launch an element-wise auxiliary kernel over `count` items with extra args.
+template <typename... Extra>
+seg_status launch_aux(seg_state* s, void* fn, long long count, Extra... extra) {
+  const int bt = 256;
+  const long long blocks = (count + bt - 1) / bt;
+  if (blocks == 0) return SEG_OK;
+  cudaError_t e;
+  if (s->prec == SEG_MIXED_FP32) {
+    KArgs<float> a = make_args<float>(s, Launch());
+    void* args[] = {&a, &extra...};
+    e = cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(bt), args, 0, s->stream);
+  } else {
+    KArgs<double> a = make_args<double>(s, Launch());
+    void* args[] = {&a, &extra...};
+    e = cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(bt), args, 0, s->stream);
+  }
+  if (e != cudaSuccess) return fail(SEG_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+  return SEG_OK;
+}
+
+seg_status sync_ctl(seg_state* s) {
+  SEG_CUDA(cudaMemcpyAsync(s->hctl, s->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, s->stream));
+  SEG_CUDA(cudaStreamSynchronize(s->stream));
+  return SEG_OK;
+}
+
+// Recompute the normalisation factors of the stored state if needed (fused
+// Algorithm 2.2 step 3 of the previous step / of freshly set data).
+seg_status ensure_norm(seg_state* s) {
+  if (!s->pending) return SEG_OK;
+  seg_status st = launch_row(s, s->ks.start, Launch());
+  if (st != SEG_OK) return st;
+  s->pending = false;
+  return SEG_OK;
+}
+
+seg_status status_from_ctl(const DevCtl& c) {
+  if (c.status & 2) return fail(SEG_ERR_NONFINITE, "a norm, inner product or energy became non-finite (or a component vanished)");
+  if (c.status & 1) return fail(SEG_ERR_NOT_CONVERGED, "a step-1 CG solve reached cg_maxit before cg_rtol");
+  return SEG_OK;
+}
+
+template <typename T>
+cudaError_t add_kernel_node(cudaGraphNode_t* node, cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps,
+                            void* fn, int grid, const KArgs<T>& a) {
+  KArgs<T> copy = a;
+  void* args[] = {&copy};
+  cudaKernelNodeParams kp{};
+  kp.func = fn;
+  kp.gridDim = dim3(grid);
+  kp.blockDim = dim3(kBlockThreads);
+  kp.sharedMemBytes = 0;
+  kp.kernelParams = args;
+  kp.extra = nullptr;
+  return cudaGraphAddKernelNode(node, g, deps, ndeps, &kp);
+}
+
+template <typename T>
+seg_status build_graph_t(seg_state* s) {
+  SEG_CUDA(cudaGraphCreate(&s->graph, 0));
+  SEG_CUDA(cudaGraphConditionalHandleCreate(&s->cond, s->graph, 0, cudaGraphCondAssignDefault));
+  Launch l;
+  l.set_cond = 1;
+  l.ignore_halt = 0;
+  KArgs<T> base = make_args<T>(s, l);
+  cudaGraphNode_t n_start, n_energy, n_loop, n_a, n_b, n_fin;
+  SEG_CUDA(add_kernel_node<T>(&n_start, s->graph, nullptr, 0, s->ks.start, s->grid, base));
+  SEG_CUDA(add_kernel_node<T>(&n_energy, s->graph, &n_start, 1, s->ks.energy, s->grid, base));
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = s->cond;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  SEG_CUDA(cudaGraphAddNode(&n_loop, s->graph, &n_energy, nullptr, 1, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  SEG_CUDA(add_kernel_node<T>(&n_a, body, nullptr, 0, s->ks.cg_a, s->grid, base));
+  SEG_CUDA(add_kernel_node<T>(&n_b, body, &n_a, 1, s->ks.cg_b, s->grid, base));
+  KArgs<T> fin = base;
+  fin.apply_x = 1;
+  fin.apply_ode = 1;
+  fin.count_step = 1;
+  SEG_CUDA(add_kernel_node<T>(&n_fin, s->graph, &n_loop, 1, s->ks.finish, s->grid, fin));
+  SEG_CUDA(cudaGraphInstantiate(&s->exec, s->graph, 0));
+  return SEG_OK;
+}
+
+template <typename T>
+void fill_args(seg_state* s) {
+  const seg_problem* p = s->p;
+  KArgs<T>& a = args_of<T>(s);
+  a = KArgs<T>{};
+  a.n = (int)p->n;
+  a.m = s->m;
+  a.ms = s->ms;
+  a.rows_per_block = (int)((p->n + s->grid - 1) / s->grid);
+  a.rowptr = p->rowptr;
+  a.col = p->col;
+  a.valA = (const T*)p->valA;
+  a.valM = (const T*)p->valM;
+  a.valK = (const T*)p->valK;
+  a.dinv = (const T*)p->dinv;
+  a.X = (T*)s->X;
+  a.R = (T*)s->R;
+  a.P0 = (T*)s->P0;
+  a.P1 = (T*)s->P1;
+  a.Q = (T*)s->Q;
+  a.ctl = s->ctl;
+  a.part = s->part;
+  a.tau = p->tau;
+  a.coef = 2.0 * p->tau / (s->eps * s->eps);
+  a.inv_eps2 = 1.0 / (s->eps * s->eps);
+  a.rtol2 = s->cg_rtol * s->cg_rtol;
+  a.maxit = s->cg_maxit;
+  a.tri = p->tri;
+  a.tarea = (const T*)p->tarea;
+  a.ntri = (int)p->f;
+  a.tri_per_block = (int)((p->f + s->grid - 1) / s->grid);
+  a.check_every = s->check_every;
+  a.energy_tol = s->energy_tol;
+}
+
+template <typename T>
+seg_status upload_vals(const std::vector<double>& src, void** dst) {
+  std::vector<T> tmp(src.begin(), src.end());
+  SEG_CUDA(cudaMalloc(dst, tmp.size() * sizeof(T)));
+  SEG_CUDA(cudaMemcpy(*dst, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return SEG_OK;
+}
+
+seg_status upload_vals_prec(seg_precision prec, const std::vector<double>& src, void** dst) {
+  return prec == SEG_MIXED_FP32 ? upload_vals<float>(src, dst) : upload_vals<double>(src, dst);
+}
+
+template <typename I>
+seg_status upload_ints(const std::vector<I>& src, I** dst) {
+  SEG_CUDA(cudaMalloc((void**)dst, std::max<size_t>(1, src.size()) * sizeof(I)));
+  if (!src.empty()) SEG_CUDA(cudaMemcpy(*dst, src.data(), src.size() * sizeof(I), cudaMemcpyHostToDevice));
+  return SEG_OK;
+}
+
+void free_state(seg_state* s) {
+  if (!s) return;
+  if (s->exec) cudaGraphExecDestroy(s->exec);
+  if (s->graph) cudaGraphDestroy(s->graph);
+  void* bufs[] = {s->X, s->R, s->P0, s->P1, s->Q, s->ctl, s->part, s->io, s->ones, s->scale_backup, s->am, s->vp};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  if (s->hctl) cudaFreeHost(s->hctl);
+  if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+  delete s;
+}
+
+seg_status reset_ctl(seg_state* s) {
+  SEG_CUDA(cudaMemsetAsync(s->ctl, 0, sizeof(DevCtl), s->stream));
+  s->pending = true;
+  return SEG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* seg_last_error(void) { return g_err.c_str(); }
+
+// ------------------------------------------------------------------ meshes
+
+seg_status seg_create_mesh(const double* xyz, int64_t n_vert, const int32_t* tri, int64_t n_tri,
+                           seg_mesh** out) {
+  if (!out) return fail(SEG_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!xyz || !tri) return fail(SEG_ERR_ARG, "xyz or tri is NULL");
+  if (n_vert < 3 || n_tri < 1 || n_vert > (int64_t)1 << 30 || n_tri > (int64_t)1 << 30)
+    return fail(SEG_ERR_ARG, "mesh sizes out of range");
+  seg_mesh* m = new (std::nothrow) seg_mesh;
+  if (!m) return fail(SEG_ERR_NO_MEMORY, "host allocation failed");
+  m->h.n = n_vert;
+  m->h.f = n_tri;
+  m->h.xyz.assign(xyz, xyz + 3 * n_vert);
+  m->h.tri.assign(tri, tri + 3 * n_tri);
+  seg_status code;
+  std::string msg = validate_mesh(m->h, &code);
+  if (code != SEG_OK) {
+    delete m;
+    return fail(code, msg);
+  }
+  *out = m;
+  return SEG_OK;
+}
+
+seg_status seg_mesh_icosphere(int32_t level, seg_mesh** out) {
+  if (!out) return fail(SEG_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (level < 0 || level > 10) return fail(SEG_ERR_ARG, "icosphere level must be in [0, 10]");
+  seg_mesh* m = new (std::nothrow) seg_mesh;
+  if (!m) return fail(SEG_ERR_NO_MEMORY, "host allocation failed");
+  make_icosphere(level, &m->h);
+  *out = m;
+  return SEG_OK;
+}
+
+seg_status seg_mesh_ellipsoid(int32_t level, double a, double b, double c, seg_mesh** out) {
+  if (!out) return fail(SEG_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!(a > 0 && b > 0 && c > 0)) return fail(SEG_ERR_ARG, "semi-axes must be positive");
+  seg_status st = seg_mesh_icosphere(level, out);
+  if (st != SEG_OK) return st;
+  std::vector<double>& x = (*out)->h.xyz;
+  for (int64_t v = 0; v < (*out)->h.n; ++v) {
+    double* p = &x[3 * v];
+    double q = std::sqrt((p[0] / a) * (p[0] / a) + (p[1] / b) * (p[1] / b) + (p[2] / c) * (p[2] / c));
+    p[0] /= q;
+    p[1] /= q;
+    p[2] /= q;
+  }
+  return SEG_OK;
+}
+
+seg_status seg_mesh_torus(int32_t nu, int32_t nv, double R, double r, seg_mesh** out) {
+  if (!out) return fail(SEG_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (nu < 3 || nv < 3 || (int64_t)nu * nv > (int64_t)1 << 29) return fail(SEG_ERR_ARG, "torus grid out of range");
+  if (!(r > 0 && R > r)) return fail(SEG_ERR_ARG, "torus radii need R > r > 0");
+  seg_mesh* m = new (std::nothrow) seg_mesh;
+  if (!m) return fail(SEG_ERR_NO_MEMORY, "host allocation failed");
+  make_torus(nu, nv, R, r, &m->h);
+  *out = m;
+  return SEG_OK;
+}
+
+seg_status seg_mesh_info(const seg_mesh* mesh, int64_t* n_vert, int64_t* n_tri) {
+  if (!mesh) return fail(SEG_ERR_ARG, "mesh is NULL");
+  if (n_vert) *n_vert = mesh->h.n;
+  if (n_tri) *n_tri = mesh->h.f;
+  return SEG_OK;
+}
+
+seg_status seg_mesh_get(const seg_mesh* mesh, double* xyz, int32_t* tri) {
+  if (!mesh) return fail(SEG_ERR_ARG, "mesh is NULL");
+  if (xyz) std::memcpy(xyz, mesh->h.xyz.data(), mesh->h.xyz.size() * sizeof(double));
+  if (tri) std::memcpy(tri, mesh->h.tri.data(), mesh->h.tri.size() * sizeof(int32_t));
+  return SEG_OK;
+}
+
+void seg_mesh_destroy(seg_mesh* mesh) { delete mesh; }
+
+// ---------------------------------------------------------------- assembly
+
+seg_status seg_assemble(const seg_mesh* mesh, double tau, seg_precision precision, seg_problem** out) {
+  if (!out) return fail(SEG_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!mesh) return fail(SEG_ERR_ARG, "mesh is NULL");
+  if (!(tau > 0) || !std::isfinite(tau)) return fail(SEG_ERR_ARG, "tau must be positive and finite");
+  if (precision != SEG_FP64 && precision != SEG_MIXED_FP32) return fail(SEG_ERR_ARG, "unknown precision");
+  HostCSR csr;
+  assemble_p1(mesh->h, &csr);
+  const int64_t n = csr.n;
+  std::vector<double> A(csr.nnz), dinv(n);
+  for (int64_t e = 0; e < csr.nnz; ++e) A[e] = csr.M[e] + tau * csr.K[e];
+  for (int64_t i = 0; i < n; ++i) {
+    double d = 0.0;
+    for (int32_t e = csr.rowptr[i]; e < csr.rowptr[i + 1]; ++e)
+      if (csr.col[e] == i) d = A[e];
+    if (!(d > 0)) return fail(SEG_ERR_MESH, "non-positive diagonal of M + tau K");
+    dinv[i] = 1.0 / d;
+  }
+  seg_problem* p = new (std::nothrow) seg_problem;
+  if (!p) return fail(SEG_ERR_NO_MEMORY, "host allocation failed");
+  p->n = n;
+  p->nnz = csr.nnz;
+  p->f = mesh->h.f;
+  p->tau = tau;
+  p->prec = precision;
+  double area = 0;
+  for (double a : csr.area) area += a;
+  p->area = area;
+  cudaError_t e = cudaGetDevice(&p->device);
+  seg_status st = SEG_OK;
+  if (e != cudaSuccess) st = fail(SEG_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  if (st == SEG_OK) st = upload_ints(csr.rowptr, &p->rowptr);
+  if (st == SEG_OK) st = upload_ints(csr.col, &p->col);
+  if (st == SEG_OK) st = upload_vals_prec(precision, A, &p->valA);
+  if (st == SEG_OK) st = upload_vals_prec(precision, csr.M, &p->valM);
+  if (st == SEG_OK) st = upload_vals_prec(precision, csr.K, &p->valK);
+  if (st == SEG_OK) st = upload_vals_prec(precision, dinv, &p->dinv);
+  if (st == SEG_OK) st = upload_ints(csr.tri_rows, &p->tri);
+  if (st == SEG_OK) st = upload_vals_prec(precision, csr.area, &p->tarea);
+  if (st == SEG_OK) st = upload_ints(csr.perm, &p->perm);
+  if (st == SEG_OK) st = upload_ints(csr.iperm, &p->iperm);
+  if (st != SEG_OK) {
+    seg_problem_destroy(p);
+    return st;
+  }
+  *out = p;
+  return SEG_OK;
+}
+
+seg_status seg_problem_info(const seg_problem* p, int64_t* n_vert, int64_t* nnz, double* tau, double* area) {
+  if (!p) return fail(SEG_ERR_ARG, "problem is NULL");
+  if (n_vert) *n_vert = p->n;
+  if (nnz) *nnz = p->nnz;
+  if (tau) *tau = p->tau;
+  if (area) *area = p->area;
+  return SEG_OK;
+}
+
+void seg_problem_destroy(seg_problem* p) {
+  if (!p) return;
+  void* bufs[] = {p->rowptr, p->col, p->valA, p->valM, p->valK, p->dinv, p->tri, p->tarea, p->perm, p->iperm};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  delete p;
+}
+
+// ------------------------------------------------------------------- state
+
+seg_status seg_state_create(const seg_problem* p, int32_t m, double eps, seg_init init, uint64_t seed,
+                            const seg_params* opt, void* cuda_stream, seg_state** out) {
+  if (!out) return fail(SEG_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!p) return fail(SEG_ERR_ARG, "problem is NULL");
+  if (m < 1) return fail(SEG_ERR_ARG, "m must be >= 1");
+  if (m > kMaxCols) return fail(SEG_ERR_UNSUPPORTED, "m must be <= 32");
+  if (!(eps > 0) || !std::isfinite(eps)) return fail(SEG_ERR_ARG, "eps must be positive and finite");
+  if (init != SEG_INIT_ONEHOT && init != SEG_INIT_UNIFORM) return fail(SEG_ERR_ARG, "unknown init kind");
+  SEG_CUDA(cudaSetDevice(p->device));
+  seg_state* s = new (std::nothrow) seg_state;
+  if (!s) return fail(SEG_ERR_NO_MEMORY, "host allocation failed");
+  s->p = p;
+  s->m = m;
+  s->eps = eps;
+  s->prec = p->prec;
+  const int vw = s->prec == SEG_MIXED_FP32 ? 4 : 2;
+  int lpr = (m + vw - 1) / vw;
+  int pw = 1;
+  while (pw < lpr) pw <<= 1;
+  s->lpr = pw;
+  s->ms = pw * vw;
+  seg_params prm{};
+  if (opt) prm = *opt;
+  s->cg_rtol = prm.cg_rtol > 0 ? prm.cg_rtol : (s->prec == SEG_MIXED_FP32 ? 1e-7 : 1e-12);
+  s->cg_maxit = prm.cg_maxit > 0 ? prm.cg_maxit : 1000;
+  s->check_every = prm.check_every > 0 ? prm.check_every
+                                       : (prm.check_every < 0 ? 0 : std::max<long long>(1, std::llround(0.1 / p->tau)));
+  s->energy_tol = prm.energy_tol > 0 ? prm.energy_tol : (prm.energy_tol < 0 ? -1.0 : 1e-6);
+  bool ok = s->prec == SEG_MIXED_FP32 ? get_kernels_f32(s->lpr, &s->ks) : get_kernels_f64(s->lpr, &s->ks);
+  if (!ok) {
+    delete s;
+    return fail(SEG_ERR_UNSUPPORTED, "no kernel specialisation for this m and precision");
+  }
+  int nsm = 0;
+  cudaError_t ce = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device);
+  if (ce != cudaSuccess) {
+    delete s;
+    return fail(SEG_ERR_CUDA, std::string("cudaDeviceGetAttribute: ") + cudaGetErrorString(ce));
+  }
+  s->grid = prm.grid_blocks > 0 ? prm.grid_blocks : 2 * nsm;
+  if (cuda_stream) {
+    s->stream = (cudaStream_t)cuda_stream;
+  } else {
+    ce = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+    if (ce != cudaSuccess) {
+      delete s;
+      return fail(SEG_ERR_CUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(ce));
+    }
+    s->own_stream = true;
+  }
+  const size_t vbytes = (size_t)p->n * s->ms * vsize(s->prec);
+  const size_t pbytes = (size_t)s->grid * kMaxDots * s->ms * 8;
+  struct {
+    void** ptr;
+    size_t bytes;
+  } allocs[] = {{&s->X, vbytes},
+                {&s->R, vbytes},
+                {&s->P0, vbytes},
+                {&s->P1, vbytes},
+                {&s->Q, vbytes},
+                {(void**)&s->ctl, sizeof(DevCtl)},
+                {&s->part, pbytes},
+                {(void**)&s->io, std::max<size_t>(8, (size_t)p->n * m * sizeof(double))},
+                {(void**)&s->ones, kMaxCols * sizeof(double)},
+                {(void**)&s->scale_backup, kMaxCols * sizeof(double)},
+                {(void**)&s->am, std::max<size_t>(4, (size_t)p->n * sizeof(int))},
+                {(void**)&s->vp, std::max<size_t>(4, (size_t)p->n)}};
+  for (auto& al : allocs) {
+    ce = cudaMalloc(al.ptr, al.bytes);
+    if (ce != cudaSuccess) {
+      free_state(s);
+      return fail(ce == cudaErrorMemoryAllocation ? SEG_ERR_NO_MEMORY : SEG_ERR_CUDA,
+                  std::string("cudaMalloc: ") + cudaGetErrorString(ce));
+    }
+    ce = cudaMemsetAsync(*al.ptr, 0, al.bytes, s->stream);
+    if (ce != cudaSuccess) {
+      free_state(s);
+      return fail(SEG_ERR_CUDA, std::string("cudaMemset: ") + cudaGetErrorString(ce));
+    }
+  }
+  ce = cudaMallocHost((void**)&s->hctl, sizeof(DevCtl));
+  if (ce != cudaSuccess) {
+    free_state(s);
+    return fail(SEG_ERR_NO_MEMORY, std::string("cudaMallocHost: ") + cudaGetErrorString(ce));
+  }
+  std::memset(s->hctl, 0, sizeof(DevCtl));
+  {
+    std::vector<double> ones(kMaxCols, 1.0);
+    ce = cudaMemcpy(s->ones, ones.data(), kMaxCols * sizeof(double), cudaMemcpyHostToDevice);
+    if (ce != cudaSuccess) {
+      free_state(s);
+      return fail(SEG_ERR_CUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(ce));
+    }
+  }
+  seg_status st;
+  if (s->prec == SEG_MIXED_FP32) {
+    fill_args<float>(s);
+    st = build_graph_t<float>(s);
+  } else {
+    fill_args<double>(s);
+    st = build_graph_t<double>(s);
+  }
+  if (st == SEG_OK) {
+    const int* perm = p->perm;
+    unsigned long long sd = (unsigned long long)seed;
+    int kind = (int)init;
+    st = launch_aux(s, s->ks.init_rng, (long long)p->n * s->ms, perm, sd, kind);
+  }
+  if (st == SEG_OK) {
+    cudaError_t se = cudaStreamSynchronize(s->stream);
+    if (se != cudaSuccess) st = fail(SEG_ERR_CUDA, std::string("init: ") + cudaGetErrorString(se));
+  }
+  if (st != SEG_OK) {
+    free_state(s);
+    return st;
+  }
+  s->pending = true;
+  *out = s;
+  return SEG_OK;
+}
+
+void seg_state_destroy(seg_state* s) {
+  if (!s) return;
+  cudaStreamSynchronize(s->stream);
+  free_state(s);
+}
+
+seg_status seg_set_u(seg_state* s, const double* u, int32_t is_device) {
+  if (!s || !u) return fail(SEG_ERR_ARG, "state or u is NULL");
+  SEG_CUDA(cudaSetDevice(s->p->device));
+  const double* src = u;
+  if (!is_device) {
+    SEG_CUDA(cudaMemcpyAsync(s->io, u, (size_t)s->p->n * s->m * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    src = s->io;
+  }
+  seg_status st = reset_ctl(s);
+  if (st != SEG_OK) return st;
+  const int* perm = s->p->perm;
+  st = launch_aux(s, s->ks.scatter_in, (long long)s->p->n * s->ms, src, perm);
+  if (st != SEG_OK) return st;
+  SEG_CUDA(cudaStreamSynchronize(s->stream));
+  s->pending = true;
+  return SEG_OK;
+}
+
+seg_status seg_get_u(seg_state* s, double* u, int32_t is_device) {
+  if (!s || !u) return fail(SEG_ERR_ARG, "state or u is NULL");
+  SEG_CUDA(cudaSetDevice(s->p->device));
+  seg_status st = ensure_norm(s);
+  if (st != SEG_OK) return st;
+  double* dst = is_device ? u : s->io;
+  const int* iperm = s->p->iperm;
+  st = launch_aux(s, s->ks.gather_out, (long long)s->p->n * s->m, dst, iperm);
+  if (st != SEG_OK) return st;
+  if (!is_device)
+    SEG_CUDA(cudaMemcpyAsync(u, s->io, (size_t)s->p->n * s->m * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  st = sync_ctl(s);
+  if (st != SEG_OK) return st;
+  return (s->hctl->status & 2) ? status_from_ctl(*s->hctl) : SEG_OK;
+}
+
+// ------------------------------------------------------------------- steps
+
+seg_status seg_step_async(seg_state* s, int64_t nsteps) {
+  if (!s) return fail(SEG_ERR_ARG, "state is NULL");
+  if (nsteps < 0) return fail(SEG_ERR_ARG, "nsteps must be >= 0");
+  SEG_CUDA(cudaSetDevice(s->p->device));
+  // remember the step count in stream order, and clear the sticky status
+  // bits of earlier calls; halted states stay halted
+  SEG_CUDA(cudaMemcpyAsync(&s->ctl->step_mark, &s->ctl->step, sizeof(long long), cudaMemcpyDeviceToDevice,
+                           s->stream));
+  SEG_CUDA(cudaMemsetAsync(&s->ctl->status, 0, sizeof(int), s->stream));
+  for (int64_t k = 0; k < nsteps; ++k) SEG_CUDA(cudaGraphLaunch(s->exec, s->stream));
+  if (nsteps > 0) s->pending = true;
+  return SEG_OK;
+}
+
+seg_status seg_sync(seg_state* s, int64_t* steps_done) {
+  if (!s) return fail(SEG_ERR_ARG, "state is NULL");
+  seg_status st = sync_ctl(s);
+  if (st != SEG_OK) return st;
+  if (steps_done) *steps_done = s->hctl->step - s->hctl->step_mark;
+  return status_from_ctl(*s->hctl);
+}
+
+seg_status seg_step(seg_state* s, int64_t nsteps, int64_t* steps_done) {
+  seg_status st = seg_step_async(s, nsteps);
+  if (st != SEG_OK) return st;
+  return seg_sync(s, steps_done);
+}
+
+seg_status seg_substep(seg_state* s, int32_t stage) {
+  if (!s) return fail(SEG_ERR_ARG, "state is NULL");
+  if (stage < 1 || stage > 3) return fail(SEG_ERR_ARG, "stage must be 1, 2 or 3");
+  SEG_CUDA(cudaSetDevice(s->p->device));
+  seg_status st = SEG_OK;
+  if (stage == 1) {
+    const bool keep_scale = !s->pending;
+    if (keep_scale)
+      SEG_CUDA(cudaMemcpyAsync(s->scale_backup, s->ctl->inv_n, kMaxCols * sizeof(double), cudaMemcpyDeviceToDevice,
+                               s->stream));
+    SEG_CUDA(cudaMemsetAsync(&s->ctl->status, 0, sizeof(int), s->stream));
+    st = launch_row(s, s->ks.start, Launch());
+    if (st != SEG_OK) return st;
+    s->pending = false;
+    st = sync_ctl(s);
+    if (st != SEG_OK) return st;
+    while (s->hctl->cont) {
+      if ((st = launch_row(s, s->ks.cg_a, Launch())) != SEG_OK) return st;
+      if ((st = launch_row(s, s->ks.cg_b, Launch())) != SEG_OK) return st;
+      if ((st = sync_ctl(s)) != SEG_OK) return st;
+    }
+    Launch l;
+    l.apply_x = 1;
+    if ((st = launch_row(s, s->ks.finish, l)) != SEG_OK) return st;
+    if (keep_scale)
+      SEG_CUDA(cudaMemcpyAsync(s->ctl->inv_n, s->scale_backup, kMaxCols * sizeof(double), cudaMemcpyDeviceToDevice,
+                               s->stream));
+  } else if (stage == 2) {
+    if ((st = ensure_norm(s)) != SEG_OK) return st;
+    Launch l;
+    l.apply_ode = 1;
+    if ((st = launch_row(s, s->ks.finish, l)) != SEG_OK) return st;
+    SEG_CUDA(cudaMemcpyAsync(s->ctl->inv_n, s->ones, kMaxCols * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
+    s->pending = false;
+  } else {
+    s->pending = true;
+    if ((st = ensure_norm(s)) != SEG_OK) return st;
+  }
+  st = sync_ctl(s);
+  if (st != SEG_OK) return st;
+  return status_from_ctl(*s->hctl);
+}
+
+// ---------------------------------------------------------------- outputs
+
+static seg_status evaluate_energy(seg_state* s) {
+  SEG_CUDA(cudaSetDevice(s->p->device));
+  s->pending = true;
+  seg_status st = ensure_norm(s);
+  if (st != SEG_OK) return st;
+  Launch l;
+  l.force = 1;
+  st = launch_row(s, s->ks.energy, l);
+  if (st != SEG_OK) return st;
+  return sync_ctl(s);
+}
+
+seg_status seg_energy(seg_state* s, double* total, double* functional, double* dirichlet, double* s_eps) {
+  if (!s) return fail(SEG_ERR_ARG, "state is NULL");
+  seg_status st = evaluate_energy(s);
+  if (st != SEG_OK) return st;
+  const DevCtl& c = *s->hctl;
+  if (total) *total = c.e_total;
+  if (functional) *functional = 0.5 * c.e_dir + c.e_s;
+  if (dirichlet) *dirichlet = c.e_dir;
+  if (s_eps) *s_eps = c.e_s;
+  if (!std::isfinite(c.e_total)) return fail(SEG_ERR_NONFINITE, "energy is not finite");
+  return (c.status & 2) ? status_from_ctl(c) : SEG_OK;
+}
+
+seg_status seg_eigenvalue_estimates(seg_state* s, double* lambda, double* lambda_cl) {
+  if (!s) return fail(SEG_ERR_ARG, "state is NULL");
+  seg_status st = evaluate_energy(s);
+  if (st != SEG_OK) return st;
+  const DevCtl& c = *s->hctl;
+  for (int i = 0; i < s->m; ++i) {
+    if (lambda) lambda[i] = c.lam[i];
+    if (lambda_cl) lambda_cl[i] = c.lam[i] + 2.0 * c.coup[i] / (s->eps * s->eps);
+  }
+  return (c.status & 2) ? status_from_ctl(c) : SEG_OK;
+}
+
+seg_status seg_labels(seg_state* s, int32_t* argmax, uint8_t* v_positive) {
+  if (!s) return fail(SEG_ERR_ARG, "state is NULL");
+  SEG_CUDA(cudaSetDevice(s->p->device));
+  seg_status st = ensure_norm(s);
+  if (st != SEG_OK) return st;
+  int* am = s->am;
+  unsigned char* vp = s->vp;
+  const int* iperm = s->p->iperm;
+  st = launch_aux(s, s->ks.labels, s->p->n, am, vp, iperm);
+  if (st != SEG_OK) return st;
+  if (argmax) SEG_CUDA(cudaMemcpyAsync(argmax, s->am, (size_t)s->p->n * sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+  if (v_positive) SEG_CUDA(cudaMemcpyAsync(v_positive, s->vp, (size_t)s->p->n, cudaMemcpyDeviceToHost, s->stream));
+  return sync_ctl(s);
+}
+
+seg_status seg_get_stats(seg_state* s, seg_stats* out) {
+  if (!s || !out) return fail(SEG_ERR_ARG, "state or out is NULL");
+  SEG_CUDA(cudaSetDevice(s->p->device));
+  seg_status st = sync_ctl(s);
+  if (st != SEG_OK) return st;
+  const DevCtl& c = *s->hctl;
+  out->steps = c.step;
+  out->cg_iterations = c.cg_total;
+  out->cg_last = c.cg_last;
+  out->cg_max = c.cg_max;
+  out->converged = c.halted == 1 ? 1 : 0;
+  out->status_bits = c.status;
+  out->last_check_total = c.e_prev;
+  out->checks = c.checks;
+  return SEG_OK;
+}
+
+// -------------------------------------------------------------- diagnostics
+
+seg_status seg_time_kernel(seg_state* s, int32_t which, int32_t reps, double* ms_per_launch) {
+  if (!s || !ms_per_launch) return fail(SEG_ERR_ARG, "state or output is NULL");
+  if (which < 0 || which > 4 || reps < 1) return fail(SEG_ERR_ARG, "which must be 0..4 and reps >= 1");
+  SEG_CUDA(cudaSetDevice(s->p->device));
+  void* fns[] = {s->ks.start, s->ks.cg_a, s->ks.cg_b, s->ks.finish, s->ks.energy};
+  Launch l;
+  l.force = 1;
+  l.apply_x = 1;
+  l.apply_ode = 1;
+  cudaEvent_t e0, e1;
+  SEG_CUDA(cudaEventCreate(&e0));
+  SEG_CUDA(cudaEventCreate(&e1));
+  seg_status st = launch_row(s, fns[which], l);  // warm-up
+  if (st == SEG_OK) {
+    cudaEventRecord(e0, s->stream);
+    for (int r = 0; r < reps && st == SEG_OK; ++r) st = launch_row(s, fns[which], l);
+    cudaEventRecord(e1, s->stream);
+  }
+  cudaError_t ce = cudaEventSynchronize(e1);
+  float ms = 0;
+  if (st == SEG_OK && ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != SEG_OK) return st;
+  if (ce != cudaSuccess) return fail(SEG_ERR_CUDA, std::string("event timing: ") + cudaGetErrorString(ce));
+  *ms_per_launch = ms / reps;
+  s->pending = true;
+  return SEG_OK;
+}
+
+seg_status seg_launch_info(seg_state* s, int32_t* grid_blocks, int32_t* block_threads, int32_t* lanes_per_row,
+                           int32_t* padded_m) {
+  if (!s) return fail(SEG_ERR_ARG, "state is NULL");
+  if (grid_blocks) *grid_blocks = s->grid;
+  if (block_threads) *block_threads = kBlockThreads;
+  if (lanes_per_row) *lanes_per_row = s->lpr;
+  if (padded_m) *padded_m = s->ms;
+  return SEG_OK;
+}
+
+}  // extern "C"

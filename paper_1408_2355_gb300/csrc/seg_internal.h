@@ -1,0 +1,135 @@
+// Internal definitions shared by the host orchestration and the CUDA kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "seg.h"
+
+namespace segimpl {
+
+constexpr int kMaxCols = 32;       // padded components per vertex row
+constexpr int kBlockThreads = 256;  // threads per block of every row kernel
+constexpr int kMaxDots = 5;        // inner products fused into one pass
+constexpr int kNumCounters = 8;    // last-block tickets, one per kernel kind
+
+enum CounterSlot { kCtrStart = 0, kCtrCgA = 1, kCtrCgB = 2, kCtrEnergy = 3 };
+
+// Device-resident control block: per-component scalars of the solve and the
+// step loop.  Written only by the last block of a reduction kernel (or by one
+// thread), read by the following kernels; the host copies it back at sync
+// points.
+struct DevCtl {
+  double n2[kMaxCols];        // ||X_i||_M^2 of the stored (un-normalised) components
+  double inv_n[kMaxCols];     // scale of the represented state u_i = X_i * inv_n[i]
+  double lam[kMaxCols];       // D_i = u_i^T K u_i of the normalised state
+  double tol2[kMaxCols];      // (cg_rtol ||M X_i||_2)^2
+  double rz[kMaxCols];        // r^T D^-1 r of the current CG iterate
+  double alpha[2][kMaxCols];  // CG step length of the last two iterations
+  double beta[kMaxCols];      // CG direction update factor
+  double coup[kMaxCols];      // int u_i^2 sum_{j != i} u_j^2 (normalised state)
+  int active[kMaxCols];       // component still iterating in the current solve
+  int it;                     // CG iterations completed in the current solve
+  int cont;                   // loop-continue flag (mirrors the graph conditional)
+  int halted;                 // 0 running, 1 stop rule met, 2 error
+  int status;                 // bit0: solve hit maxit, bit1: non-finite value
+  long long step;             // steps completed
+  long long cg_total;         // total CG iterations
+  int cg_last;
+  int cg_max;
+  long long checks;           // stop-rule checks evaluated
+  double e_total;             // last energy evaluation: sum D + S_eps
+  double e_dir;
+  double e_s;
+  double e_prev;              // total of the previous stop-rule check
+  int have_prev;
+  int pad0;
+  long long step_mark;        // ctl->step when the last batch of steps was enqueued
+  unsigned int counters[kNumCounters];
+};
+
+// Arguments of every hot-path kernel (passed by value; identical struct for
+// all kernels of a state so that one graph node layout fits all).
+template <typename T>
+struct KArgs {
+  int n;    // vertex rows
+  int m;    // components
+  int ms;   // padded components (row stride)
+  int rows_per_block;
+  const int* rowptr;
+  const int* col;
+  const T* valA;   // A = M + tau K
+  const T* valM;
+  const T* valK;
+  const T* dinv;   // 1 / diag(A)
+  T* X;            // state / CG iterate
+  T* R;            // residual
+  T* P0;           // search directions (ping-pong)
+  T* P1;
+  T* Q;            // A p
+  DevCtl* ctl;
+  void* part;      // per-block partial sums
+  double tau;
+  double coef;     // 2 tau / eps^2
+  double inv_eps2;
+  double rtol2;
+  int maxit;
+  int set_cond;    // 1 when launched inside the step graph
+  unsigned long long cond;  // cudaGraphConditionalHandle of the CG loop
+  // energy pass
+  const int* tri;  // [F][3] rows of the triangle corners (internal numbering)
+  const T* tarea;  // |T|
+  int ntri;
+  int tri_per_block;
+  long long check_every;
+  double energy_tol;
+  int force;       // evaluate the energy regardless of the cadence
+  int apply_x;     // finish pass: apply the lagged CG update of X
+  int apply_ode;   // finish pass: apply the nodal segregation ODE
+  int count_step;  // finish pass: increment the step counter
+  int ignore_halt; // run even if the control block is halted (direct calls)
+};
+
+// Function table of one (precision, lanes-per-row) specialisation.
+struct KernelSet {
+  void* start;
+  void* cg_a;
+  void* cg_b;
+  void* finish;
+  void* energy;
+  void* init_rng;     // (args, perm, seed, kind)
+  void* scatter_in;   // (args, src, perm)
+  void* gather_out;   // (args, dst, iperm)
+  void* labels;       // (args, am, vp, iperm)
+};
+
+bool get_kernels_f32(int lpr, KernelSet* ks);
+bool get_kernels_f64(int lpr, KernelSet* ks);
+
+// Host-side mesh and assembly (mesh.cpp / assemble.cpp).
+struct HostMesh {
+  std::vector<double> xyz;  // [n][3]
+  std::vector<int32_t> tri;  // [f][3]
+  int64_t n = 0, f = 0;
+};
+
+std::string validate_mesh(const HostMesh& m, seg_status* code);
+void make_icosphere(int level, HostMesh* out);
+void make_torus(int nu, int nv, double R, double r, HostMesh* out);
+
+struct HostCSR {
+  int64_t n = 0, nnz = 0;
+  std::vector<int32_t> rowptr, col;
+  std::vector<double> M, K;
+  std::vector<double> area;   // per triangle (internal order = input order)
+  std::vector<int32_t> perm;   // internal row -> caller vertex
+  std::vector<int32_t> iperm;  // caller vertex -> internal row
+  std::vector<int32_t> tri_rows;  // triangles in internal row numbering
+};
+
+void assemble_p1(const HostMesh& mesh, HostCSR* out);
+
+}  // namespace segimpl

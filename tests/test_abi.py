@@ -1,0 +1,102 @@
+"""The C-ABI library loads, exports every declared entry point, and its
+host-only calls (mesh creation, validation, generators) behave.  No call
+here touches the GPU."""
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workload as w
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def seg():
+    import __graft_entry__ as g
+
+    g.build()
+    import paper_1408_2355_gb300 as seg
+
+    return seg
+
+
+def _declared_symbols():
+    text = open(os.path.join(ROOT, "include", "seg.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(seg_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(seg):
+    names = _declared_symbols()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(seg.lib, n), n
+    assert set(names) == set(seg.EXPORTED)
+
+
+def test_no_oracle_in_the_library_path():
+    pkg = os.path.join(ROOT, "paper_1408_2355_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".cpp", ".h")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert "oracle" not in src.replace("oracle-free", ""), f
+                assert "import workload" not in src, f
+
+
+def test_struct_layouts_match_header(seg):
+    assert C.sizeof(seg.seg_params) == 32
+    assert C.sizeof(seg.seg_stats) == 48
+
+
+@pytest.mark.parametrize("level", [0, 1, 3, 5])
+def test_native_icosphere_equals_shared_generator(seg, level):
+    m = seg.seg_mesh_icosphere(level)
+    xyz, tri = seg.seg_mesh_get(m)
+    rx, rt = w.icosphere(level)
+    assert np.array_equal(tri, rt)
+    assert np.abs(xyz - rx).max() < 1e-15
+
+
+def test_native_torus_and_ellipsoid_equal_shared_generator(seg):
+    xyz, tri = seg.seg_mesh_get(seg.seg_mesh_torus(24, 12, 1.0, 0.4))
+    rx, rt = w.torus(24, 12, 1.0, 0.4)
+    assert np.array_equal(tri, rt) and np.abs(xyz - rx).max() < 1e-14
+    xyz, tri = seg.seg_mesh_get(seg.seg_mesh_ellipsoid(3, 1.0, 0.8, 0.6))
+    rx, rt = w.ellipsoid(3, 1.0, 0.8, 0.6)
+    assert np.array_equal(tri, rt) and np.abs(xyz - rx).max() < 1e-14
+
+
+def test_mesh_validation_errors(seg):
+    xyz, tri = w.icosphere(1)
+    m = seg.seg_create_mesh(xyz, tri)
+    assert seg.seg_mesh_info(m) == (42, 80)
+    bad = tri.copy()
+    bad[3, 1] = 42
+    with pytest.raises(seg.SegError) as e:
+        seg.seg_create_mesh(xyz, bad)
+    assert e.value.status == seg.SEG_ERR_ARG
+    bad = tri.copy()
+    bad[0, 1] = bad[0, 0]
+    with pytest.raises(seg.SegError) as e:
+        seg.seg_create_mesh(xyz, bad)
+    assert e.value.status == seg.SEG_ERR_MESH
+    flat = xyz.copy()
+    flat[tri[5, 1]] = flat[tri[5, 0]]
+    with pytest.raises(seg.SegError) as e:
+        seg.seg_create_mesh(flat, tri)
+    assert e.value.status == seg.SEG_ERR_MESH
+    nan = xyz.copy()
+    nan[7, 2] = np.nan
+    with pytest.raises(seg.SegError) as e:
+        seg.seg_create_mesh(nan, tri)
+    assert e.value.status == seg.SEG_ERR_ARG
+    with pytest.raises(seg.SegError):
+        seg.seg_mesh_icosphere(-1)
+    with pytest.raises(seg.SegError):
+        seg.seg_mesh_torus(8, 8, 0.3, 0.4)
+    assert "R > r" in seg.seg_last_error()
