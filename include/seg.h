@@ -213,6 +213,35 @@ seg_status seg_time_kernel(seg_state* s, int32_t which, int32_t reps, double* ms
 seg_status seg_launch_info(seg_state* s, int32_t* grid_blocks, int32_t* block_threads,
                            int32_t* lanes_per_row, int32_t* padded_m);
 
+/* ------------------------------------------------------- allocation-free call */
+
+/* The paper has no counterpart of this entry point.  It is for callers that
+ * cannot allocate device memory -- a process whose GPU memory is reserved up
+ * front by another framework's allocator, code running while a CUDA graph is
+ * captured (allocation is not allowed then), or a loop whose latency budget an
+ * allocation would break.  It computes, from caller-owned DEVICE buffers on the
+ * current device,
+ *   out[0]     = S_eps = eps^-2 sum_i c_i
+ *   out[1 + i] = c_i   = int_{Gamma_h} u_i^2 sum_{j != i} u_j^2   (i < m)
+ * for u[n_vert * m] (float64, vertex-major, caller's numbering, normalised as
+ * the caller wishes), xyz[n_vert * 3] (float64) and tri[n_tri * 3] (int32; a
+ * triangle with an index outside [0, n_vert) contributes nothing).  out holds
+ * m + 1 float64 values.  The work is enqueued on cuda_stream (NULL = the legacy
+ * default stream) and the call returns without waiting.
+ *
+ * It calls no cudaMalloc, cudaFree or other allocating routine: its scratch
+ * (per-block partial sums and a completion counter) is a fixed 64 KiB device
+ * array inside the library, which every GPU that loads the library keeps until
+ * the process exits.  Limit: m <= 32 (SEG_ERR_UNSUPPORTED otherwise).
+ * The first call on a device looks up the address of that array
+ * (cudaGetSymbolAddress) with the device current; make that first call before
+ * any stream capture.  All calls on a device share the array: calls that
+ * overlap on the GPU (other streams, other threads) race and must be
+ * serialised by the caller.  Each call clears the completion counter first. */
+seg_status seg_s_eps_noalloc(const double* u, int64_t n_vert, int32_t m, const double* xyz,
+                             const int32_t* tri, int64_t n_tri, double eps, double* out,
+                             void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

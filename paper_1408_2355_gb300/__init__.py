@@ -48,7 +48,7 @@ EXPORTED = [
     "seg_problem_destroy", "seg_state_create", "seg_state_destroy", "seg_set_u", "seg_get_u",
     "seg_step", "seg_step_async", "seg_sync", "seg_substep", "seg_energy",
     "seg_eigenvalue_estimates", "seg_labels", "seg_get_stats", "seg_last_error",
-    "seg_time_kernel", "seg_launch_info",
+    "seg_time_kernel", "seg_launch_info", "seg_s_eps_noalloc",
 ]
 
 
@@ -109,6 +109,7 @@ _SIG = {
     "seg_get_stats": [_vp, _vp],
     "seg_time_kernel": [_vp, _i32, _i32, _vp],
     "seg_launch_info": [_vp, _vp, _vp, _vp, _vp],
+    "seg_s_eps_noalloc": [_vp, _i64, _i32, _vp, _vp, _i64, _d, _vp, _vp],
 }
 for _name, _args in _SIG.items():
     _f = getattr(lib, _name)
@@ -336,3 +337,15 @@ def seg_launch_info(state: State) -> dict:
     g, b, l, p = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
     _check(lib.seg_launch_info(state.ptr, C.byref(g), C.byref(b), C.byref(l), C.byref(p)))
     return {"grid_blocks": g.value, "block_threads": b.value, "lanes_per_row": l.value, "padded_m": p.value}
+
+
+def seg_s_eps_noalloc(u, xyz, tri, eps: float, out, cuda_stream: int | None = None):
+    """Allocation-free S_eps and coupling integrals (see include/seg.h).
+
+    u (n_vert x m float64), xyz (n_vert x 3 float64), tri (n_tri x 3 int32)
+    and out (m + 1 float64) are caller-owned CUDA tensors on the current
+    device; the call only enqueues work on cuda_stream and returns.
+    """
+    n_vert, m = int(u.shape[0]), int(u.shape[1])
+    _check(lib.seg_s_eps_noalloc(_ptr(u), n_vert, m, _ptr(xyz), _ptr(tri), int(tri.shape[0]), eps, _ptr(out),
+                                 C.c_void_p(cuda_stream) if cuda_stream else None))

@@ -36,6 +36,8 @@ seg_status fail(seg_status code, const std::string& msg) {
 
 }  // namespace
 
+void segimpl::set_last_error(const char* msg) { g_err = msg; }
+
 struct seg_mesh {
   HostMesh h;
 };

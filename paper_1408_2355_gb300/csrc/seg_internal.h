@@ -109,6 +109,9 @@ struct KernelSet {
 bool get_kernels_f32(int lpr, KernelSet* ks);
 bool get_kernels_f64(int lpr, KernelSet* ks);
 
+// Record the message returned by seg_last_error() on this thread.
+void set_last_error(const char* msg);
+
 // Host-side mesh and assembly (mesh.cpp / assemble.cpp).
 struct HostMesh {
   std::vector<double> xyz;  // [n][3]
