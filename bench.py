@@ -31,14 +31,19 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 HBM_FALLBACK_GBS = 6800.0
+# DRAM bytes (read + write) per k_cg_a launch from the ncu capture summarised
+# in profiles/; None until a capture of the current kernel exists.
+TRAFFIC_CG_A = None
 METRIC = "DoF-steps/s (N*m*steps) sphere 655k m=16 FP32-mix vs FP64; p50/p99 latency"
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--launch-mode", default="graph", choices=["graph", "direct"],
+                    help="direct: kernels launched one by one (for profilers that cannot see graph kernels)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--level", type=int, default=8)
     ap.add_argument("--m", type=int, default=16)
@@ -201,16 +206,27 @@ def measured_peak():
         return HBM_FALLBACK_GBS, "fallback"
 
 
-def cg_pass_a_bytes(n, nnz, m_pad, s):
-    """Algorithmic bytes of one CG pass A launch (k_cg_a).
+def kernel_bytes(n, ntri, m_pad, s, W=8):
+    """Algorithmic bytes per launch of each hot-path kernel.
 
-    Per vertex row: read r and p_old (also gathered by the neighbours, each
-    unique row once), read and write x, write p_new and q: 6 vectors of
-    N * m_pad * s bytes; plus the CSR of A (row pointers, int32 columns,
-    values) and the Jacobi diagonal.
+    V = N * m_pad * s is one state-sized vector.  Gathered neighbour rows
+    count once (each unique row is needed once); the padded-ELL matrix rows
+    are W int32 columns plus W values per vertex, the Jacobi diagonal N * s.
+      k_start  read X, write R, columns + K + M values, diagonal
+      k_cg_a   read R, p_old, X; write X, p_new, q; columns + A values, diagonal
+      k_cg_b   read R, q; write R; diagonal
+      k_finish read X, p; write X
+      k_energy read X, triangle corners (3 int32) and areas
     """
     V = n * m_pad * s
-    return 6 * V + 4 * (n + 1) + nnz * (4 + s) + n * s
+    ell = n * W * 4
+    return {
+        "k_start": 2 * V + ell + 2 * n * W * s + n * s,
+        "k_cg_a": 6 * V + ell + n * W * s + n * s,
+        "k_cg_b": 3 * V + n * s,
+        "k_finish": 3 * V,
+        "k_energy": V + ntri * (12 + s),
+    }
 
 
 def run_ours(a, rank, ws, local):
@@ -232,6 +248,7 @@ def run_ours(a, rank, ws, local):
         prm = seg.seg_params()
         prm.check_every = 1      # energy + stop-rule pass in every step
         prm.energy_tol = -1.0    # ... but never stop: time exactly K steps
+        prm.launch_mode = 1 if a.launch_mode == "direct" else 0
         st = seg.seg_state_create(prob, a.m, a.eps, seg.SEG_INIT_UNIFORM, a.seed, prm, stream.cuda_stream)
         return prob, st
 
@@ -265,11 +282,17 @@ def run_ours(a, rank, ws, local):
     value = ws * n * a.m * a.steps / (ms / 1e3)
     e_final = seg.seg_energy(st)
 
-    # live duration of the dominant kernel (CG pass A) with CUDA events
-    t_a = seg.seg_time_kernel(st, 1, 20)
-    t_b = seg.seg_time_kernel(st, 2, 20)
-    bytes_a = cg_pass_a_bytes(n, info["nnz"], li["padded_m"], 4)
+    # live per-launch durations of the hot-path kernels with CUDA events on
+    # the state's stream (same launch geometry as inside the step graph)
     peak, peak_kind = measured_peak()
+    kb = kernel_bytes(n, int(tri.shape[0]), li["padded_m"], 4)
+    kern = {}
+    for which, name in enumerate(["k_start", "k_cg_a", "k_cg_b", "k_finish", "k_energy"]):
+        t = seg.seg_time_kernel(st, which, 20)
+        kern[name] = {"ms": t, "bytes": kb[name], "GBps": kb[name] / (t / 1e3) / 1e9,
+                      "frac": kb[name] / (t / 1e3) / 1e9 / peak}
+    t_a = kern["k_cg_a"]["ms"]
+    bytes_a = kb["k_cg_a"]
     achieved = bytes_a / (t_a / 1e3) / 1e9
 
     out = {
@@ -297,6 +320,7 @@ def run_ours(a, rank, ws, local):
             "energy_every_step": True,
             "l2": "inputs larger than L2: 5 state vectors x 42 MB + 76 MB of CSR > 129 MB L2",
             "grid_blocks": li["grid_blocks"],
+            "launch_mode": a.launch_mode,
             "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
         },
         "cg_iterations_per_step": dcg / a.steps,
@@ -311,11 +335,11 @@ def run_ours(a, rank, ws, local):
             "peak_kind": peak_kind,
             "unit": "GB/s",
             "frac": achieved / peak,
-            "traffic": None,
+            "traffic": TRAFFIC_CG_A,
             "bytes_per_launch": bytes_a,
             "launch_ms": t_a,
-            "cg_pass_b_ms": t_b,
         },
+        "kernels": kern,
     }
 
     if not a.no_e2e:

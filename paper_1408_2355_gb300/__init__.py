@@ -65,6 +65,8 @@ class seg_params(C.Structure):
         ("grid_blocks", C.c_int32),
         ("check_every", C.c_int64),
         ("energy_tol", C.c_double),
+        ("launch_mode", C.c_int32),
+        ("reserved", C.c_int32),
     ]
 
 

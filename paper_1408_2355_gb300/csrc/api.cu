@@ -47,12 +47,13 @@ struct seg_problem {
   double tau = 0, area = 0;
   seg_precision prec = SEG_FP64;
   int device = 0;
-  int* rowptr = nullptr;
-  int* col = nullptr;
+  int ell_w = 8;
+  int* ell_col = nullptr;
   void* valA = nullptr;
   void* valM = nullptr;
   void* valK = nullptr;
   void* dinv = nullptr;
+  void* diagA = nullptr;
   int* tri = nullptr;
   void* tarea = nullptr;
   int* perm = nullptr;
@@ -70,10 +71,11 @@ struct seg_state {
   double energy_tol = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  int launch_mode = 0;
   int grid = 0;
   void* X = nullptr;
-  void* R = nullptr;
-  void* P0 = nullptr;
+  void* Z = nullptr;        // preconditioned residual
+  void* P0 = nullptr;       // search directions, ping-pong
   void* P1 = nullptr;
   void* Q = nullptr;
   DevCtl* ctl = nullptr;
@@ -121,17 +123,25 @@ KArgs<T> make_args(seg_state* s, const Launch& l) {
   return a;
 }
 
+// Dynamic shared memory of a row kernel (the TMA-staged ones use some).
+unsigned smem_of(const seg_state* s, void* fn) {
+  if (fn == s->ks.start) return s->ks.smem_start;
+  if (fn == s->ks.cg_a) return s->ks.smem_cg_a;
+  return 0;
+}
+
 // Launch one row kernel (grid = s->grid) with the state's arguments.
 seg_status launch_row(seg_state* s, void* fn, const Launch& l) {
   cudaError_t e;
+  const unsigned smem = smem_of(s, fn);
   if (s->prec == SEG_MIXED_FP32) {
     KArgs<float> a = make_args<float>(s, l);
     void* args[] = {&a};
-    e = cudaLaunchKernel(fn, dim3(s->grid), dim3(kBlockThreads), args, 0, s->stream);
+    e = cudaLaunchKernel(fn, dim3(s->grid), dim3(kBlockThreads), args, smem, s->stream);
   } else {
     KArgs<double> a = make_args<double>(s, l);
     void* args[] = {&a};
-    e = cudaLaunchKernel(fn, dim3(s->grid), dim3(kBlockThreads), args, 0, s->stream);
+    e = cudaLaunchKernel(fn, dim3(s->grid), dim3(kBlockThreads), args, smem, s->stream);
   }
   if (e != cudaSuccess) return fail(SEG_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
   return SEG_OK;
@@ -173,7 +183,29 @@ seg_status ensure_norm(seg_state* s) {
   return SEG_OK;
 }
 
+// One step with the kernels of the step graph launched one by one: the CG
+// loop condition is read back by the host after every iteration.
+seg_status direct_step(seg_state* s) {
+  Launch l;
+  l.ignore_halt = 0;
+  seg_status st = launch_row(s, s->ks.start, l);
+  if (st == SEG_OK) st = launch_row(s, s->ks.energy, l);
+  if (st == SEG_OK) st = sync_ctl(s);
+  while (st == SEG_OK && s->hctl->cont && !s->hctl->halted) {
+    st = launch_row(s, s->ks.cg_a, l);
+    if (st == SEG_OK) st = launch_row(s, s->ks.cg_b, l);
+    if (st == SEG_OK) st = sync_ctl(s);
+  }
+  Launch f = l;
+  f.apply_x = 1;
+  f.apply_ode = 1;
+  f.count_step = 1;
+  if (st == SEG_OK) st = launch_row(s, s->ks.finish, f);
+  return st;
+}
+
 seg_status status_from_ctl(const DevCtl& c) {
+  if (c.status & 4) return fail(SEG_ERR_TIMEOUT, "a bounded wait for staged data timed out; the run was halted");
   if (c.status & 2) return fail(SEG_ERR_NONFINITE, "a norm, inner product or energy became non-finite (or a component vanished)");
   if (c.status & 1) return fail(SEG_ERR_NOT_CONVERGED, "a step-1 CG solve reached cg_maxit before cg_rtol");
   return SEG_OK;
@@ -181,14 +213,14 @@ seg_status status_from_ctl(const DevCtl& c) {
 
 template <typename T>
 cudaError_t add_kernel_node(cudaGraphNode_t* node, cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps,
-                            void* fn, int grid, const KArgs<T>& a) {
+                            void* fn, int grid, const KArgs<T>& a, unsigned smem) {
   KArgs<T> copy = a;
   void* args[] = {&copy};
   cudaKernelNodeParams kp{};
   kp.func = fn;
   kp.gridDim = dim3(grid);
   kp.blockDim = dim3(kBlockThreads);
-  kp.sharedMemBytes = 0;
+  kp.sharedMemBytes = smem;
   kp.kernelParams = args;
   kp.extra = nullptr;
   return cudaGraphAddKernelNode(node, g, deps, ndeps, &kp);
@@ -203,8 +235,8 @@ seg_status build_graph_t(seg_state* s) {
   l.ignore_halt = 0;
   KArgs<T> base = make_args<T>(s, l);
   cudaGraphNode_t n_start, n_energy, n_loop, n_a, n_b, n_fin;
-  SEG_CUDA(add_kernel_node<T>(&n_start, s->graph, nullptr, 0, s->ks.start, s->grid, base));
-  SEG_CUDA(add_kernel_node<T>(&n_energy, s->graph, &n_start, 1, s->ks.energy, s->grid, base));
+  SEG_CUDA(add_kernel_node<T>(&n_start, s->graph, nullptr, 0, s->ks.start, s->grid, base, s->ks.smem_start));
+  SEG_CUDA(add_kernel_node<T>(&n_energy, s->graph, &n_start, 1, s->ks.energy, s->grid, base, 0));
   cudaGraphNodeParams cp{};
   cp.type = cudaGraphNodeTypeConditional;
   cp.conditional.handle = s->cond;
@@ -212,13 +244,13 @@ seg_status build_graph_t(seg_state* s) {
   cp.conditional.size = 1;
   SEG_CUDA(cudaGraphAddNode(&n_loop, s->graph, &n_energy, nullptr, 1, &cp));
   cudaGraph_t body = cp.conditional.phGraph_out[0];
-  SEG_CUDA(add_kernel_node<T>(&n_a, body, nullptr, 0, s->ks.cg_a, s->grid, base));
-  SEG_CUDA(add_kernel_node<T>(&n_b, body, &n_a, 1, s->ks.cg_b, s->grid, base));
+  SEG_CUDA(add_kernel_node<T>(&n_a, body, nullptr, 0, s->ks.cg_a, s->grid, base, s->ks.smem_cg_a));
+  SEG_CUDA(add_kernel_node<T>(&n_b, body, &n_a, 1, s->ks.cg_b, s->grid, base, 0));
   KArgs<T> fin = base;
   fin.apply_x = 1;
   fin.apply_ode = 1;
   fin.count_step = 1;
-  SEG_CUDA(add_kernel_node<T>(&n_fin, s->graph, &n_loop, 1, s->ks.finish, s->grid, fin));
+  SEG_CUDA(add_kernel_node<T>(&n_fin, s->graph, &n_loop, 1, s->ks.finish, s->grid, fin, 0));
   SEG_CUDA(cudaGraphInstantiate(&s->exec, s->graph, 0));
   return SEG_OK;
 }
@@ -231,15 +263,15 @@ void fill_args(seg_state* s) {
   a.n = (int)p->n;
   a.m = s->m;
   a.ms = s->ms;
-  a.rows_per_block = (int)((p->n + s->grid - 1) / s->grid);
-  a.rowptr = p->rowptr;
-  a.col = p->col;
+  a.ell_w = p->ell_w;
+  a.ell_col = p->ell_col;
   a.valA = (const T*)p->valA;
   a.valM = (const T*)p->valM;
   a.valK = (const T*)p->valK;
   a.dinv = (const T*)p->dinv;
   a.X = (T*)s->X;
-  a.R = (T*)s->R;
+  a.diagA = (const T*)p->diagA;
+  a.Z = (T*)s->Z;
   a.P0 = (T*)s->P0;
   a.P1 = (T*)s->P1;
   a.Q = (T*)s->Q;
@@ -253,7 +285,6 @@ void fill_args(seg_state* s) {
   a.tri = p->tri;
   a.tarea = (const T*)p->tarea;
   a.ntri = (int)p->f;
-  a.tri_per_block = (int)((p->f + s->grid - 1) / s->grid);
   a.check_every = s->check_every;
   a.energy_tol = s->energy_tol;
 }
@@ -281,7 +312,7 @@ void free_state(seg_state* s) {
   if (!s) return;
   if (s->exec) cudaGraphExecDestroy(s->exec);
   if (s->graph) cudaGraphDestroy(s->graph);
-  void* bufs[] = {s->X, s->R, s->P0, s->P1, s->Q, s->ctl, s->part, s->io, s->ones, s->scale_backup, s->am, s->vp};
+  void* bufs[] = {s->X, s->Z, s->P0, s->P1, s->Q, s->ctl, s->part, s->io, s->ones, s->scale_backup, s->am, s->vp};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (s->hctl) cudaFreeHost(s->hctl);
@@ -393,17 +424,38 @@ seg_status seg_assemble(const seg_mesh* mesh, double tau, seg_precision precisio
   HostCSR csr;
   assemble_p1(mesh->h, &csr);
   const int64_t n = csr.n;
-  std::vector<double> A(csr.nnz), dinv(n);
+  std::vector<double> A(csr.nnz), dinv(n), diag(n);
   for (int64_t e = 0; e < csr.nnz; ++e) A[e] = csr.M[e] + tau * csr.K[e];
   for (int64_t i = 0; i < n; ++i) {
     double d = 0.0;
     for (int32_t e = csr.rowptr[i]; e < csr.rowptr[i + 1]; ++e)
       if (csr.col[e] == i) d = A[e];
     if (!(d > 0)) return fail(SEG_ERR_MESH, "non-positive diagonal of M + tau K");
+    diag[i] = d;
     dinv[i] = 1.0 / d;
+  }
+  // padded ELL rows: every row holds W entries (W = 8, or 16 for vertex
+  // degrees up to 15); unused entries repeat the row itself with value 0, so
+  // kernels read them without a branch (the data there is always finite)
+  int32_t max_row = 0;
+  for (int64_t i = 0; i < n; ++i) max_row = std::max(max_row, csr.rowptr[i + 1] - csr.rowptr[i]);
+  if (max_row > 16) return fail(SEG_ERR_UNSUPPORTED, "a vertex has more than 15 neighbours (padded rows hold 16)");
+  const int W = max_row <= 8 ? 8 : 16;
+  std::vector<int32_t> ecol((size_t)n * W);
+  std::vector<double> eA((size_t)n * W, 0.0), eM((size_t)n * W, 0.0), eK((size_t)n * W, 0.0);
+  for (int64_t i = 0; i < n; ++i)
+    for (int k = 0; k < W; ++k) ecol[i * W + k] = (int32_t)i;
+  for (int64_t i = 0; i < n; ++i) {
+    for (int32_t e = csr.rowptr[i], k = 0; e < csr.rowptr[i + 1]; ++e, ++k) {
+      ecol[i * W + k] = csr.col[e];
+      eA[i * W + k] = A[e];
+      eM[i * W + k] = csr.M[e];
+      eK[i * W + k] = csr.K[e];
+    }
   }
   seg_problem* p = new (std::nothrow) seg_problem;
   if (!p) return fail(SEG_ERR_NO_MEMORY, "host allocation failed");
+  p->ell_w = W;
   p->n = n;
   p->nnz = csr.nnz;
   p->f = mesh->h.f;
@@ -415,12 +467,12 @@ seg_status seg_assemble(const seg_mesh* mesh, double tau, seg_precision precisio
   cudaError_t e = cudaGetDevice(&p->device);
   seg_status st = SEG_OK;
   if (e != cudaSuccess) st = fail(SEG_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-  if (st == SEG_OK) st = upload_ints(csr.rowptr, &p->rowptr);
-  if (st == SEG_OK) st = upload_ints(csr.col, &p->col);
-  if (st == SEG_OK) st = upload_vals_prec(precision, A, &p->valA);
-  if (st == SEG_OK) st = upload_vals_prec(precision, csr.M, &p->valM);
-  if (st == SEG_OK) st = upload_vals_prec(precision, csr.K, &p->valK);
+  if (st == SEG_OK) st = upload_ints(ecol, &p->ell_col);
+  if (st == SEG_OK) st = upload_vals_prec(precision, eA, &p->valA);
+  if (st == SEG_OK) st = upload_vals_prec(precision, eM, &p->valM);
+  if (st == SEG_OK) st = upload_vals_prec(precision, eK, &p->valK);
   if (st == SEG_OK) st = upload_vals_prec(precision, dinv, &p->dinv);
+  if (st == SEG_OK) st = upload_vals_prec(precision, diag, &p->diagA);
   if (st == SEG_OK) st = upload_ints(csr.tri_rows, &p->tri);
   if (st == SEG_OK) st = upload_vals_prec(precision, csr.area, &p->tarea);
   if (st == SEG_OK) st = upload_ints(csr.perm, &p->perm);
@@ -444,7 +496,7 @@ seg_status seg_problem_info(const seg_problem* p, int64_t* n_vert, int64_t* nnz,
 
 void seg_problem_destroy(seg_problem* p) {
   if (!p) return;
-  void* bufs[] = {p->rowptr, p->col, p->valA, p->valM, p->valK, p->dinv, p->tri, p->tarea, p->perm, p->iperm};
+  void* bufs[] = {p->ell_col, p->valA, p->valM, p->valK, p->dinv, p->diagA, p->tri, p->tarea, p->perm, p->iperm};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete p;
@@ -474,6 +526,10 @@ seg_status seg_state_create(const seg_problem* p, int32_t m, double eps, seg_ini
   while (pw < lpr) pw <<= 1;
   s->lpr = pw;
   s->ms = pw * vw;
+  if ((int64_t)p->n * 2 * s->ms >= ((int64_t)1 << 31)) {
+    delete s;
+    return fail(SEG_ERR_UNSUPPORTED, "n_vert * padded m too large for 32-bit row offsets");
+  }
   seg_params prm{};
   if (opt) prm = *opt;
   s->cg_rtol = prm.cg_rtol > 0 ? prm.cg_rtol : (s->prec == SEG_MIXED_FP32 ? 1e-7 : 1e-12);
@@ -481,10 +537,28 @@ seg_status seg_state_create(const seg_problem* p, int32_t m, double eps, seg_ini
   s->check_every = prm.check_every > 0 ? prm.check_every
                                        : (prm.check_every < 0 ? 0 : std::max<long long>(1, std::llround(0.1 / p->tau)));
   s->energy_tol = prm.energy_tol > 0 ? prm.energy_tol : (prm.energy_tol < 0 ? -1.0 : 1e-6);
-  bool ok = s->prec == SEG_MIXED_FP32 ? get_kernels_f32(s->lpr, &s->ks) : get_kernels_f64(s->lpr, &s->ks);
+  if (prm.launch_mode != 0 && prm.launch_mode != 1) {
+    delete s;
+    return fail(SEG_ERR_ARG, "launch_mode must be 0 (graph) or 1 (direct)");
+  }
+  s->launch_mode = prm.launch_mode;
+  bool ok = s->prec == SEG_MIXED_FP32 ? get_kernels_f32(s->lpr, p->ell_w, &s->ks)
+                                      : get_kernels_f64(s->lpr, p->ell_w, &s->ks);
   if (!ok) {
     delete s;
     return fail(SEG_ERR_UNSUPPORTED, "no kernel specialisation for this m and precision");
+  }
+  {
+    // the TMA-staged kernels may need more than the default 48 KiB
+    const void* fns[2] = {s->ks.start, s->ks.cg_a};
+    const unsigned sm[2] = {s->ks.smem_start, s->ks.smem_cg_a};
+    for (int k = 0; k < 2; ++k) {
+      cudaError_t fe = cudaFuncSetAttribute(fns[k], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm[k]);
+      if (fe != cudaSuccess) {
+        delete s;
+        return fail(SEG_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(fe));
+      }
+    }
   }
   int nsm = 0;
   cudaError_t ce = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device);
@@ -509,7 +583,7 @@ seg_status seg_state_create(const seg_problem* p, int32_t m, double eps, seg_ini
     void** ptr;
     size_t bytes;
   } allocs[] = {{&s->X, vbytes},
-                {&s->R, vbytes},
+                {&s->Z, vbytes},
                 {&s->P0, vbytes},
                 {&s->P1, vbytes},
                 {&s->Q, vbytes},
@@ -625,7 +699,14 @@ seg_status seg_step_async(seg_state* s, int64_t nsteps) {
   SEG_CUDA(cudaMemcpyAsync(&s->ctl->step_mark, &s->ctl->step, sizeof(long long), cudaMemcpyDeviceToDevice,
                            s->stream));
   SEG_CUDA(cudaMemsetAsync(&s->ctl->status, 0, sizeof(int), s->stream));
-  for (int64_t k = 0; k < nsteps; ++k) SEG_CUDA(cudaGraphLaunch(s->exec, s->stream));
+  if (s->launch_mode == 0) {
+    for (int64_t k = 0; k < nsteps; ++k) SEG_CUDA(cudaGraphLaunch(s->exec, s->stream));
+  } else {
+    for (int64_t k = 0; k < nsteps; ++k) {
+      seg_status st = direct_step(s);
+      if (st != SEG_OK) return st;
+    }
+  }
   if (nsteps > 0) s->pending = true;
   return SEG_OK;
 }

@@ -1,27 +1,34 @@
 // Hot-path kernels of one step of Algorithm 2.2 on interleaved vertex rows.
 //
-// Data layout: every vector is X[row][ms] (vertex-major, ms = m padded to a
+// Data layout: every vector is V[row][ms] (vertex-major, ms = m padded to a
 // multiple of 16 bytes / sizeof(T)); one row is split across LPR lanes, each
 // lane owning VW = 16 / sizeof(T) consecutive components that it moves with
 // one 128-bit load or store.  A warp therefore covers 32 / LPR rows, and one
-// read of a CSR row (column index + value) serves all m components.
+// read of a padded-ELL matrix row (W column indices + W values) serves all m
+// components.
 //
 // Per step the kernels run in this order (one CUDA graph per step, the CG
 // loop is a device-controlled conditional WHILE node):
-//   k_start   r0 = -tau K X (warm start x0 = X: M X - A X = -tau K X), and the
-//             per-component sums ||X||_M^2, ||M X||^2, X^T K X, r.D^-1 r, r.r
-//             -- the normalisation of the previous step (step 3) is fused here
+//   k_start   r0 = -tau K X (warm start x0 = X: M X - A X = -tau K X),
+//             z0 = D^-1 r0, and the per-component sums ||X||_M^2, X^T K X,
+//             r0.z0, ||M X||^2, ||r0||^2 -- the renormalisation of the
+//             previous step (step 3) is fused here
 //   k_energy  (every check_every steps) S_eps and the coupling integrals
-//   k_cg_a    p = D^-1 r + beta p_old, q = A p, p.q; lagged x += alpha p_old
-//   k_cg_b    r -= alpha q, r.D^-1 r, r.r; convergence and beta
+//   k_cg_a    p = z + beta p_old, q = A p, p.q; lagged x += alpha p_old
+//   k_cg_b    z -= alpha D^-1 q, r.z and r.r (r = D z); convergence and beta
 //   k_finish  last x += alpha p, then the exact nodal ODE of step 2
+// The two gather kernels stage each warp's next group of rows (ELL indices,
+// values and own vector rows) in shared memory with TMA bulk copies while the
+// current group's neighbour rows are gathered.
 //
-// Inner products are per component.  For float data each lane accumulates
-// the exact products (Dekker split with fma) in a float-float pair, the warp,
-// block and grid reductions add float-float pairs, and the final value is a
-// float64; for double data everything is float64.  The grid reduction is done
-// by the last block to finish (ticket counter), in a fixed order, so results
-// are bitwise reproducible for a fixed launch geometry.
+// Inner products are per component.  For float data the ones that feed CG's
+// alpha / beta, the norms and the energies accumulate the exact products
+// (Dekker split with fma) in float-float pairs per lane, the warp, block and
+// grid reductions add float-float pairs, and the final value is a float64;
+// sums that only set the CG tolerance accumulate in float per lane.  For
+// double data everything is float64.  The grid reduction is done by the last
+// block to finish (ticket counter), in a fixed order, so results are bitwise
+// reproducible for a fixed launch geometry.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -231,6 +238,7 @@ __device__ __forceinline__ void row_exclusive(const T (&x)[NQ][VecW<T>::W], T (&
 
 // ---------------------------------------------------------------- kernels
 
+// Rows of a block: a contiguous range [r0, r1) of ceil(n / gridDim.x) rows.
 #define SEG_ROW_SETUP                                                         \
   constexpr int VW = VecW<T>::W;                                              \
   constexpr int NW = kBlockThreads / 32;                                      \
@@ -238,80 +246,310 @@ __device__ __forceinline__ void row_exclusive(const T (&x)[NQ][VecW<T>::W], T (&
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;                 \
   const int rs = lane / LPR, cg = lane % LPR, c0 = cg * VW;                   \
   (void)rs;                                                                   \
-  const int r0 = blockIdx.x * a.rows_per_block;                               \
-  const int r1 = min(a.n, r0 + a.rows_per_block);
+  const int rpb = (a.n + (int)gridDim.x - 1) / (int)gridDim.x;                \
+  const int r0 = blockIdx.x * rpb;                                            \
+  const int r1 = min(a.n, r0 + rpb);
 
-template <typename T, int LPR>
+// Padded-ELL row of W entries: column indices (-1 = padding) and values.
+template <int W>
+__device__ __forceinline__ void ld_cols(int (&c)[W], const int* p) {
+#pragma unroll
+  for (int k = 0; k < W; k += 4) {
+    const int4 v = __ldg(reinterpret_cast<const int4*>(p + k));
+    c[k] = v.x; c[k + 1] = v.y; c[k + 2] = v.z; c[k + 3] = v.w;
+  }
+}
+template <int W>
+__device__ __forceinline__ void ld_vals(float (&c)[W], const float* p) {
+#pragma unroll
+  for (int k = 0; k < W; k += 4) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p + k));
+    c[k] = v.x; c[k + 1] = v.y; c[k + 2] = v.z; c[k + 3] = v.w;
+  }
+}
+template <int W>
+__device__ __forceinline__ void ld_vals(double (&c)[W], const double* p) {
+#pragma unroll
+  for (int k = 0; k < W; k += 2) {
+    const double2 v = __ldg(reinterpret_cast<const double2*>(p + k));
+    c[k] = v.x; c[k + 1] = v.y;
+  }
+}
+
+// ------------------------------------------------ TMA bulk-copy pipeline
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+// 1-D bulk copy global -> shared (TMA); both addresses 16-byte aligned and
+// bytes a multiple of 16; completion is signalled on `bar`.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+// Order this thread's earlier generic-proxy shared-memory accesses before
+// later async-proxy (TMA) writes to the same buffer.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// Bounded wait for the phase `parity` of `bar`: false after kWaitPolls tries.
+constexpr unsigned kWaitPolls = 1u << 24;
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+  for (unsigned n = 0; n < kWaitPolls; ++n) {
+    unsigned ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+// Sources of one staged row group (all pointers to row 0 of their array).
+template <typename T, int NVAL, int NVEC>
+struct StageSrc {
+  const int* ell;
+  const T* val[NVAL];
+  const T* vec[NVEC];  // rows of ms values
+};
+
+// Per-warp staging of one group of RPW consecutive rows: the padded-ELL
+// indices and NVAL value arrays of the group and the rows of NVEC vectors.
+// Every piece is a contiguous slice of global memory, copied by one bulk copy.
+template <typename T, int LPR, int W, int NVAL, int NVEC>
+struct RowStage {
+  typedef T value_t;
+  typedef StageSrc<T, NVAL, NVEC> Src;
+  static constexpr int RPW = 32 / LPR;
+  static constexpr int MS = LPR * VecW<T>::W;  // padded components
+  static constexpr unsigned kColBytes = RPW * W * 4;
+  static constexpr unsigned kValBytes = RPW * W * sizeof(T);
+  static constexpr unsigned kVecBytes = RPW * MS * sizeof(T);  // = 512
+  static constexpr unsigned kBytes = kColBytes + NVAL * kValBytes + NVEC * kVecBytes;
+  static_assert(kColBytes % 16 == 0 && kValBytes % 16 == 0 && kVecBytes % 16 == 0, "16-byte pieces");
+
+  unsigned char* base;
+  __device__ __forceinline__ const int* cols() const { return reinterpret_cast<const int*>(base); }
+  __device__ __forceinline__ const T* vals(int k) const {
+    return reinterpret_cast<const T*>(base + kColBytes + k * kValBytes);
+  }
+  __device__ __forceinline__ const T* vec(int k) const {
+    return reinterpret_cast<const T*>(base + kColBytes + NVAL * kValBytes + k * kVecBytes);
+  }
+  // lane 0 only: copy rows [row0, row0 + nr) of the sources into this stage
+  __device__ __forceinline__ void issue(unsigned long long* bar, int row0, int nr, const Src& src) const {
+    const unsigned ncb = nr * W * 4, nvb = nr * W * sizeof(T), nrb = nr * MS * sizeof(T);
+    mbar_expect_tx(bar, ncb + NVAL * nvb + NVEC * nrb);
+    bulk_g2s(base, src.ell + (size_t)row0 * W, ncb, bar);
+#pragma unroll
+    for (int k = 0; k < NVAL; ++k)
+      bulk_g2s(base + kColBytes + k * kValBytes, src.val[k] + (size_t)row0 * W, nvb, bar);
+#pragma unroll
+    for (int k = 0; k < NVEC; ++k)
+      bulk_g2s(base + kColBytes + NVAL * kValBytes + k * kVecBytes, src.vec[k] + (size_t)row0 * MS, nrb, bar);
+  }
+};
+
+template <typename Stage>
+constexpr unsigned row_stage_smem() {
+  return (kBlockThreads / 32) * 2 * Stage::kBytes;
+}
+
+// Reads VW values of this lane from a staged row (shared memory).
+__device__ __forceinline__ void lds(float (&d)[4], const float* p) {
+  const float4 x = *reinterpret_cast<const float4*>(p);
+  d[0] = x.x; d[1] = x.y; d[2] = x.z; d[3] = x.w;
+}
+__device__ __forceinline__ void lds(double (&d)[2], const double* p) {
+  const double2 x = *reinterpret_cast<const double2*>(p);
+  d[0] = x.x; d[1] = x.y;
+}
+
+// Mark a timed-out wait: the block records the error and halts the run.
+__device__ __forceinline__ void report_timeout(DevCtl* ctl) {
+  atomicOr(&ctl->status, 4);
+  atomicExch(&ctl->halted, 2);
+}
+
+// Warp-level pipeline over the row groups of the block: group gi covers
+// rows [r0 + gi*RPW, ...); warp w takes groups w, w+NW, ...  While the rows
+// of one group are processed, the bulk copies of the warp's next group are
+// in flight.  `body(stage, row0, nr)` consumes a landed stage.  Returns false
+// if a wait timed out (the copies still in flight are waited for, bounded).
+template <typename Stage, typename Body>
+__device__ __forceinline__ bool row_pipeline(unsigned char* smem_warp, unsigned long long* bars, int r0, int r1,
+                                             const typename Stage::Src& src, Body body) {
+  constexpr int NW = kBlockThreads / 32;
+  constexpr int RPW = Stage::RPW;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  Stage st[2];
+  st[0].base = smem_warp;
+  st[1].base = smem_warp + Stage::kBytes;
+  const int ngroups = (r1 - r0 + RPW - 1) / RPW;
+  if (lane == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    mbar_init_fence();
+  }
+  __syncwarp();
+  int gi = warp;
+  if (gi < ngroups && lane == 0) {
+    const int row0 = r0 + gi * RPW;
+    st[0].issue(&bars[0], row0, min(RPW, r1 - row0), src);
+  }
+  bool ok = true;
+  int pending = gi < ngroups ? 1 : 0;  // stages with copies in flight (bit mask)
+  unsigned used[2] = {0u, 0u};         // completed phases consumed per stage
+  for (int k = 0; gi < ngroups; gi += NW, ++k) {
+    const int s = k & 1;
+    const int gn = gi + NW;
+    if (gn < ngroups) {
+      if (lane == 0) {
+        fence_proxy_async_smem();
+        const int row0 = r0 + gn * RPW;
+        st[s ^ 1].issue(&bars[s ^ 1], row0, min(RPW, r1 - row0), src);
+      }
+      pending |= 1 << (s ^ 1);
+    }
+    const bool landed = mbar_wait(&bars[s], used[s] & 1u);
+    if (!__all_sync(0xffffffffu, landed)) {
+      ok = false;
+      break;
+    }
+    pending &= ~(1 << s);
+    ++used[s];
+    const int row0 = r0 + gi * RPW;
+    body(st[s], row0, min(RPW, r1 - row0));
+    __syncwarp();
+  }
+  if (!ok) {
+    // drain: wait (bounded) for every stage that still has copies in flight
+    for (int s = 0; s < 2; ++s)
+      if (pending & (1 << s)) mbar_wait(&bars[s], used[s] & 1u);
+  }
+  return ok;
+}
+
+template <typename T, int LPR, int W>
+using StartStage = RowStage<T, LPR, W, 2, 1>;
+template <typename T, int LPR, int W>
+using CgAStage = RowStage<T, LPR, W, 1, 3>;
+
+// Start pass (warm start x0 = X of the CG solve of step 1, and the fused
+// renormalisation of the previous step):
+//   r0 = M X - (M + tau K) X = -tau K X,  z0 = D^-1 r0  -> Z,
+// per component  ||X||_M^2, X^T K X, r0.z0  (float-float) and
+// ||M X||_2^2, ||r0||_2^2 (float32 per thread; they only set the tolerance).
+template <typename T, int LPR, int W>
 __global__ void __launch_bounds__(kBlockThreads, 2) k_start(const KArgs<T> a) {
   typedef typename AccOf<T>::type Acc;
+  typedef StartStage<T, LPR, W> Stage;
   DevCtl* ctl = a.ctl;
   if (ctl->halted && !a.ignore_halt) return;
   SEG_ROW_SETUP
+  extern __shared__ __align__(128) unsigned char dyn_smem[];
+  __shared__ __align__(8) unsigned long long bars[NW][2];
   const T tau = (T)a.tau;
+  const unsigned ms = a.ms;
   Acc acc[5][VW];
 #pragma unroll
   for (int d = 0; d < 5; ++d)
 #pragma unroll
     for (int v = 0; v < VW; ++v) acc[d][v].zero();
-  for (int base = r0 + warp * RPW; base < r1; base += NW * RPW) {
-    const int row = base + rs;
-    if (row < r1) {
-      T x[VW], kx[VW], mx[VW];
-      ld(x, a.X + (size_t)row * a.ms + c0);
+  T bb[VW], rr[VW];
 #pragma unroll
-      for (int v = 0; v < VW; ++v) kx[v] = mx[v] = T(0);
-      const int e0 = __ldg(a.rowptr + row), e1 = __ldg(a.rowptr + row + 1);
-#pragma unroll 4
-      for (int e = e0; e < e1; ++e) {
-        const int j = __ldg(a.col + e);
-        const T kv = __ldg(a.valK + e), mv = __ldg(a.valM + e);
-        T xj[VW];
-        ld(xj, a.X + (size_t)j * a.ms + c0);
+  for (int v = 0; v < VW; ++v) bb[v] = rr[v] = T(0);
+  typename Stage::Src src;
+  src.ell = a.ell_col;
+  src.val[0] = a.valK;
+  src.val[1] = a.valM;
+  src.vec[0] = a.X;
+  const bool ok = row_pipeline<Stage>(
+      dyn_smem + warp * 2 * Stage::kBytes, bars[warp], r0, r1, src, [&](const Stage& sg, int row0, int nr) {
+        if (rs >= nr) return;
+        const unsigned row = row0 + rs;
+        const int* cols = sg.cols() + rs * W;
+        const T* kv = sg.vals(0) + rs * W;
+        const T* mv = sg.vals(1) + rs * W;
+        T x[VW];
+        lds(x, sg.vec(0) + rs * ms + c0);
+        const T di = __ldg(a.dinv + row);
+        T xj[W][VW];  // padding entries point at the row itself with value 0
+#pragma unroll
+        for (int k = 0; k < W; ++k) ld_ro(xj[k], a.X + ((unsigned)cols[k] * ms + c0));
+        T kx[VW], mx[VW];
+#pragma unroll
+        for (int v = 0; v < VW; ++v) kx[v] = mx[v] = T(0);
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+          const T kk = kv[k], mm = mv[k];
+#pragma unroll
+          for (int v = 0; v < VW; ++v) {
+            kx[v] = fma(kk, xj[k][v], kx[v]);
+            mx[v] = fma(mm, xj[k][v], mx[v]);
+          }
+        }
+        T r[VW], z[VW];
 #pragma unroll
         for (int v = 0; v < VW; ++v) {
-          kx[v] = fma(kv, xj[v], kx[v]);
-          mx[v] = fma(mv, xj[v], mx[v]);
+          r[v] = -tau * kx[v];
+          z[v] = di * r[v];
         }
-      }
-      const T di = __ldg(a.dinv + row);
-      T r[VW];
+        st(a.Z + (row * ms + c0), z);
 #pragma unroll
-      for (int v = 0; v < VW; ++v) r[v] = -tau * kx[v];
-      st(a.R + (size_t)row * a.ms + c0, r);
+        for (int v = 0; v < VW; ++v) {
+          acc[0][v].add_prod(x[v], mx[v]);
+          acc[2][v].add_prod(x[v], kx[v]);
+          acc[3][v].add_prod(r[v], z[v]);
+          bb[v] = fma(mx[v], mx[v], bb[v]);
+          rr[v] = fma(r[v], r[v], rr[v]);
+        }
+      });
+  if (__syncthreads_or(!ok) && threadIdx.x == 0) report_timeout(ctl);
 #pragma unroll
-      for (int v = 0; v < VW; ++v) {
-        acc[0][v].add_prod(x[v], mx[v]);
-        acc[1][v].add_prod(mx[v], mx[v]);
-        acc[2][v].add_prod(x[v], kx[v]);
-        acc[3][v].add_prod(r[v], di * r[v]);
-        acc[4][v].add_prod(r[v], r[v]);
-      }
-    }
+  for (int v = 0; v < VW; ++v) {
+    acc[1][v].add_val(bb[v]);
+    acc[4][v].add_val(rr[v]);
   }
   __shared__ double tot[5][kMaxCols];
   if (!grid_reduce<T, LPR, 5>(acc, a, kCtrStart, tot)) return;
   int act = 0, bad = 0;
   const int c = threadIdx.x;
   if (c < a.ms) {
-    const double n2 = tot[0][c], bb = tot[1][c], ukt = tot[2][c], rz = tot[3][c], rr = tot[4][c];
+    const double n2 = tot[0][c], bbt = tot[1][c], ukt = tot[2][c], rz = tot[3][c], rrt = tot[4][c];
     const bool real = c < a.m;
-    if (real && !(n2 > 0.0 && isfinite(n2) && isfinite(rr) && isfinite(ukt))) bad = 1;
+    if (real && !(n2 > 0.0 && isfinite(n2) && isfinite(rrt) && isfinite(ukt))) bad = 1;
     ctl->n2[c] = n2;
     ctl->inv_n[c] = (real && n2 > 0.0) ? 1.0 / sqrt(n2) : 0.0;
     ctl->lam[c] = (real && n2 > 0.0) ? ukt / n2 : 0.0;
-    ctl->tol2[c] = a.rtol2 * bb;
+    ctl->tol2[c] = a.rtol2 * bbt;
     ctl->rz[c] = rz;
     ctl->alpha[0][c] = 0.0;
     ctl->alpha[1][c] = 0.0;
     ctl->beta[c] = 0.0;
-    act = (real && !bad && rr > a.rtol2 * bb) ? 1 : 0;
+    act = (real && !bad && rrt > a.rtol2 * bbt) ? 1 : 0;
     ctl->active[c] = act;
   }
   const int any = __syncthreads_or(act);
   const int anybad = __syncthreads_or(bad);
   if (threadIdx.x == 0) {
     ctl->it = 0;
-    int cont = (any && !anybad) ? 1 : 0;
+    int cont = (any && !anybad && ctl->halted != 2) ? 1 : 0;
     if (anybad) {
       ctl->status |= 2;
       ctl->halted = 2;
@@ -321,19 +559,117 @@ __global__ void __launch_bounds__(kBlockThreads, 2) k_start(const KArgs<T> a) {
   }
 }
 
-// S_eps and the per-component coupling integrals c_i = int u_i^2 e_i with
-// e_i = sum_{j != i} u_j^2, integrated exactly on every flat triangle.  With
-// a = (u_i at the 3 corners) and B = sum_{j != i} a_j a_j^T, the moments of
-// the barycentric coordinates give
+// CG pass A of iteration j (it = j - 1 iterations done):
+//   p_j = z_{j-1} + beta p_{j-1}   (own row, and on the fly for every neighbour)
+//   q_j = A p_j,  p_j . q_j  (float-float);
+//   lagged  x += alpha_{j-1} p_{j-1}  (own row).
+// Padded ELL entries point at the row itself with value 0 (no branches).
+template <typename T, int LPR, int W>
+__global__ void __launch_bounds__(kBlockThreads, 2) k_cg_a(const KArgs<T> a) {
+  typedef typename AccOf<T>::type Acc;
+  typedef CgAStage<T, LPR, W> Stage;
+  DevCtl* ctl = a.ctl;
+  if (ctl->halted && !a.ignore_halt) return;
+  SEG_ROW_SETUP
+  extern __shared__ __align__(128) unsigned char dyn_smem[];
+  __shared__ __align__(8) unsigned long long bars[NW][2];
+  const int it = ctl->it;
+  const T* Pold = (it & 1) ? a.P1 : a.P0;
+  T* Pnew = (it & 1) ? a.P0 : a.P1;
+  const unsigned ms = a.ms;
+  T beta[VW], alx[VW];
+#pragma unroll
+  for (int v = 0; v < VW; ++v) {
+    beta[v] = (T)ctl->beta[c0 + v];
+    alx[v] = (T)ctl->alpha[it & 1][c0 + v];
+  }
+  Acc acc[1][VW];
+#pragma unroll
+  for (int v = 0; v < VW; ++v) acc[0][v].zero();
+  typename Stage::Src src;
+  src.ell = a.ell_col;
+  src.val[0] = a.valA;
+  src.vec[0] = a.Z;
+  src.vec[1] = Pold;
+  src.vec[2] = a.X;
+  const bool ok = row_pipeline<Stage>(
+      dyn_smem + warp * 2 * Stage::kBytes, bars[warp], r0, r1, src, [&](const Stage& sg, int row0, int nr) {
+        if (rs >= nr) return;
+        const unsigned row = row0 + rs;
+        const int* cols = sg.cols() + rs * W;
+        const T* av = sg.vals(0) + rs * W;
+        // all neighbour rows of z and p_old in flight at once
+        T zj[W][VW], pj[W][VW];
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+          const unsigned oj = (unsigned)cols[k] * ms + c0;
+          ld_ro(zj[k], a.Z + oj);
+          ld_ro(pj[k], Pold + oj);
+        }
+        T zi[VW], po[VW], x[VW];
+        lds(zi, sg.vec(0) + rs * ms + c0);
+        lds(po, sg.vec(1) + rs * ms + c0);
+        lds(x, sg.vec(2) + rs * ms + c0);
+        T pn[VW], q[VW];
+#pragma unroll
+        for (int v = 0; v < VW; ++v) {
+          pn[v] = fma(beta[v], po[v], zi[v]);
+          x[v] = fma(alx[v], po[v], x[v]);
+          q[v] = T(0);
+        }
+        st(a.X + (row * ms + c0), x);
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+          const T ak = av[k];
+#pragma unroll
+          for (int v = 0; v < VW; ++v) q[v] = fma(ak, fma(beta[v], pj[k][v], zj[k][v]), q[v]);
+        }
+        st(Pnew + (row * ms + c0), pn);
+        st(a.Q + (row * ms + c0), q);
+#pragma unroll
+        for (int v = 0; v < VW; ++v) acc[0][v].add_prod(pn[v], q[v]);
+      });
+  if (__syncthreads_or(!ok) && threadIdx.x == 0) report_timeout(ctl);
+  __shared__ double tot[1][kMaxCols];
+  if (!grid_reduce<T, LPR, 1>(acc, a, kCtrCgA, tot)) return;
+  const int c = threadIdx.x;
+  if (c < a.ms) {
+    const double pq = tot[0][c];
+    ctl->alpha[(it + 1) & 1][c] = (ctl->active[c] && pq > 0.0) ? ctl->rz[c] / pq : 0.0;
+  }
+}
+
+// Per-component coupling integral on one flat triangle: with a = (u_i at the
+// 3 corners) and B = sum_{j != i} a_j a_j^T the barycentric moments give
 //   int_T (a.lam)^2 (lam^T B lam) = |T|/360 [ (s^2 + |a|^2)(1^T B 1 + tr B)
 //        + 4 s a^T B 1 + 2 a^T B a + 4 (a o a)^T B 1 + 4 s a^T diag(B)
 //        + 6 (a o a)^T diag(B) ],   s = a_0 + a_1 + a_2.
+template <typename T>
+__device__ __forceinline__ T tri_coupling(T a0, T a1, T a2, T e00, T e11, T e22, T e01, T e02, T e12) {
+  const T s = a0 + a1 + a2;
+  const T q0 = a0 * a0, q1 = a1 * a1, q2 = a2 * a2;
+  const T aa = q0 + q1 + q2;
+  const T b1x = e00 + e01 + e02, b1y = e01 + e11 + e12, b1z = e02 + e12 + e22;
+  const T SB = b1x + b1y + b1z, trB = e00 + e11 + e22;
+  const T aB1 = a0 * b1x + a1 * b1y + a2 * b1z;
+  const T aBa = q0 * e00 + q1 * e11 + q2 * e22 + T(2) * (a0 * a1 * e01 + a0 * a2 * e02 + a1 * a2 * e12);
+  const T a2B1 = q0 * b1x + q1 * b1y + q2 * b1z;
+  const T dBa = a0 * e00 + a1 * e11 + a2 * e22;
+  const T a2dB = q0 * e00 + q1 * e11 + q2 * e22;
+  return (s * s + aa) * (SB + trB) + T(4) * s * aB1 + T(2) * aBa + T(4) * a2B1 + T(4) * s * dBa + T(6) * a2dB;
+}
+
+// S_eps and the per-component coupling integrals c_i = int u_i^2 e_i with
+// e_i = sum_{j != i} u_j^2, integrated exactly on every flat triangle.  Each
+// lane group handles TU triangles per iteration (their corner rows are
+// loaded together).
 template <typename T, int LPR>
 __global__ void __launch_bounds__(kBlockThreads, 2) k_energy(const KArgs<T> a) {
   typedef typename AccOf<T>::type Acc;
   constexpr int VW = VecW<T>::W;
   constexpr int NW = kBlockThreads / 32;
   constexpr int RPW = 32 / LPR;
+  constexpr int TU = 2;
   DevCtl* ctl = a.ctl;
   if (ctl->halted && !a.ignore_halt) return;
   if (!a.force) {
@@ -342,8 +678,9 @@ __global__ void __launch_bounds__(kBlockThreads, 2) k_energy(const KArgs<T> a) {
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int rs = lane / LPR, cg = lane % LPR, c0 = cg * VW, lbase = lane - cg;
-  const int t0 = blockIdx.x * a.tri_per_block;
-  const int t1 = min(a.ntri, t0 + a.tri_per_block);
+  const int tpb = (a.ntri + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int t0 = blockIdx.x * tpb;
+  const int t1 = min(a.ntri, t0 + tpb);
   T invn[VW];
 #pragma unroll
   for (int v = 0; v < VW; ++v) invn[v] = (T)ctl->inv_n[c0 + v];
@@ -351,55 +688,49 @@ __global__ void __launch_bounds__(kBlockThreads, 2) k_energy(const KArgs<T> a) {
 #pragma unroll
   for (int v = 0; v < VW; ++v) acc[0][v].zero();
   const T inv360 = T(1) / T(360);
-  for (int base = t0 + warp * RPW; base < t1; base += NW * RPW) {
-    const int t = base + rs;
-    const bool valid = t < t1;
-    T u[3][VW];
-    T area = T(0);
-    if (valid) {
+  for (int base = t0 + warp * RPW * TU; base < t1; base += NW * RPW * TU) {
+    T u[TU][3][VW];
+    T area[TU];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const int row = __ldg(a.tri + 3 * t + k);
-        ld(u[k], a.X + (size_t)row * a.ms + c0);
-#pragma unroll
-        for (int v = 0; v < VW; ++v) u[k][v] *= invn[v];
-      }
-      area = __ldg(a.tarea + t);
-    } else {
+    for (int q = 0; q < TU; ++q) {
+      const int t = base + q * RPW + rs;
+      area[q] = T(0);
 #pragma unroll
       for (int k = 0; k < 3; ++k)
 #pragma unroll
-        for (int v = 0; v < VW; ++v) u[k][v] = T(0);
+        for (int v = 0; v < VW; ++v) u[q][k][v] = T(0);
+      if (t < t1) {
+        const int* tr = a.tri + 3 * (size_t)t;
+        const int z0 = __ldg(tr), z1 = __ldg(tr + 1), z2 = __ldg(tr + 2);
+        ld_ro(u[q][0], a.X + (size_t)z0 * a.ms + c0);
+        ld_ro(u[q][1], a.X + (size_t)z1 * a.ms + c0);
+        ld_ro(u[q][2], a.X + (size_t)z2 * a.ms + c0);
+        area[q] = __ldg(a.tarea + t);
+      }
     }
-    // P = a a^T per component: 00, 11, 22, 01, 02, 12
-    T P[6][VW], E[6][VW];
 #pragma unroll
-    for (int v = 0; v < VW; ++v) {
-      P[0][v] = u[0][v] * u[0][v];
-      P[1][v] = u[1][v] * u[1][v];
-      P[2][v] = u[2][v] * u[2][v];
-      P[3][v] = u[0][v] * u[1][v];
-      P[4][v] = u[0][v] * u[2][v];
-      P[5][v] = u[1][v] * u[2][v];
-    }
-    row_exclusive<T, LPR, 6>(P, E, lbase, cg);
+    for (int q = 0; q < TU; ++q) {
+      T P[6][VW], E[6][VW];
 #pragma unroll
-    for (int v = 0; v < VW; ++v) {
-      const T a0 = u[0][v], a1 = u[1][v], a2 = u[2][v];
-      const T e00 = E[0][v], e11 = E[1][v], e22 = E[2][v], e01 = E[3][v], e02 = E[4][v], e12 = E[5][v];
-      const T s = a0 + a1 + a2;
-      const T q0 = a0 * a0, q1 = a1 * a1, q2 = a2 * a2;
-      const T aa = q0 + q1 + q2;
-      const T b1x = e00 + e01 + e02, b1y = e01 + e11 + e12, b1z = e02 + e12 + e22;
-      const T SB = b1x + b1y + b1z, trB = e00 + e11 + e22;
-      const T aB1 = a0 * b1x + a1 * b1y + a2 * b1z;
-      const T aBa = q0 * e00 + q1 * e11 + q2 * e22 + T(2) * (a0 * a1 * e01 + a0 * a2 * e02 + a1 * a2 * e12);
-      const T a2B1 = q0 * b1x + q1 * b1y + q2 * b1z;
-      const T dBa = a0 * e00 + a1 * e11 + a2 * e22;
-      const T a2dB = q0 * e00 + q1 * e11 + q2 * e22;
-      const T F = (s * s + aa) * (SB + trB) + T(4) * s * aB1 + T(2) * aBa + T(4) * a2B1 + T(4) * s * dBa +
-                  T(6) * a2dB;
-      acc[0][v].add_val(area * inv360 * F);
+      for (int v = 0; v < VW; ++v) {
+        const T b0 = u[q][0][v] * invn[v], b1 = u[q][1][v] * invn[v], b2 = u[q][2][v] * invn[v];
+        u[q][0][v] = b0;
+        u[q][1][v] = b1;
+        u[q][2][v] = b2;
+        P[0][v] = b0 * b0;
+        P[1][v] = b1 * b1;
+        P[2][v] = b2 * b2;
+        P[3][v] = b0 * b1;
+        P[4][v] = b0 * b2;
+        P[5][v] = b1 * b2;
+      }
+      row_exclusive<T, LPR, 6>(P, E, lbase, cg);
+#pragma unroll
+      for (int v = 0; v < VW; ++v) {
+        const T F = tri_coupling<T>(u[q][0][v], u[q][1][v], u[q][2][v], E[0][v], E[1][v], E[2][v], E[3][v],
+                                    E[4][v], E[5][v]);
+        acc[0][v].add_val(area[q] * inv360 * F);
+      }
     }
   }
   __shared__ double tot[1][kMaxCols];
@@ -440,75 +771,26 @@ __global__ void __launch_bounds__(kBlockThreads, 2) k_energy(const KArgs<T> a) {
   }
 }
 
-template <typename T, int LPR>
-__global__ void __launch_bounds__(kBlockThreads, 2) k_cg_a(const KArgs<T> a) {
-  typedef typename AccOf<T>::type Acc;
-  DevCtl* ctl = a.ctl;
-  if (ctl->halted && !a.ignore_halt) return;
-  SEG_ROW_SETUP
-  const int it = ctl->it;
-  const T* Pold = (it & 1) ? a.P1 : a.P0;
-  T* Pnew = (it & 1) ? a.P0 : a.P1;
-  T beta[VW], alx[VW];
-#pragma unroll
-  for (int v = 0; v < VW; ++v) {
-    beta[v] = (T)ctl->beta[c0 + v];
-    alx[v] = (T)ctl->alpha[it & 1][c0 + v];
-  }
-  Acc acc[1][VW];
-#pragma unroll
-  for (int v = 0; v < VW; ++v) acc[0][v].zero();
-  for (int base = r0 + warp * RPW; base < r1; base += NW * RPW) {
-    const int row = base + rs;
-    if (row < r1) {
-      const size_t off = (size_t)row * a.ms + c0;
-      T ri[VW], po[VW], x[VW], pn[VW], q[VW];
-      ld_ro(ri, a.R + off);
-      ld_ro(po, Pold + off);
-      ld(x, a.X + off);
-      const T di = __ldg(a.dinv + row);
-#pragma unroll
-      for (int v = 0; v < VW; ++v) {
-        pn[v] = fma(beta[v], po[v], di * ri[v]);
-        x[v] = fma(alx[v], po[v], x[v]);
-        q[v] = T(0);
-      }
-      st(a.X + off, x);
-      const int e0 = __ldg(a.rowptr + row), e1 = __ldg(a.rowptr + row + 1);
-#pragma unroll 4
-      for (int e = e0; e < e1; ++e) {
-        const int j = __ldg(a.col + e);
-        const T av = __ldg(a.valA + e);
-        const T dj = __ldg(a.dinv + j);
-        const size_t oj = (size_t)j * a.ms + c0;
-        T rj[VW], pj[VW];
-        ld_ro(rj, a.R + oj);
-        ld_ro(pj, Pold + oj);
-#pragma unroll
-        for (int v = 0; v < VW; ++v) q[v] = fma(av, fma(beta[v], pj[v], dj * rj[v]), q[v]);
-      }
-      st(Pnew + off, pn);
-      st(a.Q + off, q);
-#pragma unroll
-      for (int v = 0; v < VW; ++v) acc[0][v].add_prod(pn[v], q[v]);
-    }
-  }
-  __shared__ double tot[1][kMaxCols];
-  if (!grid_reduce<T, LPR, 1>(acc, a, kCtrCgA, tot)) return;
-  const int c = threadIdx.x;
-  if (c < a.ms) {
-    const double pq = tot[0][c];
-    ctl->alpha[(it + 1) & 1][c] = (ctl->active[c] && pq > 0.0) ? ctl->rz[c] / pq : 0.0;
-  }
-}
+// Streaming passes handle RU rows per lane group per iteration, loading all
+// of them before any arithmetic so that enough bytes are in flight per SM.
+constexpr int kStreamRows = 4;
 
+// CG pass B of iteration j: z_j = z_{j-1} - alpha_j D^-1 q_j (= D^-1 r_j),
+// r_j = D z_j; per component r_j.z_j (float-float) and ||r_j||^2 (float32
+// per thread, tolerance only); convergence test and beta for iteration j+1.
 template <typename T, int LPR>
 __global__ void __launch_bounds__(kBlockThreads, 2) k_cg_b(const KArgs<T> a) {
   typedef typename AccOf<T>::type Acc;
+  constexpr int RU = kStreamRows;
   DevCtl* ctl = a.ctl;
-  if (ctl->halted && !a.ignore_halt) return;
+  if (ctl->halted && !a.ignore_halt) {
+    // a kernel of this iteration halted the run: end the CG loop
+    if (a.set_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(a.cond, 0);
+    return;
+  }
   SEG_ROW_SETUP
   const int it = ctl->it;
+  const unsigned ms = a.ms;
   T al[VW];
 #pragma unroll
   for (int v = 0; v < VW; ++v) al[v] = (T)ctl->alpha[(it + 1) & 1][c0 + v];
@@ -517,24 +799,42 @@ __global__ void __launch_bounds__(kBlockThreads, 2) k_cg_b(const KArgs<T> a) {
   for (int d = 0; d < 2; ++d)
 #pragma unroll
     for (int v = 0; v < VW; ++v) acc[d][v].zero();
-  for (int base = r0 + warp * RPW; base < r1; base += NW * RPW) {
-    const int row = base + rs;
-    if (row < r1) {
-      const size_t off = (size_t)row * a.ms + c0;
-      T r[VW], q[VW];
-      ld(r, a.R + off);
-      ld_ro(q, a.Q + off);
-      const T di = __ldg(a.dinv + row);
+  T rr[VW];
 #pragma unroll
-      for (int v = 0; v < VW; ++v) r[v] = fma(-al[v], q[v], r[v]);
-      st(a.R + off, r);
+  for (int v = 0; v < VW; ++v) rr[v] = T(0);
+  for (int base = r0 + warp * RPW * RU; base < r1; base += NW * RPW * RU) {
+    T z[RU][VW], q[RU][VW], di[RU], dg[RU];
 #pragma unroll
-      for (int v = 0; v < VW; ++v) {
-        acc[0][v].add_prod(r[v], di * r[v]);
-        acc[1][v].add_prod(r[v], r[v]);
+    for (int u = 0; u < RU; ++u) {
+      const unsigned row = base + u * RPW + rs;
+      if ((int)row < r1) {
+        ld(z[u], a.Z + (row * ms + c0));
+        ld_ro(q[u], a.Q + (row * ms + c0));
+        di[u] = __ldg(a.dinv + row);
+        dg[u] = __ldg(a.diagA + row);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < RU; ++u) {
+      const unsigned row = base + u * RPW + rs;
+      if ((int)row < r1) {
+        T r[VW];
+#pragma unroll
+        for (int v = 0; v < VW; ++v) {
+          z[u][v] = fma(-al[v], di[u] * q[u][v], z[u][v]);
+          r[v] = dg[u] * z[u][v];
+        }
+        st(a.Z + (row * ms + c0), z[u]);
+#pragma unroll
+        for (int v = 0; v < VW; ++v) {
+          acc[0][v].add_prod(r[v], z[u][v]);
+          rr[v] = fma(r[v], r[v], rr[v]);
+        }
       }
     }
   }
+#pragma unroll
+  for (int v = 0; v < VW; ++v) acc[1][v].add_val(rr[v]);
   __shared__ double tot[2][kMaxCols];
   if (!grid_reduce<T, LPR, 2>(acc, a, kCtrCgB, tot)) return;
   int act = 0, bad = 0;
@@ -554,7 +854,7 @@ __global__ void __launch_bounds__(kBlockThreads, 2) k_cg_b(const KArgs<T> a) {
   if (threadIdx.x == 0) {
     const int it1 = it + 1;
     ctl->it = it1;
-    int cont = (any && it1 < a.maxit) ? 1 : 0;
+    int cont = (any && it1 < a.maxit && ctl->halted != 2) ? 1 : 0;
     if (any && it1 >= a.maxit) ctl->status |= 1;
     if (anybad) {
       ctl->status |= 2;
@@ -571,12 +871,14 @@ __global__ void __launch_bounds__(kBlockThreads, 2) k_cg_b(const KArgs<T> a) {
 //   u~ = x * inv_n,  u^_i = u~_i exp(-(2 tau/eps^2) sum_{j != i} u~_j^2).
 template <typename T, int LPR>
 __global__ void __launch_bounds__(kBlockThreads, 2) k_finish(const KArgs<T> a) {
+  constexpr int RU = kStreamRows;
   DevCtl* ctl = a.ctl;
   if (ctl->halted && !a.ignore_halt) return;
   SEG_ROW_SETUP
   const int lbase = lane - cg;
   const int it = ctl->it;
   const T* P = (it & 1) ? a.P1 : a.P0;
+  const unsigned ms = a.ms;
   T al[VW], invn[VW];
 #pragma unroll
   for (int v = 0; v < VW; ++v) {
@@ -584,34 +886,36 @@ __global__ void __launch_bounds__(kBlockThreads, 2) k_finish(const KArgs<T> a) {
     invn[v] = (T)ctl->inv_n[c0 + v];
   }
   const T mcoef = -(T)a.coef;
-  for (int base = r0 + warp * RPW; base < r1; base += NW * RPW) {
-    const int row = base + rs;
-    const bool valid = row < r1;
-    const size_t off = (size_t)row * a.ms + c0;
-    T x[VW];
+  for (int base = r0 + warp * RPW * RU; base < r1; base += NW * RPW * RU) {
+    T x[RU][VW], p[RU][VW];
 #pragma unroll
-    for (int v = 0; v < VW; ++v) x[v] = T(0);
-    if (valid) {
-      ld(x, a.X + off);
-      if (a.apply_x) {
-        T p[VW];
-        ld_ro(p, P + off);
+    for (int u = 0; u < RU; ++u) {
+      const unsigned row = base + u * RPW + rs;
 #pragma unroll
-        for (int v = 0; v < VW; ++v) x[v] = fma(al[v], p[v], x[v]);
+      for (int v = 0; v < VW; ++v) x[u][v] = p[u][v] = T(0);
+      if ((int)row < r1) {
+        ld(x[u], a.X + (row * ms + c0));
+        if (a.apply_x) ld_ro(p[u], P + (row * ms + c0));
       }
     }
-    if (a.apply_ode) {
-      T sq[1][VW], ex[1][VW], ut[VW];
 #pragma unroll
-      for (int v = 0; v < VW; ++v) {
-        ut[v] = x[v] * invn[v];
-        sq[0][v] = ut[v] * ut[v];
+    for (int u = 0; u < RU; ++u) {
+      const unsigned row = base + u * RPW + rs;
+#pragma unroll
+      for (int v = 0; v < VW; ++v) x[u][v] = fma(al[v], p[u][v], x[u][v]);
+      if (a.apply_ode) {
+        T sq[1][VW], ex[1][VW], ut[VW];
+#pragma unroll
+        for (int v = 0; v < VW; ++v) {
+          ut[v] = x[u][v] * invn[v];
+          sq[0][v] = ut[v] * ut[v];
+        }
+        row_exclusive<T, LPR, 1>(sq, ex, lbase, cg);
+#pragma unroll
+        for (int v = 0; v < VW; ++v) x[u][v] = ut[v] * t_exp(mcoef * ex[0][v]);
       }
-      row_exclusive<T, LPR, 1>(sq, ex, lbase, cg);
-#pragma unroll
-      for (int v = 0; v < VW; ++v) x[v] = ut[v] * t_exp(mcoef * ex[0][v]);
+      if ((int)row < r1) st(a.X + (row * ms + c0), x[u]);
     }
-    if (valid) st(a.X + off, x);
   }
   if (a.count_step && blockIdx.x == 0 && threadIdx.x == 0) {
     ctl->step += 1;
@@ -698,10 +1002,10 @@ __global__ void k_labels(const KArgs<T> a, int* am, unsigned char* vp, const int
   vp[z] = (bv - others > T(0)) ? 1 : 0;
 }
 
-template <typename T, int LPR>
+template <typename T, int LPR, int W>
 bool fill_kernels(KernelSet* ks) {
-  ks->start = (void*)k_start<T, LPR>;
-  ks->cg_a = (void*)k_cg_a<T, LPR>;
+  ks->start = (void*)k_start<T, LPR, W>;
+  ks->cg_a = (void*)k_cg_a<T, LPR, W>;
   ks->cg_b = (void*)k_cg_b<T, LPR>;
   ks->finish = (void*)k_finish<T, LPR>;
   ks->energy = (void*)k_energy<T, LPR>;
@@ -709,7 +1013,16 @@ bool fill_kernels(KernelSet* ks) {
   ks->scatter_in = (void*)k_scatter_in<T>;
   ks->gather_out = (void*)k_gather_out<T>;
   ks->labels = (void*)k_labels<T>;
+  ks->smem_start = row_stage_smem<StartStage<T, LPR, W>>();
+  ks->smem_cg_a = row_stage_smem<CgAStage<T, LPR, W>>();
   return true;
+}
+
+template <typename T, int LPR>
+bool fill_kernels_w(int w, KernelSet* ks) {
+  if (w == 8) return fill_kernels<T, LPR, 8>(ks);
+  if (w == 16) return fill_kernels<T, LPR, 16>(ks);
+  return false;
 }
 
 }  // namespace segimpl

@@ -1,14 +1,15 @@
-// float32-storage specialisations of the hot-path kernels (lanes per row 1..8).
+// float32-storage specialisations of the hot-path kernels (lanes per row
+// 1..8, padded-ELL widths 8 and 16).
 #include "kernels.cuh"
 
 namespace segimpl {
 
-bool get_kernels_f32(int lpr, KernelSet* ks) {
+bool get_kernels_f32(int lpr, int w, KernelSet* ks) {
   switch (lpr) {
-    case 1: return fill_kernels<float, 1>(ks);
-    case 2: return fill_kernels<float, 2>(ks);
-    case 4: return fill_kernels<float, 4>(ks);
-    case 8: return fill_kernels<float, 8>(ks);
+    case 1: return fill_kernels_w<float, 1>(w, ks);
+    case 2: return fill_kernels_w<float, 2>(w, ks);
+    case 4: return fill_kernels_w<float, 4>(w, ks);
+    case 8: return fill_kernels_w<float, 8>(w, ks);
     default: return false;
   }
 }

@@ -58,16 +58,16 @@ struct KArgs {
   int n;    // vertex rows
   int m;    // components
   int ms;   // padded components (row stride)
-  int rows_per_block;
-  const int* rowptr;
-  const int* col;
-  const T* valA;   // A = M + tau K
+  int ell_w;       // entries per padded-ELL row (8 or 16)
+  const int* ell_col;  // [n][ell_w] column indices; padding repeats the row itself
+  const T* valA;   // [n][ell_w] A = M + tau K (0 on padding)
   const T* valM;
   const T* valK;
   const T* dinv;   // 1 / diag(A)
+  const T* diagA;  // diag(A)
   T* X;            // state / CG iterate
-  T* R;            // residual
-  T* P0;           // search directions (ping-pong)
+  T* Z;            // preconditioned residual z = D^-1 r
+  T* P0;           // search directions (ping-pong between CG iterations)
   T* P1;
   T* Q;            // A p
   DevCtl* ctl;
@@ -83,7 +83,6 @@ struct KArgs {
   const int* tri;  // [F][3] rows of the triangle corners (internal numbering)
   const T* tarea;  // |T|
   int ntri;
-  int tri_per_block;
   long long check_every;
   double energy_tol;
   int force;       // evaluate the energy regardless of the cadence
@@ -104,10 +103,12 @@ struct KernelSet {
   void* scatter_in;   // (args, src, perm)
   void* gather_out;   // (args, dst, iperm)
   void* labels;       // (args, am, vp, iperm)
+  unsigned smem_start;  // dynamic shared memory of k_start (bytes)
+  unsigned smem_cg_a;   // dynamic shared memory of k_cg_a (bytes)
 };
 
-bool get_kernels_f32(int lpr, KernelSet* ks);
-bool get_kernels_f64(int lpr, KernelSet* ks);
+bool get_kernels_f32(int lpr, int ell_w, KernelSet* ks);
+bool get_kernels_f64(int lpr, int ell_w, KernelSet* ks);
 
 // Record the message returned by seg_last_error() on this thread.
 void set_last_error(const char* msg);
