@@ -216,7 +216,7 @@ def kernel_bytes(n, ntri, m_pad, s, W=8):
       k_cg_a   read R, p_old, X; write X, p_new, q; columns + A values, diagonal
       k_cg_b   read R, q; write R; diagonal
       k_finish read X, p; write X
-      k_energy read X, triangle corners (3 int32) and areas
+      k_energy_check / k_energy  read X, triangle corners (3 int32) and areas
     """
     V = n * m_pad * s
     ell = n * W * 4
@@ -225,6 +225,7 @@ def kernel_bytes(n, ntri, m_pad, s, W=8):
         "k_cg_a": 6 * V + ell + n * W * s + n * s,
         "k_cg_b": 3 * V + n * s,
         "k_finish": 3 * V,
+        "k_energy_check": V + ntri * (12 + s),
         "k_energy": V + ntri * (12 + s),
     }
 
@@ -287,7 +288,7 @@ def run_ours(a, rank, ws, local):
     peak, peak_kind = measured_peak()
     kb = kernel_bytes(n, int(tri.shape[0]), li["padded_m"], 4)
     kern = {}
-    for which, name in enumerate(["k_start", "k_cg_a", "k_cg_b", "k_finish", "k_energy"]):
+    for which, name in enumerate(["k_start", "k_cg_a", "k_cg_b", "k_finish", "k_energy_check", "k_energy"]):
         t = seg.seg_time_kernel(st, which, 20)
         kern[name] = {"ms": t, "bytes": kb[name], "GBps": kb[name] / (t / 1e3) / 1e9,
                       "frac": kb[name] / (t / 1e3) / 1e9 / peak}

@@ -209,9 +209,10 @@ const char* seg_last_error(void);
  * its stream with CUDA events; *ms_per_launch receives the mean.  which:
  * 0 = start pass (residual, norms, Dirichlet energy), 1 = CG pass A (search
  * direction update + A p + p.Ap), 2 = CG pass B (residual update + dots),
- * 3 = finish pass (last x update + nodal ODE), 4 = energy pass (S_eps and the
- * coupling integrals).  The kernels run on the state's own buffers, so the
- * state's values are undefined afterwards: call seg_set_u before using it. */
+ * 3 = finish pass (last x update + nodal ODE), 4 = energy pass of the stop rule
+ * (S_eps), 5 = energy pass with the per-component coupling integrals.  The
+ * kernels run on the state's own buffers, so the state's values are undefined
+ * afterwards: call seg_set_u before using it. */
 seg_status seg_time_kernel(seg_state* s, int32_t which, int32_t reps, double* ms_per_launch);
 
 /* Launch geometry of the row kernels of a state (nullable outputs). */

@@ -72,7 +72,8 @@ struct seg_state {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int launch_mode = 0;
-  int grid = 0;
+  int grid = 0;     // blocks of the row kernels
+  int grid_e = 0;   // blocks of the S_eps check kernel
   void* X = nullptr;
   void* Z = nullptr;        // preconditioned residual
   void* P0 = nullptr;       // search directions, ping-pong
@@ -130,18 +131,21 @@ unsigned smem_of(const seg_state* s, void* fn) {
   return 0;
 }
 
-// Launch one row kernel (grid = s->grid) with the state's arguments.
+int grid_of(const seg_state* s, void* fn) { return fn == s->ks.energy_check ? s->grid_e : s->grid; }
+
+// Launch one row kernel with the state's arguments.
 seg_status launch_row(seg_state* s, void* fn, const Launch& l) {
   cudaError_t e;
   const unsigned smem = smem_of(s, fn);
+  const dim3 grid(grid_of(s, fn));
   if (s->prec == SEG_MIXED_FP32) {
     KArgs<float> a = make_args<float>(s, l);
     void* args[] = {&a};
-    e = cudaLaunchKernel(fn, dim3(s->grid), dim3(kBlockThreads), args, smem, s->stream);
+    e = cudaLaunchKernel(fn, grid, dim3(kBlockThreads), args, smem, s->stream);
   } else {
     KArgs<double> a = make_args<double>(s, l);
     void* args[] = {&a};
-    e = cudaLaunchKernel(fn, dim3(s->grid), dim3(kBlockThreads), args, smem, s->stream);
+    e = cudaLaunchKernel(fn, grid, dim3(kBlockThreads), args, smem, s->stream);
   }
   if (e != cudaSuccess) return fail(SEG_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
   return SEG_OK;
@@ -189,7 +193,7 @@ seg_status direct_step(seg_state* s) {
   Launch l;
   l.ignore_halt = 0;
   seg_status st = launch_row(s, s->ks.start, l);
-  if (st == SEG_OK) st = launch_row(s, s->ks.energy, l);
+  if (st == SEG_OK) st = launch_row(s, s->ks.energy_check, l);
   if (st == SEG_OK) st = sync_ctl(s);
   while (st == SEG_OK && s->hctl->cont && !s->hctl->halted) {
     st = launch_row(s, s->ks.cg_a, l);
@@ -236,7 +240,7 @@ seg_status build_graph_t(seg_state* s) {
   KArgs<T> base = make_args<T>(s, l);
   cudaGraphNode_t n_start, n_energy, n_loop, n_a, n_b, n_fin;
   SEG_CUDA(add_kernel_node<T>(&n_start, s->graph, nullptr, 0, s->ks.start, s->grid, base, s->ks.smem_start));
-  SEG_CUDA(add_kernel_node<T>(&n_energy, s->graph, &n_start, 1, s->ks.energy, s->grid, base, 0));
+  SEG_CUDA(add_kernel_node<T>(&n_energy, s->graph, &n_start, 1, s->ks.energy_check, s->grid_e, base, 0));
   cudaGraphNodeParams cp{};
   cp.type = cudaGraphNodeTypeConditional;
   cp.conditional.handle = s->cond;
@@ -567,6 +571,7 @@ seg_status seg_state_create(const seg_problem* p, int32_t m, double eps, seg_ini
     return fail(SEG_ERR_CUDA, std::string("cudaDeviceGetAttribute: ") + cudaGetErrorString(ce));
   }
   s->grid = prm.grid_blocks > 0 ? prm.grid_blocks : 2 * nsm;
+  s->grid_e = 4 * nsm;
   if (cuda_stream) {
     s->stream = (cudaStream_t)cuda_stream;
   } else {
@@ -770,21 +775,23 @@ seg_status seg_substep(seg_state* s, int32_t stage) {
 
 // ---------------------------------------------------------------- outputs
 
-static seg_status evaluate_energy(seg_state* s) {
+// S_eps (and, with per_component, the coupling integrals) of the
+// renormalised current state.
+static seg_status evaluate_energy(seg_state* s, bool per_component) {
   SEG_CUDA(cudaSetDevice(s->p->device));
   s->pending = true;
   seg_status st = ensure_norm(s);
   if (st != SEG_OK) return st;
   Launch l;
   l.force = 1;
-  st = launch_row(s, s->ks.energy, l);
+  st = launch_row(s, per_component ? s->ks.energy : s->ks.energy_check, l);
   if (st != SEG_OK) return st;
   return sync_ctl(s);
 }
 
 seg_status seg_energy(seg_state* s, double* total, double* functional, double* dirichlet, double* s_eps) {
   if (!s) return fail(SEG_ERR_ARG, "state is NULL");
-  seg_status st = evaluate_energy(s);
+  seg_status st = evaluate_energy(s, false);
   if (st != SEG_OK) return st;
   const DevCtl& c = *s->hctl;
   if (total) *total = c.e_total;
@@ -797,7 +804,7 @@ seg_status seg_energy(seg_state* s, double* total, double* functional, double* d
 
 seg_status seg_eigenvalue_estimates(seg_state* s, double* lambda, double* lambda_cl) {
   if (!s) return fail(SEG_ERR_ARG, "state is NULL");
-  seg_status st = evaluate_energy(s);
+  seg_status st = evaluate_energy(s, true);
   if (st != SEG_OK) return st;
   const DevCtl& c = *s->hctl;
   for (int i = 0; i < s->m; ++i) {
@@ -843,9 +850,9 @@ seg_status seg_get_stats(seg_state* s, seg_stats* out) {
 
 seg_status seg_time_kernel(seg_state* s, int32_t which, int32_t reps, double* ms_per_launch) {
   if (!s || !ms_per_launch) return fail(SEG_ERR_ARG, "state or output is NULL");
-  if (which < 0 || which > 4 || reps < 1) return fail(SEG_ERR_ARG, "which must be 0..4 and reps >= 1");
+  if (which < 0 || which > 5 || reps < 1) return fail(SEG_ERR_ARG, "which must be 0..5 and reps >= 1");
   SEG_CUDA(cudaSetDevice(s->p->device));
-  void* fns[] = {s->ks.start, s->ks.cg_a, s->ks.cg_b, s->ks.finish, s->ks.energy};
+  void* fns[] = {s->ks.start, s->ks.cg_a, s->ks.cg_b, s->ks.finish, s->ks.energy_check, s->ks.energy};
   Launch l;
   l.force = 1;
   l.apply_x = 1;

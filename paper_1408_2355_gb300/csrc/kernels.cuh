@@ -771,6 +771,153 @@ __global__ void __launch_bounds__(kBlockThreads, 2) k_energy(const KArgs<T> a) {
   }
 }
 
+// Block + grid reduction of one float-float (or double) scalar per thread,
+// same ticket protocol as grid_reduce; the total lands in *tot of the last
+// block, which returns true.
+template <typename T>
+__device__ __forceinline__ bool grid_reduce_scalar(typename AccOf<T>::type acc, DevCtl* ctl, void* partv, int slot,
+                                                   double* tot) {
+  typedef typename AccOf<T>::type Acc;
+  typedef typename AccOf<T>::part Part;
+  constexpr int NW = kBlockThreads / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) shfl_add(acc, off);
+  __shared__ Part red[NW];
+  __shared__ unsigned int ticket;
+  if (lane == 0) red[warp] = to_part(acc);
+  __syncthreads();
+  const int G = gridDim.x;
+  Part* part = reinterpret_cast<Part*>(partv);
+  if (threadIdx.x == 0) {
+    Acc s;
+    s.zero();
+    for (int w = 0; w < NW; ++w) add_part(s, red[w]);
+    part[blockIdx.x] = to_part(s);
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) ticket = atomicAdd(&ctl->counters[slot], 1u);
+  __syncthreads();
+  if (ticket != (unsigned int)(G - 1)) return false;
+  __threadfence();
+  if (warp == 0) {
+    Acc s;
+    s.zero();
+    for (int b = lane; b < G; b += 32) add_part(s, __ldcg(&part[b]));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) shfl_add(s, off);
+    if (lane == 0) *tot = s.value();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) ctl->counters[slot] = 0u;
+  return true;
+}
+
+// Symmetric 6-point rule of degree 4 on a triangle (two orbits of points
+// with barycentric coordinates (a, a, 1 - 2a)); weights sum to 1, so
+// int_T f = |T| sum_q w_q f(q) for every polynomial of degree <= 4.  The
+// constants solve the moment equations of the barycentric monomials.
+constexpr double kQuadA1 = 0.4459484909159649;
+constexpr double kQuadW1 = 0.22338158967801156;
+constexpr double kQuadA2 = 0.0915762135097707;
+constexpr double kQuadW2 = 0.10995174365532179;
+
+// S_eps of the normalised state for the stop rule (and seg_energy): one
+// thread per triangle, the degree-4 rule, and the pair sum in prefix form
+//   sum_{i != j} u_i^2 u_j^2 = 2 sum_i u_i^2 sum_{j < i} u_j^2
+// (non-negative terms only, no cancellation).  Components are visited in
+// chunks of VW so that only one chunk of the three corner rows is live.
+template <typename T, int LPR>
+__global__ void __launch_bounds__(kBlockThreads) k_energy_check(const KArgs<T> a) {
+  typedef typename AccOf<T>::type Acc;
+  constexpr int VW = VecW<T>::W;
+  constexpr int MS = LPR * VW;
+  DevCtl* ctl = a.ctl;
+  if (ctl->halted && !a.ignore_halt) return;
+  if (!a.force) {
+    if (a.check_every <= 0) return;
+    if (ctl->step % a.check_every != 0) return;
+  }
+  __shared__ T sinv[MS];
+  if (threadIdx.x < MS) sinv[threadIdx.x] = (T)ctl->inv_n[threadIdx.x];
+  __syncthreads();
+  const T A1 = (T)kQuadA1, B1mA1 = (T)(1.0 - 3.0 * kQuadA1), W1 = (T)kQuadW1;
+  const T A2 = (T)kQuadA2, B2mA2 = (T)(1.0 - 3.0 * kQuadA2), W2 = (T)kQuadW2;
+  const unsigned ms = MS;
+  Acc acc;
+  acc.zero();
+  for (int t = blockIdx.x * kBlockThreads + threadIdx.x; t < a.ntri; t += gridDim.x * kBlockThreads) {
+    const int* tr = a.tri + 3 * (size_t)t;
+    const unsigned z0 = __ldg(tr) * ms, z1 = __ldg(tr + 1) * ms, z2 = __ldg(tr + 2) * ms;
+    const T area = __ldg(a.tarea + t);
+    T pre[6], sum[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) pre[q] = sum[q] = T(0);
+#pragma unroll
+    for (int c = 0; c < MS; c += VW) {
+      T u0[VW], u1[VW], u2[VW];
+      ld_ro(u0, a.X + (z0 + c));
+      ld_ro(u1, a.X + (z1 + c));
+      ld_ro(u2, a.X + (z2 + c));
+#pragma unroll
+      for (int v = 0; v < VW; ++v) {
+        const T s = sinv[c + v];
+        const T b0 = u0[v] * s, b1 = u1[v] * s, b2 = u2[v] * s;
+        const T tot = b0 + b1 + b2;
+        // values at the 6 points: a*tot + (b - a)*corner, b = 1 - 2a
+        const T o1 = A1 * tot, o2 = A2 * tot;
+        T val[6];
+        val[0] = fma(B1mA1, b0, o1);
+        val[1] = fma(B1mA1, b1, o1);
+        val[2] = fma(B1mA1, b2, o1);
+        val[3] = fma(B2mA2, b0, o2);
+        val[4] = fma(B2mA2, b1, o2);
+        val[5] = fma(B2mA2, b2, o2);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+          const T sq = val[q] * val[q];
+          sum[q] = fma(sq, pre[q], sum[q]);
+          pre[q] += sq;
+        }
+      }
+    }
+    const T st = T(2) * area * (W1 * (sum[0] + sum[1] + sum[2]) + W2 * (sum[3] + sum[4] + sum[5]));
+    acc.add_val(st);
+  }
+  __shared__ double tot;
+  if (!grid_reduce_scalar<T>(acc, ctl, a.part, kCtrEnergy, &tot)) return;
+  if (threadIdx.x == 0) {
+    double D = 0.0;
+    for (int c = 0; c < a.m; ++c) D += ctl->lam[c];
+    const double S = tot * a.inv_eps2;
+    const double total = D + S;
+    ctl->e_total = total;
+    ctl->e_dir = D;
+    ctl->e_s = S;
+    if (!a.force) {
+      ctl->checks += 1;
+      int stop = 0;
+      if (!isfinite(total)) {
+        ctl->status |= 2;
+        ctl->halted = 2;
+        stop = 1;
+      } else {
+        if (ctl->have_prev && a.energy_tol >= 0.0 && fabs(total - ctl->e_prev) < a.energy_tol) {
+          ctl->halted = 1;
+          stop = 1;
+        }
+        ctl->e_prev = total;
+        ctl->have_prev = 1;
+      }
+      if (stop) {
+        ctl->cont = 0;
+        if (a.set_cond) cudaGraphSetConditional(a.cond, 0);
+      }
+    }
+  }
+}
+
 // Streaming passes handle RU rows per lane group per iteration, loading all
 // of them before any arithmetic so that enough bytes are in flight per SM.
 constexpr int kStreamRows = 4;
@@ -1009,6 +1156,7 @@ bool fill_kernels(KernelSet* ks) {
   ks->cg_b = (void*)k_cg_b<T, LPR>;
   ks->finish = (void*)k_finish<T, LPR>;
   ks->energy = (void*)k_energy<T, LPR>;
+  ks->energy_check = (void*)k_energy_check<T, LPR>;
   ks->init_rng = (void*)k_init_rng<T>;
   ks->scatter_in = (void*)k_scatter_in<T>;
   ks->gather_out = (void*)k_gather_out<T>;

@@ -98,7 +98,8 @@ struct KernelSet {
   void* cg_a;
   void* cg_b;
   void* finish;
-  void* energy;
+  void* energy;        // S_eps and per-component coupling integrals
+  void* energy_check; // S_eps only (stop rule, seg_energy)
   void* init_rng;     // (args, perm, seed, kind)
   void* scatter_in;   // (args, src, perm)
   void* gather_out;   // (args, dst, iperm)

@@ -70,7 +70,9 @@ def test_level8_m16_mixed_bench_configuration(seg):
     assert np.abs(o.l2_norms(M, Ug) - 1).max() < 1e-6
     assert prev["total"] > 0
     lam, lam_cl = seg.seg_eigenvalue_estimates(st)
-    assert rel(lam_cl.sum(), e["dirichlet"] + 2 * e["s_eps"]) < 1e-9
+    # lambda_cl comes from the per-component energy kernel, S_eps from the
+    # stop-rule kernel (another quadrature): equal to float32 rounding
+    assert rel(lam_cl.sum(), e["dirichlet"] + 2 * e["s_eps"]) < 1e-6
     check_labels(seg, st, tri, U, Ug)
     stats = seg.seg_get_stats(st)
     assert stats["status_bits"] == 0 and stats["checks"] == steps
