@@ -380,6 +380,33 @@ __device__ __forceinline__ void lds(double (&d)[2], const double* p) {
   d[0] = x.x; d[1] = x.y;
 }
 
+// Copy one staged padded-ELL row (W indices or values) from shared memory
+// into registers with 16-byte loads.
+template <int W>
+__device__ __forceinline__ void lds_row(int (&d)[W], const int* p) {
+#pragma unroll
+  for (int k = 0; k < W; k += 4) {
+    const int4 v = *reinterpret_cast<const int4*>(p + k);
+    d[k] = v.x; d[k + 1] = v.y; d[k + 2] = v.z; d[k + 3] = v.w;
+  }
+}
+template <int W>
+__device__ __forceinline__ void lds_row(float (&d)[W], const float* p) {
+#pragma unroll
+  for (int k = 0; k < W; k += 4) {
+    const float4 v = *reinterpret_cast<const float4*>(p + k);
+    d[k] = v.x; d[k + 1] = v.y; d[k + 2] = v.z; d[k + 3] = v.w;
+  }
+}
+template <int W>
+__device__ __forceinline__ void lds_row(double (&d)[W], const double* p) {
+#pragma unroll
+  for (int k = 0; k < W; k += 2) {
+    const double2 v = *reinterpret_cast<const double2*>(p + k);
+    d[k] = v.x; d[k + 1] = v.y;
+  }
+}
+
 // Mark a timed-out wait: the block records the error and halts the run.
 __device__ __forceinline__ void report_timeout(DevCtl* ctl) {
   atomicOr(&ctl->status, 4);
@@ -483,9 +510,11 @@ __global__ void __launch_bounds__(kBlockThreads, 2) k_start(const KArgs<T> a) {
       dyn_smem + warp * 2 * Stage::kBytes, bars[warp], r0, r1, src, [&](const Stage& sg, int row0, int nr) {
         if (rs >= nr) return;
         const unsigned row = row0 + rs;
-        const int* cols = sg.cols() + rs * W;
-        const T* kv = sg.vals(0) + rs * W;
-        const T* mv = sg.vals(1) + rs * W;
+        int cols[W];
+        T kv[W], mv[W];
+        lds_row<W>(cols, sg.cols() + rs * W);
+        lds_row<W>(kv, sg.vals(0) + rs * W);
+        lds_row<W>(mv, sg.vals(1) + rs * W);
         T x[VW];
         lds(x, sg.vec(0) + rs * ms + c0);
         const T di = __ldg(a.dinv + row);
@@ -596,8 +625,10 @@ __global__ void __launch_bounds__(kBlockThreads, 2) k_cg_a(const KArgs<T> a) {
       dyn_smem + warp * 2 * Stage::kBytes, bars[warp], r0, r1, src, [&](const Stage& sg, int row0, int nr) {
         if (rs >= nr) return;
         const unsigned row = row0 + rs;
-        const int* cols = sg.cols() + rs * W;
-        const T* av = sg.vals(0) + rs * W;
+        int cols[W];
+        T av[W];
+        lds_row<W>(cols, sg.cols() + rs * W);
+        lds_row<W>(av, sg.vals(0) + rs * W);
         // all neighbour rows of z and p_old in flight at once
         T zj[W][VW], pj[W][VW];
 #pragma unroll
