@@ -32,8 +32,9 @@ if ROOT not in sys.path:
 
 HBM_FALLBACK_GBS = 6800.0
 # DRAM bytes (read + write) per k_cg_a launch from the ncu capture summarised
-# in profiles/; None until a capture of the current kernel exists.
-TRAFFIC_CG_A = None
+# in profiles/k_cg_a_sphere_L8_m16_mixed.md (level-8 sphere, m = 16, mixed);
+# valid for that workload and that version of the kernel only.
+TRAFFIC_CG_A = 271.1e6
 METRIC = "DoF-steps/s (N*m*steps) sphere 655k m=16 FP32-mix vs FP64; p50/p99 latency"
 
 
@@ -46,7 +47,7 @@ def parse():
                     help="direct: kernels launched one by one (for profilers that cannot see graph kernels)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--level", type=int, default=8)
-    ap.add_argument("--m", type=int, default=16)
+    ap.add_argument("--components", dest="m", type=int, default=16, help="number of components m")
     ap.add_argument("--eps", type=float, default=1e-3)
     ap.add_argument("--tau", type=float, default=5e-6)
     ap.add_argument("--seed", type=int, default=1236)

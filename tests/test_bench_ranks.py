@@ -1,0 +1,81 @@
+"""Host-side logic of bench.py on CPU: the replica ranks' barrier and
+max-over-ranks timing with the gloo backend (world size 2), and the JSON line
+of the reference arm (the oracle) alone and under two ranks."""
+
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out_dir):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class A:
+        pass
+
+    r, ws, local = bench.dist_setup(A())
+    bench.barrier(ws)
+    m = bench.max_over_ranks(1.5 + rank, ws)
+    with open(os.path.join(out_dir, f"rank{rank}.txt"), "w") as f:
+        f.write(f"{r} {ws} {m}\n")
+    import torch.distributed as dist
+
+    dist.destroy_process_group()
+
+
+def test_max_over_ranks_with_gloo(tmp_path):
+    import torch.multiprocessing as mp
+
+    port = _free_port()
+    mp.spawn(_rank_main, args=(2, port, str(tmp_path)), nprocs=2, join=True)
+    for rank in range(2):
+        r, ws, m = open(tmp_path / f"rank{rank}.txt").read().split()
+        assert int(r) == rank and int(ws) == 2 and float(m) == 2.5
+
+
+REF_ARGS = ["--impl", "reference", "--level", "3", "--components", "4", "--steps", "2", "--warmup", "1",
+            "--reference-budget-seconds", "2"]
+
+
+def _check_reference_line(line):
+    d = json.loads(line)
+    assert d["impl"] == "reference" and d["unit"] == "DoF-steps/s" and d["value"] > 0
+    assert d["higher_is_better"] is True and d["steps"] == 2 and d["warmup"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+    assert "workload" in d["config"]
+
+
+def test_reference_arm_json_line():
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py")] + REF_ARGS, capture_output=True,
+                       text=True, timeout=300, cwd=ROOT)
+    assert r.returncode == 0, r.stderr
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    _check_reference_line(lines[0])
+
+
+def test_reference_arm_under_two_ranks_prints_once():
+    port = _free_port()
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node=2",
+           "--master-addr=127.0.0.1", f"--master-port={port}", os.path.join(ROOT, "bench.py"), "--gpus", "2"]
+    r = subprocess.run(cmd + REF_ARGS, capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    _check_reference_line(lines[0])
