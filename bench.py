@@ -54,6 +54,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=64, help="0 disables the serving run")
+    ap.add_argument("--serve-compare", type=int, default=24)
+    ap.add_argument("--serve-rate", type=float, default=8.0)
+    ap.add_argument("--serve-check-every", type=int, default=25)
+    ap.add_argument("--serve-tol", type=float, default=1e-2)
+    ap.add_argument("--serve-max-steps", type=int, default=400)
+    ap.add_argument("--serve-quantum", type=int, default=16)
     ap.add_argument("--cpu-sample-seconds", type=float, default=20.0)
     ap.add_argument("--reference-budget-seconds", type=float, default=150.0)
     return ap.parse_args()
@@ -380,6 +387,168 @@ def run_ours(a, rank, ws, local):
     return out
 
 
+SERVE_MESHES = [("sphere", 4), ("sphere", 5), ("sphere", 6), ("sphere", 7), ("torus", 128, 64),
+                ("torus", 256, 128), ("torus", 512, 256), ("ellipsoid", 5), ("ellipsoid", 6), ("ellipsoid", 7)]
+
+
+def _serve_mesh(spec):
+    import workload as w
+
+    if spec[0] == "sphere":
+        return w.icosphere(spec[1])
+    if spec[0] == "torus":
+        return w.torus(spec[1], spec[2], 1.0, 0.4)
+    return w.ellipsoid(spec[1], 1.0, 0.8, 0.6)
+
+
+def serve_stream(a):
+    """The seeded request mix of the serving benchmark.
+
+    Each request picks a mesh from SERVE_MESHES, m uniform in {2..24} and one
+    of 4 interface widths eps = c h (h the mesh's mean edge length, c in
+    {1, 1.41, 2, 2.83}) with tau = 5 eps^2, so that the (mesh, tau) problems
+    are assembled once, before the stream starts, and shared.  Arrival times
+    are a Poisson process of rate --serve-rate.
+    """
+    import numpy as np
+
+    rng = np.random.default_rng(a.seed + 5)
+    arrivals = np.cumsum(rng.exponential(1.0 / a.serve_rate, a.serve_requests))
+    reqs = [(int(rng.integers(len(SERVE_MESHES))), int(rng.integers(2, 25)), int(rng.integers(4)))
+            for _ in range(a.serve_requests)]
+    return arrivals, reqs
+
+
+def serve_problems(seg, reqs, prec):
+    """{(mesh index, width index): (problem, eps)} for the requests' pairs."""
+    import numpy as np
+
+    problems, meshes = {}, {}
+    for mi, _, ci in reqs:
+        if (mi, ci) in problems:
+            continue
+        if mi not in meshes:
+            xyz, tri = _serve_mesh(SERVE_MESHES[mi])
+            e = np.concatenate([tri[:, [0, 1]], tri[:, [1, 2]], tri[:, [2, 0]]])
+            h = float(np.linalg.norm(xyz[e[:, 0]] - xyz[e[:, 1]], axis=1).mean())
+            meshes[mi] = (seg.seg_create_mesh(xyz, tri), h)
+        mesh, h = meshes[mi]
+        eps = h * 2.0 ** (ci / 2)
+        problems[(mi, ci)] = (seg.seg_assemble(mesh, 5 * eps * eps, prec), eps)
+    return problems
+
+
+def serve_params(seg, a):
+    prm = seg.seg_params()
+    prm.check_every = a.serve_check_every
+    prm.energy_tol = a.serve_tol
+    prm.max_steps = a.serve_max_steps
+    return prm
+
+
+def run_serving(a, seg, prec, stream):
+    """Requests through the continuous-batching server.
+
+    stream=True: each request is submitted at its Poisson arrival time (real
+    time on the server clock); stream=False: all are submitted at once (a
+    burst, for throughput).  Every request runs to its stop rule (|change of
+    the total energy| < --serve-tol between checks --serve-check-every steps
+    apart) or --serve-max-steps.  Latency = completion - arrival.
+    """
+    import numpy as np
+
+    arrivals, reqs = serve_stream(a)
+    if not stream:
+        arrivals, reqs = np.zeros(a.serve_compare), reqs[:a.serve_compare]
+    problems = serve_problems(seg, reqs, prec)
+    prm = serve_params(seg, a)
+    sp = seg.seg_server_params()
+    sp.steps_per_tick = a.serve_quantum
+    srv = seg.seg_server_create(sp)
+    n_req = len(reqs)
+    ids = [None] * n_req
+    nxt = 0
+    t_start = seg.seg_server_clock(srv)
+    while True:
+        now = seg.seg_server_clock(srv) - t_start
+        while nxt < n_req and arrivals[nxt] <= now:
+            mi, m, ci = reqs[nxt]
+            prob, eps = problems[(mi, ci)]
+            ids[nxt] = seg.seg_server_submit(srv, prob, m, eps, seg.SEG_INIT_UNIFORM,
+                                             a.seed + 1000 + nxt, prm)
+            nxt += 1
+        running, queued = seg.seg_server_tick(srv)
+        if nxt == n_req and running == 0 and queued == 0:
+            break
+        if running == 0 and queued == 0:
+            time.sleep(max(0.0, min(0.01, arrivals[nxt] - now)))
+    makespan = seg.seg_server_clock(srv) - t_start
+    lat, dof_steps, conv, failed = [], 0.0, 0, 0
+    for k, rid in enumerate(ids):
+        info = seg.seg_server_info(srv, rid)
+        if info["phase"] != 2:
+            failed += 1
+            continue
+        lat.append(info["t_done"] - t_start - arrivals[k])
+        dof_steps += info["n_vert"] * info["m"] * info["steps"]
+        conv += info["converged"]
+    seg.seg_server_destroy(srv)
+    lat = np.array(lat)
+    return {
+        "value": dof_steps / makespan, "unit": "DoF-steps/s", "completed": int(len(lat)), "failed": failed,
+        "converged_fraction": conv / max(1, len(lat)),
+        "p50_latency_s": float(np.percentile(lat, 50)) if len(lat) else None,
+        "p99_latency_s": float(np.percentile(lat, 99)) if len(lat) else None,
+        "makespan_s": makespan, "dof_steps": dof_steps,
+    }
+
+
+def run_alone(a, seg, prec):
+    """The burst's requests, one after another, each stepped alone (seg_step)."""
+    import torch
+
+    reqs = serve_stream(a)[1][:a.serve_compare]
+    problems = serve_problems(seg, reqs, prec)
+    prm = serve_params(seg, a)
+    dof_steps, conv = 0.0, 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k, (mi, m, ci) in enumerate(reqs):
+        prob, eps = problems[(mi, ci)]
+        st = seg.seg_state_create(prob, m, eps, seg.SEG_INIT_UNIFORM, a.seed + 1000 + k, prm)
+        steps = seg.seg_step(st, a.serve_max_steps)
+        conv += seg.seg_get_stats(st)["converged"]
+        seg.seg_get_u(st)
+        dof_steps += seg.seg_problem_info(prob)["n_vert"] * m * steps
+        del st
+    dt = time.perf_counter() - t0
+    return {"value": dof_steps / dt, "unit": "DoF-steps/s", "seconds": dt, "dof_steps": dof_steps,
+            "converged_fraction": conv / len(reqs)}
+
+
+def serving_section(a):
+    """Serving benchmark: the Poisson stream (latency), and the first
+    --serve-compare requests as a burst through the server in mixed precision
+    against the same requests each stepped alone in FP64 and in mixed
+    precision (throughput)."""
+    import paper_1408_2355_gb300 as seg
+
+    out = {"requests": a.serve_requests, "arrival_rate_per_s": a.serve_rate,
+           "mix": "meshes " + ", ".join("-".join(map(str, s)) for s in SERVE_MESHES)
+                  + "; m ~ U{2..24}; eps = c h, c in {1, 1.41, 2, 2.83}, h mean edge length; tau = 5 eps^2",
+           "compared_requests": a.serve_compare,
+           "stop_rule": {"check_every": a.serve_check_every, "energy_tol": a.serve_tol,
+                         "max_steps": a.serve_max_steps},
+           "steps_per_tick": a.serve_quantum}
+    out["stream_mixed"] = run_serving(a, seg, seg.SEG_MIXED_FP32, True)
+    out["burst_mixed"] = run_serving(a, seg, seg.SEG_MIXED_FP32, False)
+    out["alone_mixed"] = run_alone(a, seg, seg.SEG_MIXED_FP32)
+    out["alone_fp64"] = run_alone(a, seg, seg.SEG_FP64)
+    out["burst_mixed_over_alone_fp64"] = out["burst_mixed"]["value"] / out["alone_fp64"]["value"]
+    out["burst_mixed_over_alone_mixed"] = out["burst_mixed"]["value"] / out["alone_mixed"]["value"]
+    return out
+
+
 def run_reference(a, rank, ws):
     """The oracle as the reference arm, timed on the host cores (rank 0 only)."""
     import numpy as np
@@ -425,6 +594,8 @@ def main():
         return
     out = run_ours(a, rank, ws, local)
     if rank == 0:
+        if a.serve_requests > 0 and ws == 1:
+            out["serving"] = serving_section(a)
         if not a.no_cpu_baseline and ws >= 1:
             out["cpu_baseline"] = cpu_baseline(a)
         print(json.dumps(out), flush=True)

@@ -81,6 +81,8 @@ typedef struct {
                             by one with a host check per CG iteration (slower; for tools
                             that cannot look inside graphs with conditional nodes) */
   int32_t reserved;      /* must be 0 */
+  int64_t max_steps;     /* the state stops for good after this many steps (0: no limit); unlike
+                            seg_step's nsteps this also holds inside batches and the server */
 } seg_params;
 
 typedef struct {
@@ -176,6 +178,80 @@ seg_status seg_sync(seg_state* s, int64_t* steps_done);
  * scaled by the current normalisation factors; the state must be brought back
  * with stage 3 (or seg_set_u) before seg_step.  Synchronises. */
 seg_status seg_substep(seg_state* s, int32_t stage);
+
+/* --------------------------------------------------------------- batches */
+
+/* Several states advanced together (states of different meshes, m and eps):
+ * every pass of a step of Algorithm 2.2 is one kernel launch over all members,
+ * each member on its own block range, and the members' CG loops run inside one
+ * device-controlled loop that continues while any member iterates.  Members
+ * must share the precision, the lanes-per-row class (padded m: 1-4, 5-8,
+ * 9-16 or 17-32 components in float32; 1-2, 3-4, 5-8, 9-16, 17-32 in float64)
+ * and the padded matrix row width, and be on one device; n <= 32.  A member's
+ * results are bitwise the same as when it is stepped alone.  While a batch
+ * exists its members must not be stepped on their own streams concurrently.
+ * cuda_stream = NULL: the batch's own stream. */
+typedef struct seg_batch seg_batch;
+seg_status seg_batch_create(seg_state* const* states, int32_t n, void* cuda_stream, seg_batch** out);
+
+/* Advance every member by up to nsteps steps (members that meet their stop
+ * rule stay where they are); synchronises and returns the first error status
+ * of any member (see seg_step).  The _async form only enqueues the work. */
+seg_status seg_batch_step(seg_batch* b, int64_t nsteps);
+seg_status seg_batch_step_async(seg_batch* b, int64_t nsteps);
+seg_status seg_batch_sync(seg_batch* b);
+void seg_batch_destroy(seg_batch* b);
+
+/* ----------------------------------------------------------------- serving */
+
+/* A request server with continuous batching: requests (a problem, m, eps,
+ * initial data and parameters) are queued; each tick admits queued requests
+ * in arrival order while their device footprint fits the memory budget,
+ * advances every resident request by steps_per_tick steps -- resident
+ * requests of one class (see seg_batch_create) share one batched launch per
+ * pass, different classes run on different streams and overlap -- and retires
+ * the requests that met their stop rule or step limit (result copied to host
+ * memory, device memory released).  A request's result is bitwise the same as
+ * when its state is stepped alone.  Problems must outlive their requests.
+ * Every request must be able to finish: give it a stop rule (energy_tol >= 0)
+ * or max_steps. */
+typedef struct seg_server seg_server;
+
+typedef struct {
+  uint64_t hbm_budget_bytes;  /* device bytes for resident states; 0: 80% of free memory at creation */
+  int32_t max_resident;       /* 0: no limit other than memory */
+  int32_t steps_per_tick;     /* 0: 16 */
+} seg_server_params;
+
+typedef struct {
+  int32_t phase;           /* 0 queued, 1 running, 2 done, 3 failed */
+  int32_t status;          /* seg_status (why a request failed) */
+  int64_t steps;           /* steps taken */
+  int32_t converged;       /* 1: the stop rule fired; 0: the step limit ended it */
+  int32_t m;
+  int64_t n_vert;
+  double total_energy;     /* total energy at the last stop-rule check */
+  double t_submit;         /* seconds on the server clock (seg_server_clock) */
+  double t_admit;
+  double t_done;
+} seg_request_info;
+
+seg_status seg_server_create(const seg_server_params* opt, seg_server** out);
+/* Queue a request; *id (required) receives its id.  opt as for seg_state_create. */
+seg_status seg_server_submit(seg_server* srv, const seg_problem* p, int32_t m, double eps, seg_init init,
+                             uint64_t seed, const seg_params* opt, int64_t* id);
+/* One scheduling tick (admit, step, retire); running/queued (nullable)
+ * receive the counts after the tick.  Synchronises. */
+seg_status seg_server_tick(seg_server* srv, int32_t* running, int32_t* queued);
+seg_status seg_server_info(seg_server* srv, int64_t id, seg_request_info* out);
+/* Final state u[n_vert * m] (float64, caller's vertex order) of a done request. */
+seg_status seg_server_result(seg_server* srv, int64_t id, double* u);
+/* Seconds since the server was created (host steady clock). */
+double seg_server_clock(const seg_server* srv);
+void seg_server_destroy(seg_server* srv);
+
+/* Device bytes a state of m components on problem p allocates. */
+seg_status seg_state_bytes(const seg_problem* p, int32_t m, uint64_t* bytes);
 
 /* ---------------------------------------------------------------- outputs */
 

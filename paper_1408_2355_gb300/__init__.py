@@ -49,6 +49,9 @@ EXPORTED = [
     "seg_step", "seg_step_async", "seg_sync", "seg_substep", "seg_energy",
     "seg_eigenvalue_estimates", "seg_labels", "seg_get_stats", "seg_last_error",
     "seg_time_kernel", "seg_launch_info", "seg_s_eps_noalloc",
+    "seg_batch_create", "seg_batch_step", "seg_batch_step_async", "seg_batch_sync", "seg_batch_destroy",
+    "seg_server_create", "seg_server_submit", "seg_server_tick", "seg_server_info", "seg_server_result",
+    "seg_server_clock", "seg_server_destroy", "seg_state_bytes",
 ]
 
 
@@ -67,6 +70,7 @@ class seg_params(C.Structure):
         ("energy_tol", C.c_double),
         ("launch_mode", C.c_int32),
         ("reserved", C.c_int32),
+        ("max_steps", C.c_int64),
     ]
 
 
@@ -80,6 +84,29 @@ class seg_stats(C.Structure):
         ("status_bits", C.c_int32),
         ("last_check_total", C.c_double),
         ("checks", C.c_int64),
+    ]
+
+
+class seg_server_params(C.Structure):
+    _fields_ = [
+        ("hbm_budget_bytes", C.c_uint64),
+        ("max_resident", C.c_int32),
+        ("steps_per_tick", C.c_int32),
+    ]
+
+
+class seg_request_info(C.Structure):
+    _fields_ = [
+        ("phase", C.c_int32),
+        ("status", C.c_int32),
+        ("steps", C.c_int64),
+        ("converged", C.c_int32),
+        ("m", C.c_int32),
+        ("n_vert", C.c_int64),
+        ("total_energy", C.c_double),
+        ("t_submit", C.c_double),
+        ("t_admit", C.c_double),
+        ("t_done", C.c_double),
     ]
 
 
@@ -112,12 +139,25 @@ _SIG = {
     "seg_time_kernel": [_vp, _i32, _i32, _vp],
     "seg_launch_info": [_vp, _vp, _vp, _vp, _vp],
     "seg_s_eps_noalloc": [_vp, _i64, _i32, _vp, _vp, _i64, _d, _vp, _vp],
+    "seg_batch_create": [_vp, _i32, _vp, _pp],
+    "seg_batch_step": [_vp, _i64],
+    "seg_batch_step_async": [_vp, _i64],
+    "seg_batch_sync": [_vp],
+    "seg_server_create": [_vp, _pp],
+    "seg_server_submit": [_vp, _vp, _i32, _d, C.c_int, C.c_uint64, _vp, _vp],
+    "seg_server_tick": [_vp, _vp, _vp],
+    "seg_server_info": [_vp, _i64, _vp],
+    "seg_server_result": [_vp, _i64, _vp],
+    "seg_state_bytes": [_vp, _i32, _vp],
 }
 for _name, _args in _SIG.items():
     _f = getattr(lib, _name)
     _f.argtypes = _args
     _f.restype = C.c_int
-for _name in ("seg_mesh_destroy", "seg_problem_destroy", "seg_state_destroy"):
+lib.seg_server_clock.argtypes = [_vp]
+lib.seg_server_clock.restype = C.c_double
+for _name in ("seg_mesh_destroy", "seg_problem_destroy", "seg_state_destroy", "seg_batch_destroy",
+              "seg_server_destroy"):
     getattr(lib, _name).argtypes = [_vp]
     getattr(lib, _name).restype = None
 lib.seg_last_error.argtypes = []
@@ -296,6 +336,95 @@ def seg_sync(state: State) -> int:
     done = C.c_int64()
     _check(lib.seg_sync(state.ptr, C.byref(done)))
     return done.value
+
+
+class Batch(_Handle):
+    _destroy = "seg_batch_destroy"
+
+    def __init__(self, ptr, states):
+        super().__init__(ptr)
+        self.states = list(states)  # keep the members alive
+
+
+def seg_batch_create(states, cuda_stream: int | None = None) -> Batch:
+    arr = (C.c_void_p * len(states))(*[s.ptr for s in states])
+    out = C.c_void_p()
+    _check(lib.seg_batch_create(C.cast(arr, C.c_void_p), len(states),
+                                C.c_void_p(cuda_stream) if cuda_stream else None, C.byref(out)))
+    return Batch(out, states)
+
+
+def seg_batch_step(batch: Batch, nsteps: int, ok_not_converged: bool = False):
+    ok = (SEG_OK, SEG_ERR_NOT_CONVERGED) if ok_not_converged else (SEG_OK,)
+    _check(lib.seg_batch_step(batch.ptr, nsteps), ok)
+
+
+def seg_batch_step_async(batch: Batch, nsteps: int):
+    _check(lib.seg_batch_step_async(batch.ptr, nsteps))
+
+
+def seg_batch_sync(batch: Batch):
+    _check(lib.seg_batch_sync(batch.ptr))
+
+
+def seg_batch_destroy(batch: Batch):
+    batch.close()
+
+
+class Server(_Handle):
+    _destroy = "seg_server_destroy"
+
+    def __init__(self, ptr):
+        super().__init__(ptr)
+        self.problems = []  # problems of submitted requests stay alive with the server
+
+
+def seg_server_create(params: seg_server_params | None = None) -> Server:
+    out = C.c_void_p()
+    _check(lib.seg_server_create(C.byref(params) if params is not None else None, C.byref(out)))
+    return Server(out)
+
+
+def seg_server_submit(server: Server, problem: Problem, m: int, eps: float, init: int = SEG_INIT_UNIFORM,
+                      seed: int = 0, params: seg_params | None = None) -> int:
+    rid = C.c_int64()
+    _check(lib.seg_server_submit(server.ptr, problem.ptr, m, eps, init, seed & 0xFFFFFFFFFFFFFFFF,
+                                 C.byref(params) if params is not None else None, C.byref(rid)))
+    server.problems.append(problem)
+    return rid.value
+
+
+def seg_server_tick(server: Server):
+    running, queued = C.c_int32(), C.c_int32()
+    _check(lib.seg_server_tick(server.ptr, C.byref(running), C.byref(queued)))
+    return running.value, queued.value
+
+
+def seg_server_info(server: Server, rid: int) -> dict:
+    info = seg_request_info()
+    _check(lib.seg_server_info(server.ptr, rid, C.byref(info)))
+    return {k: getattr(info, k) for k, _ in seg_request_info._fields_}
+
+
+def seg_server_result(server: Server, rid: int):
+    info = seg_server_info(server, rid)
+    out = np.empty((info["n_vert"], info["m"]), dtype=np.float64)
+    _check(lib.seg_server_result(server.ptr, rid, _ptr(out)))
+    return out
+
+
+def seg_server_clock(server: Server) -> float:
+    return lib.seg_server_clock(server.ptr)
+
+
+def seg_server_destroy(server: Server):
+    server.close()
+
+
+def seg_state_bytes(problem: Problem, m: int) -> int:
+    b = C.c_uint64()
+    _check(lib.seg_state_bytes(problem.ptr, m, C.byref(b)))
+    return b.value
 
 
 def seg_substep(state: State, stage: int):

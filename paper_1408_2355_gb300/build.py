@@ -23,7 +23,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build", platform.machine())
 LIB = os.path.join(BUILD, "libseg.so")
 
-SOURCES = ["api.cu", "kernels_f32.cu", "kernels_f64.cu", "mesh.cpp", "assemble.cpp", "noalloc.cu"]
+SOURCES = ["api.cu", "kernels_f32.cu", "kernels_f64.cu", "mesh.cpp", "assemble.cpp", "noalloc.cu", "server.cpp"]
 HEADERS = ["seg_internal.h", "kernels.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

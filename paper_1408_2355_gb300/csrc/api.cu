@@ -37,6 +37,7 @@ seg_status fail(seg_status code, const std::string& msg) {
 }  // namespace
 
 void segimpl::set_last_error(const char* msg) { g_err = msg; }
+const char* segimpl::last_error() { return g_err.c_str(); }
 
 struct seg_mesh {
   HostMesh h;
@@ -69,6 +70,7 @@ struct seg_state {
   int cg_maxit = 0;
   long long check_every = 0;
   double energy_tol = 0;
+  long long max_steps = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int launch_mode = 0;
@@ -195,7 +197,8 @@ seg_status direct_step(seg_state* s) {
   seg_status st = launch_row(s, s->ks.start, l);
   if (st == SEG_OK) st = launch_row(s, s->ks.energy_check, l);
   if (st == SEG_OK) st = sync_ctl(s);
-  while (st == SEG_OK && s->hctl->cont && !s->hctl->halted) {
+  while (st == SEG_OK && s->hctl->cont && !s->hctl->halted &&
+         !(s->max_steps > 0 && s->hctl->step >= s->max_steps)) {
     st = launch_row(s, s->ks.cg_a, l);
     if (st == SEG_OK) st = launch_row(s, s->ks.cg_b, l);
     if (st == SEG_OK) st = sync_ctl(s);
@@ -291,6 +294,7 @@ void fill_args(seg_state* s) {
   a.ntri = (int)p->f;
   a.check_every = s->check_every;
   a.energy_tol = s->energy_tol;
+  a.max_steps = s->max_steps;
 }
 
 template <typename T>
@@ -541,6 +545,7 @@ seg_status seg_state_create(const seg_problem* p, int32_t m, double eps, seg_ini
   s->check_every = prm.check_every > 0 ? prm.check_every
                                        : (prm.check_every < 0 ? 0 : std::max<long long>(1, std::llround(0.1 / p->tau)));
   s->energy_tol = prm.energy_tol > 0 ? prm.energy_tol : (prm.energy_tol < 0 ? -1.0 : 1e-6);
+  s->max_steps = prm.max_steps > 0 ? prm.max_steps : 0;
   if (prm.launch_mode != 0 && prm.launch_mode != 1) {
     delete s;
     return fail(SEG_ERR_ARG, "launch_mode must be 0 (graph) or 1 (direct)");
@@ -554,9 +559,9 @@ seg_status seg_state_create(const seg_problem* p, int32_t m, double eps, seg_ini
   }
   {
     // the TMA-staged kernels may need more than the default 48 KiB
-    const void* fns[2] = {s->ks.start, s->ks.cg_a};
-    const unsigned sm[2] = {s->ks.smem_start, s->ks.smem_cg_a};
-    for (int k = 0; k < 2; ++k) {
+    const void* fns[4] = {s->ks.start, s->ks.cg_a, s->ks.b_start, s->ks.b_cg_a};
+    const unsigned sm[4] = {s->ks.smem_start, s->ks.smem_cg_a, s->ks.smem_start, s->ks.smem_cg_a};
+    for (int k = 0; k < 4; ++k) {
       cudaError_t fe = cudaFuncSetAttribute(fns[k], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm[k]);
       if (fe != cudaSuccess) {
         delete s;
@@ -570,8 +575,12 @@ seg_status seg_state_create(const seg_problem* p, int32_t m, double eps, seg_ini
     delete s;
     return fail(SEG_ERR_CUDA, std::string("cudaDeviceGetAttribute: ") + cudaGetErrorString(ce));
   }
-  s->grid = prm.grid_blocks > 0 ? prm.grid_blocks : 2 * nsm;
-  s->grid_e = 4 * nsm;
+  // blocks of at least 256 rows (1024 triangles), at most 2 (4) per SM; the
+  // geometry is part of the state, so results do not depend on whether the
+  // state runs alone or in a batch
+  s->grid = prm.grid_blocks > 0 ? prm.grid_blocks
+                                : (int)std::min<int64_t>(2 * nsm, std::max<int64_t>(1, (p->n + 255) / 256));
+  s->grid_e = (int)std::min<int64_t>(4 * nsm, std::max<int64_t>(1, (p->f + 1023) / 1024));
   if (cuda_stream) {
     s->stream = (cudaStream_t)cuda_stream;
   } else {
@@ -583,7 +592,7 @@ seg_status seg_state_create(const seg_problem* p, int32_t m, double eps, seg_ini
     s->own_stream = true;
   }
   const size_t vbytes = (size_t)p->n * s->ms * vsize(s->prec);
-  const size_t pbytes = (size_t)s->grid * kMaxDots * s->ms * 8;
+  const size_t pbytes = std::max<size_t>((size_t)s->grid * kMaxDots * s->ms, (size_t)s->grid_e) * 8;
   struct {
     void** ptr;
     size_t bytes;
@@ -650,6 +659,32 @@ seg_status seg_state_create(const seg_problem* p, int32_t m, double eps, seg_ini
   }
   s->pending = true;
   *out = s;
+  return SEG_OK;
+}
+
+}  // extern "C"
+
+long long segimpl::state_class_key(const seg_state* s) {
+  return (long long)s->prec | (long long)s->lpr << 4 | (long long)s->p->ell_w << 12 | (long long)s->p->device << 20;
+}
+
+extern "C" {
+
+seg_status seg_state_bytes(const seg_problem* p, int32_t m, uint64_t* bytes) {
+  if (!p || !bytes) return fail(SEG_ERR_ARG, "problem or bytes is NULL");
+  if (m < 1 || m > kMaxCols) return fail(SEG_ERR_ARG, "m must be in [1, 32]");
+  int nsm = 0;
+  SEG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device));
+  const int vw = p->prec == SEG_MIXED_FP32 ? 4 : 2;
+  int lpr = (m + vw - 1) / vw, pw = 1;
+  while (pw < lpr) pw <<= 1;
+  const uint64_t ms = (uint64_t)pw * vw, n = (uint64_t)p->n;
+  const uint64_t grid = std::min<uint64_t>(2 * nsm, std::max<uint64_t>(1, (n + 255) / 256));
+  const uint64_t grid_e = std::min<uint64_t>(4 * nsm, std::max<uint64_t>(1, ((uint64_t)p->f + 1023) / 1024));
+  const uint64_t vbytes = n * ms * vsize(p->prec);
+  const uint64_t pbytes = std::max<uint64_t>(grid * kMaxDots * ms, grid_e) * 8;
+  *bytes = 5 * vbytes + sizeof(DevCtl) + pbytes + std::max<uint64_t>(8, n * m * 8) + 2 * kMaxCols * 8 +
+           std::max<uint64_t>(4, n * 4) + std::max<uint64_t>(4, n);
   return SEG_OK;
 }
 
@@ -771,6 +806,173 @@ seg_status seg_substep(seg_state* s, int32_t stage) {
   st = sync_ctl(s);
   if (st != SEG_OK) return st;
   return status_from_ctl(*s->hctl);
+}
+
+// ---------------------------------------------------------------- batches
+
+}  // extern "C"
+
+struct seg_batch {
+  std::vector<seg_state*> members;
+  seg_precision prec = SEG_FP64;
+  KernelSet ks{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  void* tab = nullptr;  // device KArgs<T>[n]
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphConditionalHandle cond = 0;
+};
+
+namespace {
+
+template <typename T>
+cudaError_t add_batch_node(cudaGraphNode_t* node, cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps,
+                           void* fn, const BatchArgs<T>& b, int threads, unsigned smem) {
+  BatchArgs<T> copy = b;
+  void* args[] = {&copy};
+  cudaKernelNodeParams kp{};
+  kp.func = fn;
+  kp.gridDim = dim3(b.off[b.ninst] > 0 ? b.off[b.ninst] : 1);
+  kp.blockDim = dim3(threads);
+  kp.sharedMemBytes = smem;
+  kp.kernelParams = args;
+  return cudaGraphAddKernelNode(node, g, deps, ndeps, &kp);
+}
+
+template <typename T>
+seg_status build_batch_t(seg_batch* b) {
+  const int n = (int)b->members.size();
+  std::vector<KArgs<T>> tab(n);
+  BatchArgs<T> rows{}, tris{}, vote{};
+  for (int i = 0; i < n; ++i) {
+    seg_state* s = b->members[i];
+    Launch l;
+    l.ignore_halt = 0;
+    l.apply_x = 1;
+    l.apply_ode = 1;
+    l.count_step = 1;
+    tab[i] = make_args<T>(s, l);
+    rows.off[i + 1] = rows.off[i] + s->grid;
+    tris.off[i + 1] = tris.off[i] + s->grid_e;
+  }
+  SEG_CUDA(cudaMalloc(&b->tab, n * sizeof(KArgs<T>)));
+  SEG_CUDA(cudaMemcpy(b->tab, tab.data(), n * sizeof(KArgs<T>), cudaMemcpyHostToDevice));
+  SEG_CUDA(cudaGraphCreate(&b->graph, 0));
+  SEG_CUDA(cudaGraphConditionalHandleCreate(&b->cond, b->graph, 0, cudaGraphCondAssignDefault));
+  for (BatchArgs<T>* x : {&rows, &tris, &vote}) {
+    x->tab = (const KArgs<T>*)b->tab;
+    x->ninst = n;
+    x->cond = (unsigned long long)b->cond;
+  }
+  vote.off[n] = 1;  // one block
+  cudaGraphNode_t n_start, n_energy, n_vote0, n_loop, n_a, n_b, n_vote, n_fin;
+  SEG_CUDA(add_batch_node<T>(&n_start, b->graph, nullptr, 0, b->ks.b_start, rows, kBlockThreads, b->ks.smem_start));
+  SEG_CUDA(add_batch_node<T>(&n_energy, b->graph, &n_start, 1, b->ks.b_energy_check, tris, kBlockThreads, 0));
+  SEG_CUDA(add_batch_node<T>(&n_vote0, b->graph, &n_energy, 1, b->ks.b_vote, vote, kMaxBatch, 0));
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = b->cond;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  SEG_CUDA(cudaGraphAddNode(&n_loop, b->graph, &n_vote0, nullptr, 1, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  SEG_CUDA(add_batch_node<T>(&n_a, body, nullptr, 0, b->ks.b_cg_a, rows, kBlockThreads, b->ks.smem_cg_a));
+  SEG_CUDA(add_batch_node<T>(&n_b, body, &n_a, 1, b->ks.b_cg_b, rows, kBlockThreads, 0));
+  SEG_CUDA(add_batch_node<T>(&n_vote, body, &n_b, 1, b->ks.b_vote, vote, kMaxBatch, 0));
+  SEG_CUDA(add_batch_node<T>(&n_fin, b->graph, &n_loop, 1, b->ks.b_finish, rows, kBlockThreads, 0));
+  SEG_CUDA(cudaGraphInstantiate(&b->exec, b->graph, 0));
+  return SEG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+seg_status seg_batch_create(seg_state* const* states, int32_t n, void* cuda_stream, seg_batch** out) {
+  if (!out) return fail(SEG_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!states || n < 1 || n > kMaxBatch) return fail(SEG_ERR_ARG, "a batch holds 1 to 32 states");
+  seg_state* s0 = states[0];
+  if (!s0) return fail(SEG_ERR_ARG, "state is NULL");
+  for (int i = 0; i < n; ++i) {
+    seg_state* s = states[i];
+    if (!s) return fail(SEG_ERR_ARG, "state is NULL");
+    for (int j = 0; j < i; ++j)
+      if (states[j] == s) return fail(SEG_ERR_ARG, "a state appears twice in the batch");
+    if (s->prec != s0->prec || s->lpr != s0->lpr || s->p->ell_w != s0->p->ell_w || s->p->device != s0->p->device)
+      return fail(SEG_ERR_ARG,
+                  "batch members must share precision, padded component count class, row width and device");
+  }
+  SEG_CUDA(cudaSetDevice(s0->p->device));
+  seg_batch* b = new (std::nothrow) seg_batch;
+  if (!b) return fail(SEG_ERR_NO_MEMORY, "host allocation failed");
+  b->members.assign(states, states + n);
+  b->prec = s0->prec;
+  b->ks = s0->ks;
+  cudaError_t e = cudaSuccess;
+  if (cuda_stream) {
+    b->stream = (cudaStream_t)cuda_stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    b->own_stream = e == cudaSuccess;
+  }
+  seg_status st = e == cudaSuccess ? SEG_OK : fail(SEG_ERR_CUDA, cudaGetErrorString(e));
+  // members' pending work on their own streams must be done first
+  for (int i = 0; i < n && st == SEG_OK; ++i) {
+    e = cudaStreamSynchronize(states[i]->stream);
+    if (e != cudaSuccess) st = fail(SEG_ERR_CUDA, cudaGetErrorString(e));
+  }
+  if (st == SEG_OK) st = b->prec == SEG_MIXED_FP32 ? build_batch_t<float>(b) : build_batch_t<double>(b);
+  if (st != SEG_OK) {
+    seg_batch_destroy(b);
+    return st;
+  }
+  *out = b;
+  return SEG_OK;
+}
+
+seg_status seg_batch_step_async(seg_batch* b, int64_t nsteps) {
+  if (!b) return fail(SEG_ERR_ARG, "batch is NULL");
+  if (nsteps < 0) return fail(SEG_ERR_ARG, "nsteps must be >= 0");
+  SEG_CUDA(cudaSetDevice(b->members[0]->p->device));
+  for (seg_state* s : b->members) {
+    SEG_CUDA(cudaMemcpyAsync(&s->ctl->step_mark, &s->ctl->step, sizeof(long long), cudaMemcpyDeviceToDevice,
+                             b->stream));
+    SEG_CUDA(cudaMemsetAsync(&s->ctl->status, 0, sizeof(int), b->stream));
+  }
+  for (int64_t k = 0; k < nsteps; ++k) SEG_CUDA(cudaGraphLaunch(b->exec, b->stream));
+  if (nsteps > 0)
+    for (seg_state* s : b->members) s->pending = true;
+  return SEG_OK;
+}
+
+seg_status seg_batch_sync(seg_batch* b) {
+  if (!b) return fail(SEG_ERR_ARG, "batch is NULL");
+  for (seg_state* s : b->members)
+    SEG_CUDA(cudaMemcpyAsync(s->hctl, s->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, b->stream));
+  SEG_CUDA(cudaStreamSynchronize(b->stream));
+  for (seg_state* s : b->members) {
+    seg_status st = status_from_ctl(*s->hctl);
+    if (st != SEG_OK) return st;
+  }
+  return SEG_OK;
+}
+
+seg_status seg_batch_step(seg_batch* b, int64_t nsteps) {
+  seg_status st = seg_batch_step_async(b, nsteps);
+  if (st != SEG_OK) return st;
+  return seg_batch_sync(b);
+}
+
+void seg_batch_destroy(seg_batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->tab) cudaFree(b->tab);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b;
 }
 
 // ---------------------------------------------------------------- outputs

@@ -143,7 +143,7 @@ __device__ __forceinline__ void shfl_add(AccD& a, int off) { a.v += __shfl_xor_s
 // block only.  Must be reached by every block of the grid.
 template <typename T, int LPR, int ND>
 __device__ __forceinline__ bool grid_reduce(typename AccOf<T>::type (&acc)[ND][VecW<T>::W],
-                                            const KArgs<T>& a, int slot, double (*tot)[kMaxCols]) {
+                                            const KArgs<T>& a, int slot, double (*tot)[kMaxCols], int vb, int vg) {
   typedef typename AccOf<T>::type Acc;
   typedef typename AccOf<T>::part Part;
   constexpr int VW = VecW<T>::W;
@@ -164,14 +164,14 @@ __device__ __forceinline__ bool grid_reduce(typename AccOf<T>::type (&acc)[ND][V
       for (int v = 0; v < VW; ++v) red[d][warp][cg * VW + v] = to_part(acc[d][v]);
   }
   __syncthreads();
-  const int G = gridDim.x;
+  const int G = vg;
   Part* part = reinterpret_cast<Part*>(a.part);
   for (int t = threadIdx.x; t < ND * a.ms; t += kBlockThreads) {
     const int d = t / a.ms, c = t % a.ms;
     Acc s;
     s.zero();
     for (int w = 0; w < NW; ++w) add_part(s, red[d][w][c]);
-    part[(size_t)(d * a.ms + c) * G + blockIdx.x] = to_part(s);
+    part[(size_t)(d * a.ms + c) * G + vb] = to_part(s);
   }
   __threadfence();
   __syncthreads();
@@ -246,8 +246,8 @@ __device__ __forceinline__ void row_exclusive(const T (&x)[NQ][VecW<T>::W], T (&
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;                 \
   const int rs = lane / LPR, cg = lane % LPR, c0 = cg * VW;                   \
   (void)rs;                                                                   \
-  const int rpb = (a.n + (int)gridDim.x - 1) / (int)gridDim.x;                \
-  const int r0 = blockIdx.x * rpb;                                            \
+  const int rpb = (a.n + vg - 1) / vg;                                        \
+  const int r0 = vb * rpb;                                                    \
   const int r1 = min(a.n, r0 + rpb);
 
 // Padded-ELL row of W entries: column indices (-1 = padding) and values.
@@ -483,11 +483,11 @@ using CgAStage = RowStage<T, LPR, W, 1, 3>;
 // per component  ||X||_M^2, X^T K X, r0.z0  (float-float) and
 // ||M X||_2^2, ||r0||_2^2 (float32 per thread; they only set the tolerance).
 template <typename T, int LPR, int W>
-__global__ void __launch_bounds__(kBlockThreads, 2) k_start(const KArgs<T> a) {
+__device__ __forceinline__ void body_start(const KArgs<T>& a, const int vb, const int vg) {
   typedef typename AccOf<T>::type Acc;
   typedef StartStage<T, LPR, W> Stage;
   DevCtl* ctl = a.ctl;
-  if (ctl->halted && !a.ignore_halt) return;
+  if (state_finished(a, ctl)) return;
   SEG_ROW_SETUP
   extern __shared__ __align__(128) unsigned char dyn_smem[];
   __shared__ __align__(8) unsigned long long bars[NW][2];
@@ -556,7 +556,7 @@ __global__ void __launch_bounds__(kBlockThreads, 2) k_start(const KArgs<T> a) {
     acc[4][v].add_val(rr[v]);
   }
   __shared__ double tot[5][kMaxCols];
-  if (!grid_reduce<T, LPR, 5>(acc, a, kCtrStart, tot)) return;
+  if (!grid_reduce<T, LPR, 5>(acc, a, kCtrStart, tot, vb, vg)) return;
   int act = 0, bad = 0;
   const int c = threadIdx.x;
   if (c < a.ms) {
@@ -594,11 +594,12 @@ __global__ void __launch_bounds__(kBlockThreads, 2) k_start(const KArgs<T> a) {
 //   lagged  x += alpha_{j-1} p_{j-1}  (own row).
 // Padded ELL entries point at the row itself with value 0 (no branches).
 template <typename T, int LPR, int W>
-__global__ void __launch_bounds__(kBlockThreads, 2) k_cg_a(const KArgs<T> a) {
+__device__ __forceinline__ void body_cg_a(const KArgs<T>& a, const int vb, const int vg) {
   typedef typename AccOf<T>::type Acc;
   typedef CgAStage<T, LPR, W> Stage;
   DevCtl* ctl = a.ctl;
-  if (ctl->halted && !a.ignore_halt) return;
+  if (state_finished(a, ctl)) return;
+  if (!ctl->cont) return;  // this instance's CG loop has ended
   SEG_ROW_SETUP
   extern __shared__ __align__(128) unsigned char dyn_smem[];
   __shared__ __align__(8) unsigned long long bars[NW][2];
@@ -662,7 +663,7 @@ __global__ void __launch_bounds__(kBlockThreads, 2) k_cg_a(const KArgs<T> a) {
       });
   if (__syncthreads_or(!ok) && threadIdx.x == 0) report_timeout(ctl);
   __shared__ double tot[1][kMaxCols];
-  if (!grid_reduce<T, LPR, 1>(acc, a, kCtrCgA, tot)) return;
+  if (!grid_reduce<T, LPR, 1>(acc, a, kCtrCgA, tot, vb, vg)) return;
   const int c = threadIdx.x;
   if (c < a.ms) {
     const double pq = tot[0][c];
@@ -695,22 +696,22 @@ __device__ __forceinline__ T tri_coupling(T a0, T a1, T a2, T e00, T e11, T e22,
 // lane group handles TU triangles per iteration (their corner rows are
 // loaded together).
 template <typename T, int LPR>
-__global__ void __launch_bounds__(kBlockThreads, 2) k_energy(const KArgs<T> a) {
+__device__ __forceinline__ void body_energy(const KArgs<T>& a, const int vb, const int vg) {
   typedef typename AccOf<T>::type Acc;
   constexpr int VW = VecW<T>::W;
   constexpr int NW = kBlockThreads / 32;
   constexpr int RPW = 32 / LPR;
   constexpr int TU = 2;
   DevCtl* ctl = a.ctl;
-  if (ctl->halted && !a.ignore_halt) return;
+  if (state_finished(a, ctl)) return;
   if (!a.force) {
     if (a.check_every <= 0) return;
     if (ctl->step % a.check_every != 0) return;
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int rs = lane / LPR, cg = lane % LPR, c0 = cg * VW, lbase = lane - cg;
-  const int tpb = (a.ntri + (int)gridDim.x - 1) / (int)gridDim.x;
-  const int t0 = blockIdx.x * tpb;
+  const int tpb = (a.ntri + (int)vg - 1) / (int)vg;
+  const int t0 = vb * tpb;
   const int t1 = min(a.ntri, t0 + tpb);
   T invn[VW];
 #pragma unroll
@@ -765,7 +766,7 @@ __global__ void __launch_bounds__(kBlockThreads, 2) k_energy(const KArgs<T> a) {
     }
   }
   __shared__ double tot[1][kMaxCols];
-  if (!grid_reduce<T, LPR, 1>(acc, a, kCtrEnergy, tot)) return;
+  if (!grid_reduce<T, LPR, 1>(acc, a, kCtrEnergy, tot, vb, vg)) return;
   if (threadIdx.x < a.ms) ctl->coup[threadIdx.x] = threadIdx.x < a.m ? tot[0][threadIdx.x] : 0.0;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -807,7 +808,7 @@ __global__ void __launch_bounds__(kBlockThreads, 2) k_energy(const KArgs<T> a) {
 // block, which returns true.
 template <typename T>
 __device__ __forceinline__ bool grid_reduce_scalar(typename AccOf<T>::type acc, DevCtl* ctl, void* partv, int slot,
-                                                   double* tot) {
+                                                   double* tot, int vb, int vg) {
   typedef typename AccOf<T>::type Acc;
   typedef typename AccOf<T>::part Part;
   constexpr int NW = kBlockThreads / 32;
@@ -818,13 +819,13 @@ __device__ __forceinline__ bool grid_reduce_scalar(typename AccOf<T>::type acc, 
   __shared__ unsigned int ticket;
   if (lane == 0) red[warp] = to_part(acc);
   __syncthreads();
-  const int G = gridDim.x;
+  const int G = vg;
   Part* part = reinterpret_cast<Part*>(partv);
   if (threadIdx.x == 0) {
     Acc s;
     s.zero();
     for (int w = 0; w < NW; ++w) add_part(s, red[w]);
-    part[blockIdx.x] = to_part(s);
+    part[vb] = to_part(s);
   }
   __threadfence();
   __syncthreads();
@@ -860,12 +861,12 @@ constexpr double kQuadW2 = 0.10995174365532179;
 // (non-negative terms only, no cancellation).  Components are visited in
 // chunks of VW so that only one chunk of the three corner rows is live.
 template <typename T, int LPR>
-__global__ void __launch_bounds__(kBlockThreads) k_energy_check(const KArgs<T> a) {
+__device__ __forceinline__ void body_energy_check(const KArgs<T>& a, const int vb, const int vg) {
   typedef typename AccOf<T>::type Acc;
   constexpr int VW = VecW<T>::W;
   constexpr int MS = LPR * VW;
   DevCtl* ctl = a.ctl;
-  if (ctl->halted && !a.ignore_halt) return;
+  if (state_finished(a, ctl)) return;
   if (!a.force) {
     if (a.check_every <= 0) return;
     if (ctl->step % a.check_every != 0) return;
@@ -878,7 +879,7 @@ __global__ void __launch_bounds__(kBlockThreads) k_energy_check(const KArgs<T> a
   const unsigned ms = MS;
   Acc acc;
   acc.zero();
-  for (int t = blockIdx.x * kBlockThreads + threadIdx.x; t < a.ntri; t += gridDim.x * kBlockThreads) {
+  for (int t = vb * kBlockThreads + threadIdx.x; t < a.ntri; t += vg * kBlockThreads) {
     const int* tr = a.tri + 3 * (size_t)t;
     const unsigned z0 = __ldg(tr) * ms, z1 = __ldg(tr + 1) * ms, z2 = __ldg(tr + 2) * ms;
     const T area = __ldg(a.tarea + t);
@@ -917,7 +918,7 @@ __global__ void __launch_bounds__(kBlockThreads) k_energy_check(const KArgs<T> a
     acc.add_val(st);
   }
   __shared__ double tot;
-  if (!grid_reduce_scalar<T>(acc, ctl, a.part, kCtrEnergy, &tot)) return;
+  if (!grid_reduce_scalar<T>(acc, ctl, a.part, kCtrEnergy, &tot, vb, vg)) return;
   if (threadIdx.x == 0) {
     double D = 0.0;
     for (int c = 0; c < a.m; ++c) D += ctl->lam[c];
@@ -957,15 +958,16 @@ constexpr int kStreamRows = 4;
 // r_j = D z_j; per component r_j.z_j (float-float) and ||r_j||^2 (float32
 // per thread, tolerance only); convergence test and beta for iteration j+1.
 template <typename T, int LPR>
-__global__ void __launch_bounds__(kBlockThreads, 2) k_cg_b(const KArgs<T> a) {
+__device__ __forceinline__ void body_cg_b(const KArgs<T>& a, const int vb, const int vg) {
   typedef typename AccOf<T>::type Acc;
   constexpr int RU = kStreamRows;
   DevCtl* ctl = a.ctl;
-  if (ctl->halted && !a.ignore_halt) {
+  if (state_finished(a, ctl)) {
     // a kernel of this iteration halted the run: end the CG loop
-    if (a.set_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(a.cond, 0);
+    if (a.set_cond && vb == 0 && threadIdx.x == 0) cudaGraphSetConditional(a.cond, 0);
     return;
   }
+  if (!ctl->cont) return;  // this instance's CG loop has ended
   SEG_ROW_SETUP
   const int it = ctl->it;
   const unsigned ms = a.ms;
@@ -1014,7 +1016,7 @@ __global__ void __launch_bounds__(kBlockThreads, 2) k_cg_b(const KArgs<T> a) {
 #pragma unroll
   for (int v = 0; v < VW; ++v) acc[1][v].add_val(rr[v]);
   __shared__ double tot[2][kMaxCols];
-  if (!grid_reduce<T, LPR, 2>(acc, a, kCtrCgB, tot)) return;
+  if (!grid_reduce<T, LPR, 2>(acc, a, kCtrCgB, tot, vb, vg)) return;
   int act = 0, bad = 0;
   const int c = threadIdx.x;
   if (c < a.ms) {
@@ -1048,10 +1050,10 @@ __global__ void __launch_bounds__(kBlockThreads, 2) k_cg_b(const KArgs<T> a) {
 // exact solution of the nodal ODE of step 2 (Jacobi form):
 //   u~ = x * inv_n,  u^_i = u~_i exp(-(2 tau/eps^2) sum_{j != i} u~_j^2).
 template <typename T, int LPR>
-__global__ void __launch_bounds__(kBlockThreads, 2) k_finish(const KArgs<T> a) {
+__device__ __forceinline__ void body_finish(const KArgs<T>& a, const int vb, const int vg) {
   constexpr int RU = kStreamRows;
   DevCtl* ctl = a.ctl;
-  if (ctl->halted && !a.ignore_halt) return;
+  if (state_finished(a, ctl)) return;
   SEG_ROW_SETUP
   const int lbase = lane - cg;
   const int it = ctl->it;
@@ -1095,12 +1097,60 @@ __global__ void __launch_bounds__(kBlockThreads, 2) k_finish(const KArgs<T> a) {
       if ((int)row < r1) st(a.X + (row * ms + c0), x[u]);
     }
   }
-  if (a.count_step && blockIdx.x == 0 && threadIdx.x == 0) {
+  if (a.count_step && vb == 0 && threadIdx.x == 0) {
     ctl->step += 1;
     ctl->cg_last = it;
     ctl->cg_total += it;
     if (it > ctl->cg_max) ctl->cg_max = it;
   }
+}
+
+
+// ------------------------------------------------- kernels and batch kernels
+
+// One launch per pass: the single-instance kernels run a body over the whole
+// grid; the batch kernels split the grid into per-instance block ranges
+// [off[i], off[i+1]) and run instance i's body on its range, so one launch
+// advances every instance of a batch.
+template <typename T>
+__device__ __forceinline__ int batch_slot(const BatchArgs<T>& b) {
+  int i = 0;
+  while (i + 1 < b.ninst && (int)blockIdx.x >= b.off[i + 1]) ++i;
+  return i;
+}
+
+#define SEG_DEFINE_PASS(NAME, MINB, TPL, ...)                                                           \
+  TPL __global__ void __launch_bounds__(kBlockThreads, MINB) k_##NAME(const KArgs<T> a) {           \
+    body_##NAME<__VA_ARGS__>(a, blockIdx.x, gridDim.x);                                             \
+  }                                                                                                 \
+  TPL __global__ void __launch_bounds__(kBlockThreads, MINB) kb_##NAME(const BatchArgs<T> b) {         \
+    const int i = batch_slot(b);                                                                    \
+    const KArgs<T> a = b.tab[i];                                                                    \
+    body_##NAME<__VA_ARGS__>(a, (int)blockIdx.x - b.off[i], b.off[i + 1] - b.off[i]);               \
+  }
+
+#define SEG_TPL_W template <typename T, int LPR, int W>
+#define SEG_TPL template <typename T, int LPR>
+SEG_DEFINE_PASS(start, 2, SEG_TPL_W, T, LPR, W)
+SEG_DEFINE_PASS(cg_a, 2, SEG_TPL_W, T, LPR, W)
+SEG_DEFINE_PASS(cg_b, 2, SEG_TPL, T, LPR)
+SEG_DEFINE_PASS(finish, 2, SEG_TPL, T, LPR)
+SEG_DEFINE_PASS(energy, 2, SEG_TPL, T, LPR)
+SEG_DEFINE_PASS(energy_check, 4, SEG_TPL, T, LPR)
+#undef SEG_TPL
+#undef SEG_TPL_W
+#undef SEG_DEFINE_PASS
+
+// Condition of a batch's CG loop: continue while any instance is iterating.
+template <typename T>
+__global__ void k_batch_vote(const BatchArgs<T> b) {
+  int go = 0;
+  if ((int)threadIdx.x < b.ninst) {
+    const KArgs<T>& a = b.tab[threadIdx.x];
+    go = (a.ctl->cont && !state_finished(a, a.ctl)) ? 1 : 0;
+  }
+  const int any = __syncthreads_or(go);
+  if (threadIdx.x == 0) cudaGraphSetConditional(b.cond, any);
 }
 
 // ------------------------------------------------------- auxiliary kernels
@@ -1192,6 +1242,12 @@ bool fill_kernels(KernelSet* ks) {
   ks->scatter_in = (void*)k_scatter_in<T>;
   ks->gather_out = (void*)k_gather_out<T>;
   ks->labels = (void*)k_labels<T>;
+  ks->b_start = (void*)kb_start<T, LPR, W>;
+  ks->b_cg_a = (void*)kb_cg_a<T, LPR, W>;
+  ks->b_cg_b = (void*)kb_cg_b<T, LPR>;
+  ks->b_finish = (void*)kb_finish<T, LPR>;
+  ks->b_energy_check = (void*)kb_energy_check<T, LPR>;
+  ks->b_vote = (void*)k_batch_vote<T>;
   ks->smem_start = row_stage_smem<StartStage<T, LPR, W>>();
   ks->smem_cg_a = row_stage_smem<CgAStage<T, LPR, W>>();
   return true;

@@ -90,6 +90,27 @@ struct KArgs {
   int apply_ode;   // finish pass: apply the nodal segregation ODE
   int count_step;  // finish pass: increment the step counter
   int ignore_halt; // run even if the control block is halted (direct calls)
+  long long max_steps;  // > 0: the state is finished once step >= max_steps
+};
+
+// True if a step pass must not touch this state: it halted (stop rule or
+// error) or reached its step limit.  Every block reads the same values, so
+// the decision is uniform over the grid.
+template <typename T>
+__device__ __forceinline__ bool state_finished(const KArgs<T>& a, const DevCtl* ctl) {
+  if (a.ignore_halt) return false;
+  return ctl->halted != 0 || (a.max_steps > 0 && ctl->step >= a.max_steps);
+}
+
+// Arguments of a batched launch: instance i owns blocks [off[i], off[i+1])
+// and runs with the arguments tab[i] (device memory).
+constexpr int kMaxBatch = 32;
+template <typename T>
+struct BatchArgs {
+  const KArgs<T>* tab;
+  int ninst;
+  int off[kMaxBatch + 1];
+  unsigned long long cond;  // conditional handle of the batch's CG loop
 };
 
 // Function table of one (precision, lanes-per-row) specialisation.
@@ -104,6 +125,12 @@ struct KernelSet {
   void* scatter_in;   // (args, src, perm)
   void* gather_out;   // (args, dst, iperm)
   void* labels;       // (args, am, vp, iperm)
+  void* b_start;        // batched passes (BatchArgs)
+  void* b_cg_a;
+  void* b_cg_b;
+  void* b_finish;
+  void* b_energy_check;
+  void* b_vote;         // one block: the batch's CG loop condition
   unsigned smem_start;  // dynamic shared memory of k_start (bytes)
   unsigned smem_cg_a;   // dynamic shared memory of k_cg_a (bytes)
 };
@@ -113,6 +140,11 @@ bool get_kernels_f64(int lpr, int ell_w, KernelSet* ks);
 
 // Record the message returned by seg_last_error() on this thread.
 void set_last_error(const char* msg);
+const char* last_error();
+
+// Key equal for states that may share a batch (precision, lanes per row,
+// padded matrix row width, device).
+long long state_class_key(const seg_state* s);
 
 // Host-side mesh and assembly (mesh.cpp / assemble.cpp).
 struct HostMesh {

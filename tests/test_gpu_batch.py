@@ -1,0 +1,89 @@
+"""Batched stepping: several states (different meshes, m, eps) advanced with
+one launch per pass.  Each member's result must be bitwise the same as the
+same state stepped alone, and the two-instance torus + ellipsoid workload
+must match the oracle."""
+
+import numpy as np
+import pytest
+
+import workload as w
+from oracle import seg_oracle as o
+from tests.gpu_helpers import lib, make_state, rel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def seg():
+    return lib()
+
+
+def _members(seg, prec):
+    specs = [
+        (w.icosphere(3), 5, 0.05, 1e-3, 11),
+        (w.torus(40, 20, 1.0, 0.4), 6, 0.08, 1e-3, 12),
+        (w.ellipsoid(4, 1.0, 0.8, 0.6), 7, 0.03, 5e-4, 13),
+        (w.icosphere(2), 6, 0.3, 1e-2, 14),  # constant data: its stop rule fires at step 10
+    ]
+    states = []
+    for (xyz, tri), m, eps, tau, seed in specs:
+        st = make_state(seg, xyz, tri, tau, m, eps, prec, seed=seed, check_every=10,
+                        energy_tol=1e-8 if prec == 0 else 1e-5)
+        if seed == 14:
+            seg.seg_set_u(st, np.full((xyz.shape[0], m), 1.0))
+        states.append(st)
+    return states
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_batch_members_equal_alone(seg, prec):
+    steps = 30
+    alone = _members(seg, prec)
+    done_alone = [seg.seg_step(s, steps) for s in alone]
+    assert done_alone[3] == 10 and done_alone[0] == steps
+    batched = _members(seg, prec)
+    b = seg.seg_batch_create(batched)
+    seg.seg_batch_step(b, steps)
+    for sa, sb in zip(alone, batched):
+        assert np.array_equal(seg.seg_get_u(sa), seg.seg_get_u(sb))
+        ta, tb = seg.seg_get_stats(sa), seg.seg_get_stats(sb)
+        for k in ("steps", "cg_iterations", "cg_max", "converged", "checks"):
+            assert ta[k] == tb[k], k
+        assert ta["last_check_total"] == tb["last_check_total"]
+    # members remain usable on their own after the batch
+    seg.seg_batch_destroy(b)
+    seg.seg_step(batched[0], 2)
+    seg.seg_step(alone[0], 2)
+    assert np.array_equal(seg.seg_get_u(alone[0]), seg.seg_get_u(batched[0]))
+
+
+def test_batch_rejects_mixed_classes(seg):
+    xyz, tri = w.icosphere(2)
+    a = make_state(seg, xyz, tri, 1e-3, 3, 0.1, 1)
+    c = make_state(seg, xyz, tri, 1e-3, 16, 0.1, 1)
+    d = make_state(seg, xyz, tri, 1e-3, 3, 0.1, 0)
+    for pair in ([a, c], [a, d], [a, a]):
+        with pytest.raises(seg.SegError) as e:
+            seg.seg_batch_create(pair)
+        assert e.value.status == seg.SEG_ERR_ARG
+
+
+@pytest.mark.parametrize("m", [6, 12])
+def test_torus_and_ellipsoid_batched_against_oracle(seg, m):
+    """Torus R = 1, r = 0.4 on a 1024 x 512 grid and the level-8 ellipsoid
+    (1, 0.8, 0.6), eps = 1e-3, tau = 5e-6, mixed precision, two instances in
+    one launch per pass."""
+    meshes = [w.torus(1024, 512, 1.0, 0.4), w.ellipsoid(8, 1.0, 0.8, 0.6)]
+    eps, tau, steps = 1e-3, 5e-6, 2
+    states = [make_state(seg, xyz, tri, tau, m, eps, 1, seed=1237 + k, check_every=1, energy_tol=-1.0)
+              for k, (xyz, tri) in enumerate(meshes)]
+    b = seg.seg_batch_create(states)
+    seg.seg_batch_step(b, steps)
+    for k, ((xyz, tri), st) in enumerate(zip(meshes, states)):
+        M, K = o.assemble(xyz, tri)
+        U = o.initial_state(M, w.uniform01(1237 + k, xyz.shape[0], m))
+        for _ in range(steps):
+            U = o.step(M, K, tau, eps, U)
+        Ug = seg.seg_get_u(st)
+        assert np.abs(Ug - U).max() <= 1e-4 * np.abs(U).max()
+        assert rel(seg.seg_energy(st)["total"], o.energy(xyz, tri, K, U, eps)["total"]) <= 1e-5
