@@ -54,12 +54,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=64, help="0 disables the serving run")
+    ap.add_argument("--serve-requests", type=int, default=256, help="0 disables the serving run")
     ap.add_argument("--serve-compare", type=int, default=24)
-    ap.add_argument("--serve-rate", type=float, default=8.0)
+    ap.add_argument("--serve-rate", type=float, default=20.0)
     ap.add_argument("--serve-check-every", type=int, default=25)
-    ap.add_argument("--serve-tol", type=float, default=1e-2)
-    ap.add_argument("--serve-max-steps", type=int, default=400)
+    ap.add_argument("--serve-tol", type=float, default=1e-3)
+    ap.add_argument("--serve-max-steps", type=int, default=300)
     ap.add_argument("--serve-quantum", type=int, default=16)
     ap.add_argument("--cpu-sample-seconds", type=float, default=20.0)
     ap.add_argument("--reference-budget-seconds", type=float, default=150.0)
@@ -404,37 +404,31 @@ def _serve_mesh(spec):
 def serve_stream(a):
     """The seeded request mix of the serving benchmark.
 
-    Each request picks a mesh from SERVE_MESHES, m uniform in {2..24} and one
-    of 4 interface widths eps = c h (h the mesh's mean edge length, c in
-    {1, 1.41, 2, 2.83}) with tau = 5 eps^2, so that the (mesh, tau) problems
-    are assembled once, before the stream starts, and shared.  Arrival times
-    are a Poisson process of rate --serve-rate.
+    Each request picks a mesh from SERVE_MESHES, m uniform in {2..24} and eps
+    log-uniform in [1e-3, 1e-2], drawn from 8 geometric levels so that the
+    (mesh, tau) problems are assembled once, before the stream starts, and
+    shared; tau = eps^2.  Arrival times are a Poisson process of rate
+    --serve-rate.
     """
     import numpy as np
 
     rng = np.random.default_rng(a.seed + 5)
     arrivals = np.cumsum(rng.exponential(1.0 / a.serve_rate, a.serve_requests))
-    reqs = [(int(rng.integers(len(SERVE_MESHES))), int(rng.integers(2, 25)), int(rng.integers(4)))
+    reqs = [(int(rng.integers(len(SERVE_MESHES))), int(rng.integers(2, 25)), int(rng.integers(8)))
             for _ in range(a.serve_requests)]
     return arrivals, reqs
 
 
 def serve_problems(seg, reqs, prec):
-    """{(mesh index, width index): (problem, eps)} for the requests' pairs."""
-    import numpy as np
-
+    """{(mesh index, eps level): (problem, eps)} for the requests' pairs."""
     problems, meshes = {}, {}
     for mi, _, ci in reqs:
         if (mi, ci) in problems:
             continue
         if mi not in meshes:
-            xyz, tri = _serve_mesh(SERVE_MESHES[mi])
-            e = np.concatenate([tri[:, [0, 1]], tri[:, [1, 2]], tri[:, [2, 0]]])
-            h = float(np.linalg.norm(xyz[e[:, 0]] - xyz[e[:, 1]], axis=1).mean())
-            meshes[mi] = (seg.seg_create_mesh(xyz, tri), h)
-        mesh, h = meshes[mi]
-        eps = h * 2.0 ** (ci / 2)
-        problems[(mi, ci)] = (seg.seg_assemble(mesh, 5 * eps * eps, prec), eps)
+            meshes[mi] = seg.seg_create_mesh(*_serve_mesh(SERVE_MESHES[mi]))
+        eps = 1e-3 * 10.0 ** (ci / 7)
+        problems[(mi, ci)] = (seg.seg_assemble(meshes[mi], eps * eps, prec), eps)
     return problems
 
 
@@ -535,7 +529,7 @@ def serving_section(a):
 
     out = {"requests": a.serve_requests, "arrival_rate_per_s": a.serve_rate,
            "mix": "meshes " + ", ".join("-".join(map(str, s)) for s in SERVE_MESHES)
-                  + "; m ~ U{2..24}; eps = c h, c in {1, 1.41, 2, 2.83}, h mean edge length; tau = 5 eps^2",
+                  + "; m ~ U{2..24}; eps log-uniform in [1e-3, 1e-2] on 8 levels; tau = eps^2",
            "compared_requests": a.serve_compare,
            "stop_rule": {"check_every": a.serve_check_every, "energy_tol": a.serve_tol,
                          "max_steps": a.serve_max_steps},
