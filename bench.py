@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch geometry")
     ap.add_argument("--serve-requests", type=int, default=256, help="0 disables the serving run")
     ap.add_argument("--serve-compare", type=int, default=24)
     ap.add_argument("--serve-rate", type=float, default=20.0)
@@ -252,6 +253,8 @@ def run_ours(a, rank, ws, local):
     mesh = seg.seg_create_mesh(xyz, tri)
     stream = torch.cuda.Stream()
 
+    tunes = {}
+
     def make(prec):
         prob = seg.seg_assemble(mesh, a.tau, prec)
         prm = seg.seg_params()
@@ -259,6 +262,9 @@ def run_ours(a, rank, ws, local):
         prm.energy_tol = -1.0    # ... but never stop: time exactly K steps
         prm.launch_mode = 1 if a.launch_mode == "direct" else 0
         st = seg.seg_state_create(prob, a.m, a.eps, seg.SEG_INIT_UNIFORM, a.seed, prm, stream.cuda_stream)
+        if not a.no_autotune:  # launch geometry by measurement, after 3 steps (setup, not timed)
+            seg.seg_step(st, 3)
+            tunes[prec] = seg.seg_autotune(st, 10)
         return prob, st
 
     def timed(st, K, W):
@@ -329,6 +335,7 @@ def run_ours(a, rank, ws, local):
             "energy_every_step": True,
             "l2": "inputs larger than L2: 5 state vectors x 42 MB + 76 MB of CSR > 129 MB L2",
             "grid_blocks": li["grid_blocks"],
+            "autotune": tunes.get(seg.SEG_MIXED_FP32),
             "launch_mode": a.launch_mode,
             "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
         },
@@ -382,7 +389,8 @@ def run_ours(a, rank, ws, local):
         ms64 = max_over_ranks(ms64, ws)
         out["fp64"] = {"value": ws * n * a.m * k64 / (ms64 / 1e3), "unit": "DoF-steps/s", "steps": k64,
                        "ms_per_step": ms64 / k64,
-                       "cg_iterations_per_step": (s1["cg_iterations"] - s0["cg_iterations"]) / k64}
+                       "cg_iterations_per_step": (s1["cg_iterations"] - s0["cg_iterations"]) / k64,
+                       "grid_blocks": seg.seg_launch_info(st64)["grid_blocks"], "autotune": tunes.get(seg.SEG_FP64)}
         out["mixed_over_fp64"] = out["value"] / out["fp64"]["value"]
     return out
 

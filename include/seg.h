@@ -50,7 +50,7 @@ typedef enum {
   SEG_ERR_NO_MEMORY = -4,      /* host or device allocation failed */
   SEG_ERR_NOT_CONVERGED = -5,  /* a step-1 solve reached cg_maxit before cg_rtol */
   SEG_ERR_NONFINITE = -6,      /* a norm or energy became NaN/Inf or a component vanished */
-  SEG_ERR_TIMEOUT = -7,        /* reserved: a bounded device wait gave up */
+  SEG_ERR_TIMEOUT = -7,        /* a bounded device wait for staged data gave up; the run was halted */
   SEG_ERR_UNSUPPORTED = -8     /* configuration outside the supported range (e.g. m > 32) */
 } seg_status;
 
@@ -71,7 +71,7 @@ typedef struct {
   double cg_rtol;        /* step-1 CG stops at ||r||_2 <= cg_rtol ||M u||_2 per component;
                             default 1e-12 (SEG_FP64), 1e-7 (SEG_MIXED_FP32) */
   int32_t cg_maxit;      /* default 1000 */
-  int32_t grid_blocks;   /* CUDA blocks of the row kernels; default 2 per SM */
+  int32_t grid_blocks;   /* CUDA blocks of the row kernels (<= 2048); default 3 per SM */
   int64_t check_every;   /* Sec. 2.2 stop rule cadence M_tau; default round(0.1 / tau);
                             the energy check is skipped entirely if set < 0 */
   double energy_tol;     /* stop when |total_k - total_{k - M_tau}| < energy_tol; default
@@ -91,7 +91,7 @@ typedef struct {
   int32_t cg_last;          /* CG iterations of the last completed step */
   int32_t cg_max;           /* largest per-step CG iteration count */
   int32_t converged;        /* 1 once the Sec. 2.2 stop rule fired */
-  int32_t status_bits;      /* bit0: a solve hit cg_maxit; bit1: non-finite norm/energy */
+  int32_t status_bits;      /* bit0: a solve hit cg_maxit; bit1: non-finite norm/energy; bit2: timeout */
   double last_check_total;  /* total energy at the latest stop-rule check */
   int64_t checks;           /* number of stop-rule checks evaluated */
 } seg_stats;
@@ -294,6 +294,39 @@ seg_status seg_time_kernel(seg_state* s, int32_t which, int32_t reps, double* ms
 /* Launch geometry of the row kernels of a state (nullable outputs). */
 seg_status seg_launch_info(seg_state* s, int32_t* grid_blocks, int32_t* block_threads,
                            int32_t* lanes_per_row, int32_t* padded_m);
+
+/* ---------------------------------------------------------------- autotuner */
+
+#define SEG_TUNE_MAX 8
+typedef struct {
+  int32_t grid_blocks;         /* chosen blocks of the row kernels */
+  int32_t grid_blocks_energy;  /* chosen blocks of the energy-check kernel */
+  int32_t n_candidates;        /* row grids tried (first SEG_TUNE_MAX listed) */
+  int32_t reserved;
+  int32_t cand_grid[SEG_TUNE_MAX];
+  double cand_ms[SEG_TUNE_MAX]; /* modelled step time of each row grid, ms */
+  double ms_model;             /* modelled step time of the chosen row grid */
+  double ms_energy;            /* one energy check with the chosen grid, ms */
+  double cg_weight;            /* CG iterations per step used in the model */
+} seg_tune_result;
+
+/* Pick the launch geometry of a state by measurement (no counterpart in the
+ * paper; the arithmetic of Algorithm 2.2 is unchanged).  The row grid (and
+ * with it the block of rows each CUDA block owns) is chosen among 1 ..
+ * 3 blocks per SM and 2 or 4 waves of 3 blocks per SM (at most one block per
+ * 256 rows, at most 2048 blocks), by the modelled step time
+ *     t_start + k (t_cgA + t_cgB) + t_finish,
+ * each t the mean of `reps` (<= 0: 10) timed launches and k the state's CG
+ * iterations per step so far (8 before its first step); the energy-check grid
+ * among 1 .. 4 blocks per SM and 2 or 4 waves of 4 blocks per SM by its own
+ * time.  The state's data and
+ * counters are saved before and restored bitwise after the timing launches,
+ * and its step graph is rebuilt with the chosen geometry.  Later steps give
+ * the same results as without tuning up to the summation order of the
+ * per-block partial inner products.  A batch built from the state earlier
+ * keeps the geometry it was built with.  Needs device memory for one copy of
+ * the state vector (SEG_ERR_NO_MEMORY otherwise).  Synchronises. */
+seg_status seg_autotune(seg_state* s, int32_t reps, seg_tune_result* out);
 
 /* ------------------------------------------------------- allocation-free call */
 

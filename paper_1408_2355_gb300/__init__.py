@@ -48,7 +48,7 @@ EXPORTED = [
     "seg_problem_destroy", "seg_state_create", "seg_state_destroy", "seg_set_u", "seg_get_u",
     "seg_step", "seg_step_async", "seg_sync", "seg_substep", "seg_energy",
     "seg_eigenvalue_estimates", "seg_labels", "seg_get_stats", "seg_last_error",
-    "seg_time_kernel", "seg_launch_info", "seg_s_eps_noalloc",
+    "seg_time_kernel", "seg_launch_info", "seg_autotune", "seg_s_eps_noalloc",
     "seg_batch_create", "seg_batch_step", "seg_batch_step_async", "seg_batch_sync", "seg_batch_destroy",
     "seg_server_create", "seg_server_submit", "seg_server_tick", "seg_server_info", "seg_server_result",
     "seg_server_clock", "seg_server_destroy", "seg_state_bytes",
@@ -95,6 +95,23 @@ class seg_server_params(C.Structure):
     ]
 
 
+SEG_TUNE_MAX = 8
+
+
+class seg_tune_result(C.Structure):
+    _fields_ = [
+        ("grid_blocks", C.c_int32),
+        ("grid_blocks_energy", C.c_int32),
+        ("n_candidates", C.c_int32),
+        ("reserved", C.c_int32),
+        ("cand_grid", C.c_int32 * SEG_TUNE_MAX),
+        ("cand_ms", C.c_double * SEG_TUNE_MAX),
+        ("ms_model", C.c_double),
+        ("ms_energy", C.c_double),
+        ("cg_weight", C.c_double),
+    ]
+
+
 class seg_request_info(C.Structure):
     _fields_ = [
         ("phase", C.c_int32),
@@ -138,6 +155,7 @@ _SIG = {
     "seg_get_stats": [_vp, _vp],
     "seg_time_kernel": [_vp, _i32, _i32, _vp],
     "seg_launch_info": [_vp, _vp, _vp, _vp, _vp],
+    "seg_autotune": [_vp, _i32, _vp],
     "seg_s_eps_noalloc": [_vp, _i64, _i32, _vp, _vp, _i64, _d, _vp, _vp],
     "seg_batch_create": [_vp, _i32, _vp, _pp],
     "seg_batch_step": [_vp, _i64],
@@ -468,6 +486,15 @@ def seg_launch_info(state: State) -> dict:
     g, b, l, p = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
     _check(lib.seg_launch_info(state.ptr, C.byref(g), C.byref(b), C.byref(l), C.byref(p)))
     return {"grid_blocks": g.value, "block_threads": b.value, "lanes_per_row": l.value, "padded_m": p.value}
+
+
+def seg_autotune(state: State, reps: int = 10) -> dict:
+    r = seg_tune_result()
+    _check(lib.seg_autotune(state.ptr, reps, C.byref(r)))
+    k = r.n_candidates
+    return {"grid_blocks": r.grid_blocks, "grid_blocks_energy": r.grid_blocks_energy,
+            "candidates": [(r.cand_grid[i], r.cand_ms[i]) for i in range(k)], "ms_model": r.ms_model,
+            "ms_energy": r.ms_energy, "cg_weight": r.cg_weight}
 
 
 def seg_s_eps_noalloc(u, xyz, tri, eps: float, out, cuda_stream: int | None = None):

@@ -76,6 +76,8 @@ struct seg_state {
   int launch_mode = 0;
   int grid = 0;     // blocks of the row kernels
   int grid_e = 0;   // blocks of the S_eps check kernel
+  int grid_cap = 0;    // the partial-sum buffer holds this many row blocks
+  int grid_e_cap = 0;  // ... and this many triangle blocks
   void* X = nullptr;
   void* Z = nullptr;        // preconditioned residual
   void* P0 = nullptr;       // search directions, ping-pong
@@ -101,6 +103,15 @@ struct seg_state {
 namespace {
 
 size_t vsize(seg_precision p) { return p == SEG_MIXED_FP32 ? sizeof(float) : sizeof(double); }
+
+// Bytes of the partial-sum buffer: up to kMaxDots * ms sums over `grid` row
+// blocks or one sum over `grid_e` triangle blocks, each followed by its
+// per-group-of-32 level (8-byte parts).
+size_t partial_bytes(int ms, int grid, int grid_e) {
+  const size_t rows = (size_t)kMaxDots * ms * (grid + (grid + 31) / 32);
+  const size_t tris = (size_t)grid_e + (grid_e + 31) / 32;
+  return std::max(rows, tris) * 8;
+}
 
 template <typename T>
 KArgs<T>& args_of(seg_state* s);
@@ -209,6 +220,39 @@ seg_status direct_step(seg_state* s) {
   f.count_step = 1;
   if (st == SEG_OK) st = launch_row(s, s->ks.finish, f);
   return st;
+}
+
+// Mean duration of `reps` back-to-back launches of hot-path kernel `which`
+// (0 start, 1 CG A, 2 CG B, 3 finish, 4 energy check, 5 energy) on the
+// state's buffers, after one warm-up launch.
+seg_status time_launches(seg_state* s, int which, int reps, double* ms_per_launch) {
+  void* fns[] = {s->ks.start, s->ks.cg_a, s->ks.cg_b, s->ks.finish, s->ks.energy_check, s->ks.energy};
+  Launch l;
+  l.force = 1;
+  l.apply_x = 1;
+  l.apply_ode = 1;
+  cudaEvent_t e0, e1;
+  SEG_CUDA(cudaEventCreate(&e0));
+  cudaError_t ce = cudaEventCreate(&e1);
+  if (ce != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(SEG_ERR_CUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(ce));
+  }
+  seg_status st = launch_row(s, fns[which], l);  // warm-up
+  if (st == SEG_OK) {
+    cudaEventRecord(e0, s->stream);
+    for (int r = 0; r < reps && st == SEG_OK; ++r) st = launch_row(s, fns[which], l);
+    cudaEventRecord(e1, s->stream);
+  }
+  ce = cudaEventSynchronize(e1);
+  float ms = 0;
+  if (st == SEG_OK && ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != SEG_OK) return st;
+  if (ce != cudaSuccess) return fail(SEG_ERR_CUDA, std::string("event timing: ") + cudaGetErrorString(ce));
+  *ms_per_launch = ms / reps;
+  return SEG_OK;
 }
 
 seg_status status_from_ctl(const DevCtl& c) {
@@ -550,6 +594,10 @@ seg_status seg_state_create(const seg_problem* p, int32_t m, double eps, seg_ini
     delete s;
     return fail(SEG_ERR_ARG, "launch_mode must be 0 (graph) or 1 (direct)");
   }
+  if (prm.grid_blocks > kMaxGrid) {
+    delete s;
+    return fail(SEG_ERR_ARG, "grid_blocks must be at most 2048");
+  }
   s->launch_mode = prm.launch_mode;
   bool ok = s->prec == SEG_MIXED_FP32 ? get_kernels_f32(s->lpr, p->ell_w, &s->ks)
                                       : get_kernels_f64(s->lpr, p->ell_w, &s->ks);
@@ -575,12 +623,14 @@ seg_status seg_state_create(const seg_problem* p, int32_t m, double eps, seg_ini
     delete s;
     return fail(SEG_ERR_CUDA, std::string("cudaDeviceGetAttribute: ") + cudaGetErrorString(ce));
   }
-  // blocks of at least 256 rows (1024 triangles), at most 2 (4) per SM; the
-  // geometry is part of the state, so results do not depend on whether the
-  // state runs alone or in a batch
+  // blocks of at least 256 rows (1024 triangles), at most kRowBlocksPerSM
+  // (kTriBlocksPerSM) per SM; the geometry is part of the state, so results
+  // do not depend on whether the state runs alone or in a batch
   s->grid = prm.grid_blocks > 0 ? prm.grid_blocks
-                                : (int)std::min<int64_t>(2 * nsm, std::max<int64_t>(1, (p->n + 255) / 256));
-  s->grid_e = (int)std::min<int64_t>(4 * nsm, std::max<int64_t>(1, (p->f + 1023) / 1024));
+                                : (int)std::min<int64_t>(kRowBlocksPerSM * nsm, std::max<int64_t>(1, (p->n + 255) / 256));
+  s->grid_e = (int)std::min<int64_t>(kTriBlocksPerSM * nsm, std::max<int64_t>(1, (p->f + 1023) / 1024));
+  s->grid_cap = std::max(s->grid, std::min(kMaxGrid, kTuneWaves * kRowBlocksPerSM * nsm));
+  s->grid_e_cap = std::max(s->grid_e, std::min(kMaxGrid, kTuneWaves * kTriBlocksPerSM * nsm));
   if (cuda_stream) {
     s->stream = (cudaStream_t)cuda_stream;
   } else {
@@ -592,7 +642,7 @@ seg_status seg_state_create(const seg_problem* p, int32_t m, double eps, seg_ini
     s->own_stream = true;
   }
   const size_t vbytes = (size_t)p->n * s->ms * vsize(s->prec);
-  const size_t pbytes = std::max<size_t>((size_t)s->grid * kMaxDots * s->ms, (size_t)s->grid_e) * 8;
+  const size_t pbytes = partial_bytes(s->ms, s->grid_cap, s->grid_e_cap);
   struct {
     void** ptr;
     size_t bytes;
@@ -679,10 +729,11 @@ seg_status seg_state_bytes(const seg_problem* p, int32_t m, uint64_t* bytes) {
   int lpr = (m + vw - 1) / vw, pw = 1;
   while (pw < lpr) pw <<= 1;
   const uint64_t ms = (uint64_t)pw * vw, n = (uint64_t)p->n;
-  const uint64_t grid = std::min<uint64_t>(2 * nsm, std::max<uint64_t>(1, (n + 255) / 256));
-  const uint64_t grid_e = std::min<uint64_t>(4 * nsm, std::max<uint64_t>(1, ((uint64_t)p->f + 1023) / 1024));
+  // partial sums sized for every geometry the autotuner may pick
+  const uint64_t grid = (uint64_t)std::min(kMaxGrid, kTuneWaves * kRowBlocksPerSM * nsm);
+  const uint64_t grid_e = (uint64_t)std::min(kMaxGrid, kTuneWaves * kTriBlocksPerSM * nsm);
   const uint64_t vbytes = n * ms * vsize(p->prec);
-  const uint64_t pbytes = std::max<uint64_t>(grid * kMaxDots * ms, grid_e) * 8;
+  const uint64_t pbytes = partial_bytes((int)ms, (int)grid, (int)grid_e);
   *bytes = 5 * vbytes + sizeof(DevCtl) + pbytes + std::max<uint64_t>(8, n * m * 8) + 2 * kMaxCols * 8 +
            std::max<uint64_t>(4, n * 4) + std::max<uint64_t>(4, n);
   return SEG_OK;
@@ -1054,30 +1105,113 @@ seg_status seg_time_kernel(seg_state* s, int32_t which, int32_t reps, double* ms
   if (!s || !ms_per_launch) return fail(SEG_ERR_ARG, "state or output is NULL");
   if (which < 0 || which > 5 || reps < 1) return fail(SEG_ERR_ARG, "which must be 0..5 and reps >= 1");
   SEG_CUDA(cudaSetDevice(s->p->device));
-  void* fns[] = {s->ks.start, s->ks.cg_a, s->ks.cg_b, s->ks.finish, s->ks.energy_check, s->ks.energy};
-  Launch l;
-  l.force = 1;
-  l.apply_x = 1;
-  l.apply_ode = 1;
-  cudaEvent_t e0, e1;
-  SEG_CUDA(cudaEventCreate(&e0));
-  SEG_CUDA(cudaEventCreate(&e1));
-  seg_status st = launch_row(s, fns[which], l);  // warm-up
-  if (st == SEG_OK) {
-    cudaEventRecord(e0, s->stream);
-    for (int r = 0; r < reps && st == SEG_OK; ++r) st = launch_row(s, fns[which], l);
-    cudaEventRecord(e1, s->stream);
-  }
-  cudaError_t ce = cudaEventSynchronize(e1);
-  float ms = 0;
-  if (st == SEG_OK && ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  if (st != SEG_OK) return st;
-  if (ce != cudaSuccess) return fail(SEG_ERR_CUDA, std::string("event timing: ") + cudaGetErrorString(ce));
-  *ms_per_launch = ms / reps;
+  seg_status st = time_launches(s, which, reps, ms_per_launch);
   s->pending = true;
-  return SEG_OK;
+  return st;
+}
+
+seg_status seg_autotune(seg_state* s, int32_t reps, seg_tune_result* out) {
+  if (!s || !out) return fail(SEG_ERR_ARG, "state or out is NULL");
+  if (reps < 1) reps = 10;
+  std::memset(out, 0, sizeof(*out));
+  SEG_CUDA(cudaSetDevice(s->p->device));
+  int nsm = 0;
+  SEG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, s->p->device));
+  seg_status st = sync_ctl(s);
+  if (st != SEG_OK) return st;
+  // CG iterations per step so far (the weight of the two CG passes)
+  const double k = s->hctl->step > 0 ? (double)s->hctl->cg_total / (double)s->hctl->step : 8.0;
+  // save the data the timing launches overwrite: X and the control block;
+  // Z, P and Q are rewritten by every step before they are read (the first
+  // CG pass multiplies the old P by beta = 0, so any finite P will do)
+  const size_t vbytes = (size_t)s->p->n * s->ms * vsize(s->prec);
+  void* saved_x = nullptr;
+  DevCtl* saved_ctl = nullptr;
+  cudaError_t ce = cudaMalloc(&saved_x, vbytes);
+  if (ce == cudaSuccess) ce = cudaMalloc((void**)&saved_ctl, sizeof(DevCtl));
+  if (ce != cudaSuccess) {
+    cudaFree(saved_x);
+    return fail(SEG_ERR_NO_MEMORY, std::string("cudaMalloc: ") + cudaGetErrorString(ce));
+  }
+  const bool pending = s->pending;
+  const int grid0 = s->grid, grid_e0 = s->grid_e;
+  ce = cudaMemcpyAsync(saved_x, s->X, vbytes, cudaMemcpyDeviceToDevice, s->stream);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(saved_ctl, s->ctl, sizeof(DevCtl), cudaMemcpyDeviceToDevice, s->stream);
+  if (ce != cudaSuccess) st = fail(SEG_ERR_CUDA, std::string("save: ") + cudaGetErrorString(ce));
+  // candidate row grids: 1 .. kRowBlocksPerSM blocks per SM (one wave), and
+  // 2 .. kTuneWaves waves of them (the hardware hands out the later blocks as
+  // earlier ones finish, which evens out blocks that run slower), at most one
+  // block per 256 rows; triangle grids likewise with kTriBlocksPerSM
+  std::vector<int> rows_c, tris_c;
+  const int64_t n_cap = std::max<int64_t>(1, (s->p->n + 255) / 256);
+  const int64_t f_cap = std::max<int64_t>(1, (s->p->f + 1023) / 1024);
+  for (int b = 1; b <= kRowBlocksPerSM; ++b) rows_c.push_back((int)std::min<int64_t>((int64_t)b * nsm, n_cap));
+  for (int b = 1; b <= kTriBlocksPerSM; ++b) tris_c.push_back((int)std::min<int64_t>((int64_t)b * nsm, f_cap));
+  for (int w = 2; w <= kTuneWaves; w *= 2) {
+    rows_c.push_back((int)std::min<int64_t>((int64_t)w * kRowBlocksPerSM * nsm, n_cap));
+    tris_c.push_back((int)std::min<int64_t>((int64_t)w * kTriBlocksPerSM * nsm, f_cap));
+  }
+  rows_c.push_back(grid0);
+  tris_c.push_back(grid_e0);
+  for (auto* v : {&rows_c, &tris_c}) {
+    std::sort(v->begin(), v->end());
+    v->erase(std::unique(v->begin(), v->end()), v->end());
+  }
+  int best = grid0, best_e = grid_e0;
+  double best_ms = 1e300, best_e_ms = 1e300;
+  for (size_t c = 0; c < rows_c.size() && st == SEG_OK; ++c) {
+    const int g = rows_c[c];
+    if (g > s->grid_cap) continue;
+    s->grid = g;
+    double t[4] = {0, 0, 0, 0};
+    for (int w = 0; w < 4 && st == SEG_OK; ++w) st = time_launches(s, w, reps, &t[w]);
+    if (st != SEG_OK) break;
+    const double model = t[0] + k * (t[1] + t[2]) + t[3];
+    if (out->n_candidates < SEG_TUNE_MAX) {
+      out->cand_grid[out->n_candidates] = g;
+      out->cand_ms[out->n_candidates] = model;
+      out->n_candidates += 1;
+    }
+    if (model < best_ms) {
+      best_ms = model;
+      best = g;
+    }
+  }
+  for (size_t c = 0; c < tris_c.size() && st == SEG_OK; ++c) {
+    const int g = tris_c[c];
+    if (g > s->grid_e_cap) continue;
+    s->grid_e = g;
+    double t = 0;
+    st = time_launches(s, 4, reps, &t);
+    if (st == SEG_OK && t < best_e_ms) {
+      best_e_ms = t;
+      best_e = g;
+    }
+  }
+  // restore the state's data bitwise
+  ce = cudaMemcpyAsync(s->X, saved_x, vbytes, cudaMemcpyDeviceToDevice, s->stream);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(s->ctl, saved_ctl, sizeof(DevCtl), cudaMemcpyDeviceToDevice, s->stream);
+  for (void* b : {s->Z, s->P0, s->P1, s->Q})
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(b, 0, vbytes, s->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s->stream);
+  cudaFree(saved_x);
+  cudaFree(saved_ctl);
+  if (st == SEG_OK && ce != cudaSuccess) st = fail(SEG_ERR_CUDA, std::string("restore: ") + cudaGetErrorString(ce));
+  s->pending = pending;
+  s->grid = st == SEG_OK ? best : grid0;
+  s->grid_e = st == SEG_OK ? best_e : grid_e0;
+  out->grid_blocks = s->grid;
+  out->grid_blocks_energy = s->grid_e;
+  out->ms_model = st == SEG_OK ? best_ms : 0.0;
+  out->ms_energy = st == SEG_OK ? best_e_ms : 0.0;
+  out->cg_weight = k;
+  // the step graph has the geometry baked in
+  if (s->exec) cudaGraphExecDestroy(s->exec);
+  if (s->graph) cudaGraphDestroy(s->graph);
+  s->exec = nullptr;
+  s->graph = nullptr;
+  const seg_status gs = s->prec == SEG_MIXED_FP32 ? build_graph_t<float>(s) : build_graph_t<double>(s);
+  return st != SEG_OK ? st : gs;
 }
 
 seg_status seg_launch_info(seg_state* s, int32_t* grid_blocks, int32_t* block_threads, int32_t* lanes_per_row,

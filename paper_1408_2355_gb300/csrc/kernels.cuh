@@ -137,9 +137,86 @@ __device__ __forceinline__ void shfl_add(AccF& a, int off) {
 }
 __device__ __forceinline__ void shfl_add(AccD& a, int off) { a.v += __shfl_xor_sync(0xffffffffu, a.v, off); }
 
+__device__ __forceinline__ void zero_part(float2& p) { p = make_float2(0.f, 0.f); }
+__device__ __forceinline__ void zero_part(double& p) { p = 0.0; }
+
+// Deterministic two-level sum over the G blocks of a grid of P partial sums:
+// part[p * G + b] holds block b's partial of sum p (every block has written
+// its own before the call).  The last block of each group of 32 blocks to
+// arrive sums the group's partials in block order (a fixed shuffle tree) into
+// part[P * G + p * NG + group]; the last group to finish sums the NG group
+// partials the same way and calls out(p, total) from one lane per p.  Returns
+// true in that block only.  Must be reached by every block of the grid.
+template <typename Acc, typename Part, typename Out>
+__device__ __forceinline__ bool reduce_blocks(Part* part, unsigned int* gcount, unsigned int* count, int P, int vb,
+                                              int G, Out out) {
+  constexpr int NW = kBlockThreads / 32;
+  constexpr int U = 4;  // sums per warp in flight
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __shared__ unsigned int ticket;
+  const int NG = (G + 31) >> 5;
+  const int grp = vb >> 5, g0 = grp << 5, gn = min(32, G - g0);
+  Part* part1 = part + (size_t)P * G;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) ticket = atomicAdd(&gcount[grp], 1u);
+  __syncthreads();
+  if (ticket != (unsigned int)(gn - 1)) return false;
+  __threadfence();
+  for (int p0 = warp * U; p0 < P; p0 += NW * U) {
+    Part v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      zero_part(v[u]);
+      if (p0 + u < P && lane < gn) v[u] = __ldcg(&part[(size_t)(p0 + u) * G + g0 + lane]);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      Acc s;
+      s.zero();
+      add_part(s, v[u]);
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) shfl_add(s, off);
+      if (lane == 0 && p0 + u < P) part1[(size_t)(p0 + u) * NG + grp] = to_part(s);
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    gcount[grp] = 0u;  // every block of the group has arrived
+    ticket = atomicAdd(count, 1u);
+  }
+  __syncthreads();
+  if (ticket != (unsigned int)(NG - 1)) return false;
+  __threadfence();
+  for (int p0 = warp * U; p0 < P; p0 += NW * U) {
+    Part v[U], w[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      zero_part(v[u]);
+      zero_part(w[u]);
+      if (p0 + u < P && lane < NG) v[u] = __ldcg(&part1[(size_t)(p0 + u) * NG + lane]);
+      if (p0 + u < P && lane + 32 < NG) w[u] = __ldcg(&part1[(size_t)(p0 + u) * NG + lane + 32]);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      Acc s;
+      s.zero();
+      add_part(s, v[u]);
+      add_part(s, w[u]);
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) shfl_add(s, off);
+      if (lane == 0 && p0 + u < P) out(p0 + u, s.value());
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *count = 0u;
+  return true;
+}
+
 // Block + grid reduction of ND per-component sums.  Every block writes its
-// partial; the last block to arrive sums the partials of all blocks in block
-// order and leaves the totals in tot[ND][kMaxCols].  Returns true in the last
+// partial; the grid's partials are summed by reduce_blocks, which leaves the
+// totals in tot[ND][kMaxCols] of the last block.  Returns true in the last
 // block only.  Must be reached by every block of the grid.
 template <typename T, int LPR, int ND>
 __device__ __forceinline__ bool grid_reduce(typename AccOf<T>::type (&acc)[ND][VecW<T>::W],
@@ -156,7 +233,6 @@ __device__ __forceinline__ bool grid_reduce(typename AccOf<T>::type (&acc)[ND][V
 #pragma unroll
       for (int v = 0; v < VW; ++v) shfl_add(acc[d][v], off);
   __shared__ Part red[ND][NW][kMaxCols];
-  __shared__ unsigned int ticket;
   if (lane < LPR) {
 #pragma unroll
     for (int d = 0; d < ND; ++d)
@@ -173,23 +249,9 @@ __device__ __forceinline__ bool grid_reduce(typename AccOf<T>::type (&acc)[ND][V
     for (int w = 0; w < NW; ++w) add_part(s, red[d][w][c]);
     part[(size_t)(d * a.ms + c) * G + vb] = to_part(s);
   }
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) ticket = atomicAdd(&a.ctl->counters[slot], 1u);
-  __syncthreads();
-  if (ticket != (unsigned int)(G - 1)) return false;
-  __threadfence();
-  for (int pidx = warp; pidx < ND * a.ms; pidx += NW) {
-    Acc s;
-    s.zero();
-    for (int b = lane; b < G; b += 32) add_part(s, __ldcg(&part[(size_t)pidx * G + b]));
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) shfl_add(s, off);
-    if (lane == 0) tot[pidx / a.ms][pidx % a.ms] = s.value();
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) a.ctl->counters[slot] = 0u;
-  return true;
+  const int ms = a.ms;
+  return reduce_blocks<Acc>(part, a.ctl->gcounters[slot], &a.ctl->counters[slot], ND * ms, vb, G,
+                            [&](int p, double v) { tot[p / ms][p % ms] = v; });
 }
 
 // Exclusive sums over the components of one vertex row held by the LPR lanes
@@ -328,6 +390,8 @@ struct StageSrc {
   const T* vec[NVEC];  // rows of ms values
 };
 
+constexpr int kPipeStages = 4;  // deepest copy ring of the staged row passes
+
 // Per-warp staging of one group of RPW consecutive rows: the padded-ELL
 // indices and NVAL value arrays of the group and the rows of NVEC vectors.
 // Every piece is a contiguous slice of global memory, copied by one bulk copy.
@@ -341,6 +405,14 @@ struct RowStage {
   static constexpr unsigned kValBytes = RPW * W * sizeof(T);
   static constexpr unsigned kVecBytes = RPW * MS * sizeof(T);  // = 512
   static constexpr unsigned kBytes = kColBytes + NVAL * kValBytes + NVEC * kVecBytes;
+  // stages of each warp's copy ring (up to kStages - 1 row groups in flight
+  // while one is consumed): as many as fit 64 KiB per block, 2 .. kPipeStages
+  static constexpr int kStages =
+      (int)(65536u / ((kBlockThreads / 32) * kBytes)) < 2
+          ? 2
+          : ((int)(65536u / ((kBlockThreads / 32) * kBytes)) > kPipeStages
+                 ? kPipeStages
+                 : (int)(65536u / ((kBlockThreads / 32) * kBytes)));
   static_assert(kColBytes % 16 == 0 && kValBytes % 16 == 0 && kVecBytes % 16 == 0, "16-byte pieces");
 
   unsigned char* base;
@@ -367,7 +439,7 @@ struct RowStage {
 
 template <typename Stage>
 constexpr unsigned row_stage_smem() {
-  return (kBlockThreads / 32) * 2 * Stage::kBytes;
+  return (kBlockThreads / 32) * Stage::kStages * Stage::kBytes;
 }
 
 // Reads VW values of this lane from a staged row (shared memory).
@@ -414,60 +486,73 @@ __device__ __forceinline__ void report_timeout(DevCtl* ctl) {
 }
 
 // Warp-level pipeline over the row groups of the block: group gi covers
-// rows [r0 + gi*RPW, ...); warp w takes groups w, w+NW, ...  While the rows
-// of one group are processed, the bulk copies of the warp's next group are
-// in flight.  `body(stage, row0, nr)` consumes a landed stage.  Returns false
+// rows [r0 + gi*RPW, ...); warp w takes groups w, w+NW, ...  The copies of
+// the warp's next Stage::kStages - 1 groups are in flight while one group is
+// processed.  `body(stage, row0, nr)` consumes a landed stage.  Returns false
 // if a wait timed out (the copies still in flight are waited for, bounded).
 template <typename Stage, typename Body>
 __device__ __forceinline__ bool row_pipeline(unsigned char* smem_warp, unsigned long long* bars, int r0, int r1,
                                              const typename Stage::Src& src, Body body) {
   constexpr int NW = kBlockThreads / 32;
   constexpr int RPW = Stage::RPW;
+  constexpr int NS = Stage::kStages;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  Stage st[2];
-  st[0].base = smem_warp;
-  st[1].base = smem_warp + Stage::kBytes;
   const int ngroups = (r1 - r0 + RPW - 1) / RPW;
   if (lane == 0) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
+#pragma unroll
+    for (int k = 0; k < NS; ++k) mbar_init(&bars[k], 1);
     mbar_init_fence();
   }
   __syncwarp();
-  int gi = warp;
-  if (gi < ngroups && lane == 0) {
-    const int row0 = r0 + gi * RPW;
-    st[0].issue(&bars[0], row0, min(RPW, r1 - row0), src);
+  auto stage = [&](int k) {
+    Stage sg;
+    sg.base = smem_warp + k * Stage::kBytes;
+    return sg;
+  };
+  // prologue: groups 0 .. NS-2 of this warp into stages 0 .. NS-2
+  unsigned pending = 0;  // stages with copies in flight (bit mask)
+#pragma unroll
+  for (int k = 0; k < NS - 1; ++k) {
+    const int g = warp + k * NW;
+    if (g < ngroups) {
+      if (lane == 0) {
+        const int row0 = r0 + g * RPW;
+        stage(k).issue(&bars[k], row0, min(RPW, r1 - row0), src);
+      }
+      pending |= 1u << k;
+    }
   }
   bool ok = true;
-  int pending = gi < ngroups ? 1 : 0;  // stages with copies in flight (bit mask)
-  unsigned used[2] = {0u, 0u};         // completed phases consumed per stage
-  for (int k = 0; gi < ngroups; gi += NW, ++k) {
-    const int s = k & 1;
-    const int gn = gi + NW;
+  unsigned phase = 0;  // bit k: parity of the next completion of stage k
+  int s = 0;
+  for (int gi = warp; gi < ngroups; gi += NW) {
+    // refill the stage consumed in the previous iteration
+    const int gn = gi + (NS - 1) * NW;
+    const int sn = s == 0 ? NS - 1 : s - 1;
     if (gn < ngroups) {
       if (lane == 0) {
         fence_proxy_async_smem();
         const int row0 = r0 + gn * RPW;
-        st[s ^ 1].issue(&bars[s ^ 1], row0, min(RPW, r1 - row0), src);
+        stage(sn).issue(&bars[sn], row0, min(RPW, r1 - row0), src);
       }
-      pending |= 1 << (s ^ 1);
+      pending |= 1u << sn;
     }
-    const bool landed = mbar_wait(&bars[s], used[s] & 1u);
+    const bool landed = mbar_wait(&bars[s], (phase >> s) & 1u);
     if (!__all_sync(0xffffffffu, landed)) {
       ok = false;
       break;
     }
-    pending &= ~(1 << s);
-    ++used[s];
+    pending &= ~(1u << s);
+    phase ^= 1u << s;
     const int row0 = r0 + gi * RPW;
-    body(st[s], row0, min(RPW, r1 - row0));
+    body(stage(s), row0, min(RPW, r1 - row0));
     __syncwarp();
+    s = s == NS - 1 ? 0 : s + 1;
   }
   if (!ok) {
     // drain: wait (bounded) for every stage that still has copies in flight
-    for (int s = 0; s < 2; ++s)
-      if (pending & (1 << s)) mbar_wait(&bars[s], used[s] & 1u);
+    for (int k = 0; k < NS; ++k)
+      if (pending & (1u << k)) mbar_wait(&bars[k], (phase >> k) & 1u);
   }
   return ok;
 }
@@ -490,7 +575,7 @@ __device__ __forceinline__ void body_start(const KArgs<T>& a, const int vb, cons
   if (state_finished(a, ctl)) return;
   SEG_ROW_SETUP
   extern __shared__ __align__(128) unsigned char dyn_smem[];
-  __shared__ __align__(8) unsigned long long bars[NW][2];
+  __shared__ __align__(8) unsigned long long bars[NW][kPipeStages];
   const T tau = (T)a.tau;
   const unsigned ms = a.ms;
   Acc acc[5][VW];
@@ -507,7 +592,7 @@ __device__ __forceinline__ void body_start(const KArgs<T>& a, const int vb, cons
   src.val[1] = a.valM;
   src.vec[0] = a.X;
   const bool ok = row_pipeline<Stage>(
-      dyn_smem + warp * 2 * Stage::kBytes, bars[warp], r0, r1, src, [&](const Stage& sg, int row0, int nr) {
+      dyn_smem + warp * Stage::kStages * Stage::kBytes, bars[warp], r0, r1, src, [&](const Stage& sg, int row0, int nr) {
         if (rs >= nr) return;
         const unsigned row = row0 + rs;
         int cols[W];
@@ -599,10 +684,10 @@ __device__ __forceinline__ void body_cg_a(const KArgs<T>& a, const int vb, const
   typedef CgAStage<T, LPR, W> Stage;
   DevCtl* ctl = a.ctl;
   if (state_finished(a, ctl)) return;
-  if (!ctl->cont) return;  // this instance's CG loop has ended
+  if (!ctl->cont && !a.force) return;  // this instance's CG loop has ended (timing runs: force)
   SEG_ROW_SETUP
   extern __shared__ __align__(128) unsigned char dyn_smem[];
-  __shared__ __align__(8) unsigned long long bars[NW][2];
+  __shared__ __align__(8) unsigned long long bars[NW][kPipeStages];
   const int it = ctl->it;
   const T* Pold = (it & 1) ? a.P1 : a.P0;
   T* Pnew = (it & 1) ? a.P0 : a.P1;
@@ -623,7 +708,7 @@ __device__ __forceinline__ void body_cg_a(const KArgs<T>& a, const int vb, const
   src.vec[1] = Pold;
   src.vec[2] = a.X;
   const bool ok = row_pipeline<Stage>(
-      dyn_smem + warp * 2 * Stage::kBytes, bars[warp], r0, r1, src, [&](const Stage& sg, int row0, int nr) {
+      dyn_smem + warp * Stage::kStages * Stage::kBytes, bars[warp], r0, r1, src, [&](const Stage& sg, int row0, int nr) {
         if (rs >= nr) return;
         const unsigned row = row0 + rs;
         int cols[W];
@@ -816,10 +901,8 @@ __device__ __forceinline__ bool grid_reduce_scalar(typename AccOf<T>::type acc, 
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) shfl_add(acc, off);
   __shared__ Part red[NW];
-  __shared__ unsigned int ticket;
   if (lane == 0) red[warp] = to_part(acc);
   __syncthreads();
-  const int G = vg;
   Part* part = reinterpret_cast<Part*>(partv);
   if (threadIdx.x == 0) {
     Acc s;
@@ -827,23 +910,8 @@ __device__ __forceinline__ bool grid_reduce_scalar(typename AccOf<T>::type acc, 
     for (int w = 0; w < NW; ++w) add_part(s, red[w]);
     part[vb] = to_part(s);
   }
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) ticket = atomicAdd(&ctl->counters[slot], 1u);
-  __syncthreads();
-  if (ticket != (unsigned int)(G - 1)) return false;
-  __threadfence();
-  if (warp == 0) {
-    Acc s;
-    s.zero();
-    for (int b = lane; b < G; b += 32) add_part(s, __ldcg(&part[b]));
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) shfl_add(s, off);
-    if (lane == 0) *tot = s.value();
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) ctl->counters[slot] = 0u;
-  return true;
+  return reduce_blocks<Acc>(part, ctl->gcounters[slot], &ctl->counters[slot], 1, vb, vg,
+                            [&](int, double v) { *tot = v; });
 }
 
 // Symmetric 6-point rule of degree 4 on a triangle (two orbits of points
@@ -967,7 +1035,7 @@ __device__ __forceinline__ void body_cg_b(const KArgs<T>& a, const int vb, const
     if (a.set_cond && vb == 0 && threadIdx.x == 0) cudaGraphSetConditional(a.cond, 0);
     return;
   }
-  if (!ctl->cont) return;  // this instance's CG loop has ended
+  if (!ctl->cont && !a.force) return;  // this instance's CG loop has ended (timing runs: force)
   SEG_ROW_SETUP
   const int it = ctl->it;
   const unsigned ms = a.ms;
@@ -1131,12 +1199,12 @@ __device__ __forceinline__ int batch_slot(const BatchArgs<T>& b) {
 
 #define SEG_TPL_W template <typename T, int LPR, int W>
 #define SEG_TPL template <typename T, int LPR>
-SEG_DEFINE_PASS(start, 2, SEG_TPL_W, T, LPR, W)
-SEG_DEFINE_PASS(cg_a, 2, SEG_TPL_W, T, LPR, W)
-SEG_DEFINE_PASS(cg_b, 2, SEG_TPL, T, LPR)
-SEG_DEFINE_PASS(finish, 2, SEG_TPL, T, LPR)
+SEG_DEFINE_PASS(start, 3, SEG_TPL_W, T, LPR, W)
+SEG_DEFINE_PASS(cg_a, 3, SEG_TPL_W, T, LPR, W)
+SEG_DEFINE_PASS(cg_b, 3, SEG_TPL, T, LPR)
+SEG_DEFINE_PASS(finish, 3, SEG_TPL, T, LPR)
 SEG_DEFINE_PASS(energy, 2, SEG_TPL, T, LPR)
-SEG_DEFINE_PASS(energy_check, 4, SEG_TPL, T, LPR)
+SEG_DEFINE_PASS(energy_check, kTriBlocksPerSM, SEG_TPL, T, LPR)
 #undef SEG_TPL
 #undef SEG_TPL_W
 #undef SEG_DEFINE_PASS

@@ -13,7 +13,13 @@ namespace segimpl {
 
 constexpr int kMaxCols = 32;       // padded components per vertex row
 constexpr int kBlockThreads = 256;  // threads per block of every row kernel
-constexpr int kMaxDots = 5;        // inner products fused into one pass
+constexpr int kMaxDots = 5;         // inner products fused into one pass
+// Resident blocks per SM the row passes are compiled for (register bound)
+// and launched with; the triangle passes use kTriBlocksPerSM.
+constexpr int kRowBlocksPerSM = 3;
+constexpr int kTriBlocksPerSM = 4;
+constexpr int kMaxGrid = 2048;  // blocks of one kernel of a state (two-level grid reduction)
+constexpr int kTuneWaves = 4;   // the autotuner tries up to this many waves of blocks
 constexpr int kNumCounters = 8;    // last-block tickets, one per kernel kind
 
 enum CounterSlot { kCtrStart = 0, kCtrCgA = 1, kCtrCgB = 2, kCtrEnergy = 3 };
@@ -49,6 +55,7 @@ struct DevCtl {
   int pad0;
   long long step_mark;        // ctl->step when the last batch of steps was enqueued
   unsigned int counters[kNumCounters];
+  unsigned int gcounters[kNumCounters][kMaxGrid / 32];  // per group of 32 blocks
 };
 
 // Arguments of every hot-path kernel (passed by value; identical struct for
@@ -85,7 +92,7 @@ struct KArgs {
   int ntri;
   long long check_every;
   double energy_tol;
-  int force;       // evaluate the energy regardless of the cadence
+  int force;       // timing/forced launches: energy regardless of the cadence, CG passes regardless of the loop state
   int apply_x;     // finish pass: apply the lagged CG update of X
   int apply_ode;   // finish pass: apply the nodal segregation ODE
   int count_step;  // finish pass: increment the step counter

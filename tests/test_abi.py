@@ -53,6 +53,7 @@ def test_struct_layouts_match_header(seg):
     assert C.sizeof(seg.seg_server_params) == 16
     assert C.sizeof(seg.seg_request_info) == 64
     assert C.sizeof(seg.seg_stats) == 48
+    assert C.sizeof(seg.seg_tune_result) == 136
 
 
 @pytest.mark.parametrize("level", [0, 1, 3, 5])
