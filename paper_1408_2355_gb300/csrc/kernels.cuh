@@ -1199,10 +1199,10 @@ __device__ __forceinline__ int batch_slot(const BatchArgs<T>& b) {
 
 #define SEG_TPL_W template <typename T, int LPR, int W>
 #define SEG_TPL template <typename T, int LPR>
-SEG_DEFINE_PASS(start, 3, SEG_TPL_W, T, LPR, W)
-SEG_DEFINE_PASS(cg_a, 3, SEG_TPL_W, T, LPR, W)
-SEG_DEFINE_PASS(cg_b, 3, SEG_TPL, T, LPR)
-SEG_DEFINE_PASS(finish, 3, SEG_TPL, T, LPR)
+SEG_DEFINE_PASS(start, kRowBlocksPerSM, SEG_TPL_W, T, LPR, W)
+SEG_DEFINE_PASS(cg_a, kRowBlocksPerSM, SEG_TPL_W, T, LPR, W)
+SEG_DEFINE_PASS(cg_b, kRowBlocksPerSM, SEG_TPL, T, LPR)
+SEG_DEFINE_PASS(finish, kRowBlocksPerSM, SEG_TPL, T, LPR)
 SEG_DEFINE_PASS(energy, 2, SEG_TPL, T, LPR)
 SEG_DEFINE_PASS(energy_check, kTriBlocksPerSM, SEG_TPL, T, LPR)
 #undef SEG_TPL
