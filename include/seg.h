@@ -116,6 +116,40 @@ seg_status seg_mesh_ellipsoid(int32_t level, double a, double b, double c, seg_m
  * each grid quad split along one fixed diagonal. */
 seg_status seg_mesh_torus(int32_t nu, int32_t nv, double R, double r, seg_mesh** out);
 
+/* Surfaces that refinement moves new vertices onto. */
+typedef enum {
+  SEG_SURFACE_NONE = 0,       /* keep the edge midpoints (the polyhedron itself) */
+  SEG_SURFACE_ELLIPSOID = 1,  /* x^2/p0^2 + y^2/p1^2 + z^2/p2^2 = 1 by radial map; p0=p1=p2=1: unit sphere */
+  SEG_SURFACE_TORUS = 2,      /* core radius p0, tube radius p1 (p0 > p1 > 0): closest point */
+  SEG_SURFACE_DZIUK = 3       /* surface (D) of Sec. 3.4: Phi = (x1 - x3^2)^2 + x2^2 + x3^2 - 1 = 0,
+                                 Newton projection x <- x - Phi grad Phi / |grad Phi|^2 until
+                                 |Phi| <= 1e-14 (at most 50 iterations) */
+} seg_surface_kind;
+
+typedef struct {
+  int32_t kind;      /* seg_surface_kind */
+  int32_t reserved;  /* must be 0 */
+  double p0, p1, p2;
+} seg_surface;
+
+/* Surface (D) of Sec. 3.4: the icosahedron's vertices Newton-projected onto
+ * Phi = 0, then `level` refinements (seg_mesh_refine with SEG_SURFACE_DZIUK).
+ * N = 10*4^level + 2.  SEG_ERR_ARG for level outside [0, 10]. */
+seg_status seg_mesh_dziuk(int32_t level, seg_mesh** out);
+
+/* One global refinement (Sec. 3.3 refines the mesh between continuation
+ * levels): every triangle is split into four through its edge midpoints and
+ * every new vertex is moved onto `surf`.  Numbering: coarse vertices keep
+ * their numbers; the midpoint of edge (lo, hi), lo < hi, becomes vertex
+ * n_coarse + (rank of the edge in (lo, hi) order); the children of coarse
+ * triangle t are t, F + t, 2F + t (at its corners 0, 1, 2) and 3F + t (the
+ * middle one).  parents (nullable, host, [n_fine][2] int32) receives the
+ * parent edge of every fine vertex ((z, z) for a coarse vertex): the input of
+ * seg_prolong.  Refining the level-L icosphere with the unit sphere gives the
+ * level-(L+1) icosphere exactly. */
+seg_status seg_mesh_refine(const seg_mesh* coarse, const seg_surface* surf, seg_mesh** fine,
+                           int32_t* parents);
+
 /* Sizes of a mesh, and a copy of its arrays (either output may be NULL). */
 seg_status seg_mesh_info(const seg_mesh* mesh, int64_t* n_vert, int64_t* n_tri);
 seg_status seg_mesh_get(const seg_mesh* mesh, double* xyz, int32_t* tri);
@@ -128,6 +162,15 @@ void seg_mesh_destroy(seg_mesh* mesh);
  * current CUDA device in the requested precision) for time step tau > 0. */
 seg_status seg_assemble(const seg_mesh* mesh, double tau, seg_precision precision,
                         seg_problem** out);
+
+/* seg_assemble with options.  SEG_ASSEMBLE_LUMPED_MASS: the mass-lumped
+ * variant -- M is replaced by M_L = diag(row sums of M) = diag(|star(z)|/3)
+ * wherever the method uses it (the matrix of step 1, its right-hand side
+ * M_L u and the L2 norm of step 3); K, the energies and S_eps are unchanged.
+ * SEG_ERR_ARG for an unknown flag. */
+#define SEG_ASSEMBLE_LUMPED_MASS 1u
+seg_status seg_assemble_ex(const seg_mesh* mesh, double tau, seg_precision precision, uint32_t flags,
+                           seg_problem** out);
 
 /* n_vert, number of nonzeros of M/K/A, tau, total area |Gamma_h| (any may be NULL). */
 seg_status seg_problem_info(const seg_problem* p, int64_t* n_vert, int64_t* nnz, double* tau,
@@ -268,6 +311,32 @@ seg_status seg_energy(seg_state* s, double* total, double* functional, double* d
  * lambda[i] = D_i (Sec. 3.2: the H^1 semi-norm of the normalised component),
  * lambda_cl[i] = D_i + (2/eps^2) int u_i^2 sum_{j!=i} u_j^2 (the formula of Sec. 1.1). */
 seg_status seg_eigenvalue_estimates(seg_state* s, double* lambda, double* lambda_cl);
+
+/* The l^p energy of Problem 1.2 from the eigenvalue estimates lambda[i] = D_i:
+ * ((1/m) sum_i lambda_i^p)^(1/p) for 1 <= p < inf, max_i lambda_i for
+ * p = +inf (pass INFINITY).  SEG_ERR_ARG for p < 1 or NaN. */
+seg_status seg_energy_p(seg_state* s, double p, double* e_p);
+
+/* Start `fine` from the P1 interpolation of `coarse`'s current state on a
+ * refined mesh (Sec. 3.3: the previous level's minimiser is the initial
+ * condition of the next): u_fine(z) = (u(parents[2z]) + u(parents[2z+1]))/2,
+ * parents as written by seg_mesh_refine (host array, [n_fine][2], copied).
+ * The result replaces fine's state like seg_set_u (normalised in fine's L2
+ * norm before its next step).  Both states need the same m; all arithmetic
+ * runs on the device.  SEG_ERR_ARG for mismatched sizes or a parent index
+ * out of range. */
+seg_status seg_prolong(seg_state* coarse, seg_state* fine, const int32_t* parents);
+
+/* One level of the continuation of Sec. 3.3: refine coarse_mesh onto `surf`
+ * (seg_mesh_refine), assemble with tau_next in coarse's precision and
+ * assembly flags, create a state with eps_next and `opt` (NULL: defaults) on
+ * a new stream, and start it from the P1 interpolation of coarse
+ * (seg_prolong).  The caller owns the three outputs.  The paper's rule
+ * divides eps and tau by sqrt(2) per bisection level; one refinement here
+ * equals two bisection levels, so eps_next = eps / 2, tau_next = tau / 2. */
+seg_status seg_continue(seg_state* coarse, const seg_mesh* coarse_mesh, const seg_surface* surf,
+                        double eps_next, double tau_next, const seg_params* opt, seg_mesh** fine_mesh,
+                        seg_problem** fine_problem, seg_state** fine_state);
 
 /* Partition read-out per vertex (host arrays of length n_vert, nullable):
  * argmax[z] = argmax_i u_i(z) (lowest index on ties); v_positive[z] = 1 if

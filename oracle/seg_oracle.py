@@ -308,6 +308,74 @@ def run(xyz, tri, U0, tau, eps, nsteps, tol=1e-6, check_every=None, rtol=1e-14):
     return U, k, history
 
 
+# ---------------------------------------------------------------------------
+# Variants and extensions: lumped mass, l^p energies (Problem 1.2),
+# continuation with refinement and prolongation (Sec. 3.3)
+# ---------------------------------------------------------------------------
+
+
+def lumped_mass(xyz, tri):
+    """Mass matrix of the vertex quadrature int_T f ~ |T|/3 (f(a) + f(b) + f(c)):
+    the lumped-mass variant, M_L = diag(|star(z)| / 3), |star(z)| the area of
+    the triangles around z.  (The paper uses the consistent M; this variant
+    replaces it in steps 1 and 3.)"""
+    n = xyz.shape[0]
+    area = triangle_areas(xyz, tri)
+    d = np.zeros(n)
+    for k in range(3):
+        np.add.at(d, tri[:, k], area / 3.0)
+    return sp.diags(d).tocsr()
+
+
+def energy_p(lams, p):
+    """E_p of Problem 1.2 from the eigenvalue estimates lambda_i:
+    ((1/m) sum lambda_i^p)^(1/p) for 1 <= p < inf, max lambda_i for p = inf."""
+    lams = np.asarray(lams, dtype=np.float64)
+    if p == math.inf:
+        return float(lams.max())
+    if p < 1:
+        raise ValueError("p must be >= 1")
+    top = lams.max()  # scaled by the largest value so that lambda^p cannot overflow
+    if top == 0.0:
+        return 0.0
+    return float(top * np.mean((lams / top) ** p) ** (1.0 / p))
+
+
+def prolong(U, parents):
+    """P1 interpolation onto a refined mesh (Sec. 3.3: the previous minimiser
+    is the initial condition on the next level).  A fine vertex with parent
+    edge (a, b) takes (U[a] + U[b]) / 2 (its value at the edge midpoint of the
+    coarse polyhedron); a coarse vertex (a = b) keeps its value."""
+    return 0.5 * (U[parents[:, 0]] + U[parents[:, 1]])
+
+
+def continuation(levels, U0, eps0, tau0, steps, factor=0.5, rtol=1e-14):
+    """The refinement rule of Sec. 3.3 run for a fixed number of steps per level.
+
+    levels: list of (xyz, tri, parents) for level 0, 1, ...; parents of level
+    l maps its vertices to level l - 1 (ignored for level 0).  Level 0 starts
+    from the drawn values U0; every later level starts from the P1
+    interpolation of the previous level's final state, with eps and tau
+    multiplied by `factor` per level (one global red refinement = two
+    bisection levels, each dividing eps and tau by sqrt 2).  Returns a list of
+    (U, energy record) per level.
+    """
+    out = []
+    eps, tau = eps0, tau0
+    U = None
+    for l, (xyz, tri, parents) in enumerate(levels):
+        M, K = assemble(xyz, tri)
+        if l == 0:
+            U = initial_state(M, U0)
+        else:
+            eps, tau = eps * factor, tau * factor
+            U = normalise(M, prolong(U, parents))
+        for _ in range(steps):
+            U = step(M, K, tau, eps, U, rtol=rtol)
+        out.append((U, energy(xyz, tri, K, U, eps)))
+    return out
+
+
 def constant_state_s_eps(m, area, eps):
     """S_eps of u_i = |Gamma_h|^{-1/2} for all i: m (m - 1) / (eps^2 |Gamma_h|)."""
     return m * (m - 1) / (eps ** 2 * area)

@@ -44,10 +44,10 @@ SEG_INIT_UNIFORM = 1
 
 EXPORTED = [
     "seg_create_mesh", "seg_mesh_icosphere", "seg_mesh_ellipsoid", "seg_mesh_torus",
-    "seg_mesh_info", "seg_mesh_get", "seg_mesh_destroy", "seg_assemble", "seg_problem_info",
+    "seg_mesh_dziuk", "seg_mesh_refine", "seg_mesh_info", "seg_mesh_get", "seg_mesh_destroy", "seg_assemble", "seg_assemble_ex", "seg_problem_info",
     "seg_problem_destroy", "seg_state_create", "seg_state_destroy", "seg_set_u", "seg_get_u",
     "seg_step", "seg_step_async", "seg_sync", "seg_substep", "seg_energy",
-    "seg_eigenvalue_estimates", "seg_labels", "seg_get_stats", "seg_last_error",
+    "seg_eigenvalue_estimates", "seg_energy_p", "seg_prolong", "seg_continue", "seg_labels", "seg_get_stats", "seg_last_error",
     "seg_time_kernel", "seg_launch_info", "seg_autotune", "seg_s_eps_noalloc",
     "seg_batch_create", "seg_batch_step", "seg_batch_step_async", "seg_batch_sync", "seg_batch_destroy",
     "seg_server_create", "seg_server_submit", "seg_server_tick", "seg_server_info", "seg_server_result",
@@ -138,9 +138,12 @@ _SIG = {
     "seg_mesh_icosphere": [_i32, _pp],
     "seg_mesh_ellipsoid": [_i32, _d, _d, _d, _pp],
     "seg_mesh_torus": [_i32, _i32, _d, _d, _pp],
+    "seg_mesh_dziuk": [_i32, _pp],
+    "seg_mesh_refine": [_vp, _vp, _pp, _vp],
     "seg_mesh_info": [_vp, _vp, _vp],
     "seg_mesh_get": [_vp, _vp, _vp],
     "seg_assemble": [_vp, _d, C.c_int, _pp],
+    "seg_assemble_ex": [_vp, _d, C.c_int, C.c_uint32, _pp],
     "seg_problem_info": [_vp, _vp, _vp, _vp, _vp],
     "seg_state_create": [_vp, _i32, _d, C.c_int, C.c_uint64, _vp, _vp, _pp],
     "seg_set_u": [_vp, _vp, _i32],
@@ -151,6 +154,9 @@ _SIG = {
     "seg_substep": [_vp, _i32],
     "seg_energy": [_vp, _vp, _vp, _vp, _vp],
     "seg_eigenvalue_estimates": [_vp, _vp, _vp],
+    "seg_energy_p": [_vp, _d, _vp],
+    "seg_prolong": [_vp, _vp, _vp],
+    "seg_continue": [_vp, _vp, _vp, _d, _d, _vp, _pp, _pp, _pp],
     "seg_labels": [_vp, _vp, _vp],
     "seg_get_stats": [_vp, _vp],
     "seg_time_kernel": [_vp, _i32, _i32, _vp],
@@ -268,6 +274,34 @@ def seg_mesh_torus(nu: int, nv: int, R: float, r: float) -> Mesh:
     return Mesh(out)
 
 
+SEG_SURFACE_NONE, SEG_SURFACE_ELLIPSOID, SEG_SURFACE_TORUS, SEG_SURFACE_DZIUK = 0, 1, 2, 3
+
+
+class seg_surface(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("reserved", C.c_int32), ("p0", C.c_double), ("p1", C.c_double),
+                ("p2", C.c_double)]
+
+
+def surface(kind: int, p0: float = 0.0, p1: float = 0.0, p2: float = 0.0) -> seg_surface:
+    return seg_surface(kind, 0, p0, p1, p2)
+
+
+def seg_mesh_dziuk(level: int) -> Mesh:
+    out = C.c_void_p()
+    _check(lib.seg_mesh_dziuk(level, C.byref(out)))
+    return Mesh(out)
+
+
+def seg_mesh_refine(mesh: Mesh, surf: seg_surface):
+    """Returns (fine mesh, parents[n_fine, 2] int32)."""
+    n, f = seg_mesh_info(mesh)
+    parents = np.empty((n + 3 * f, 2), dtype=np.int32)
+    out = C.c_void_p()
+    _check(lib.seg_mesh_refine(mesh.ptr, C.byref(surf), C.byref(out), _ptr(parents)))
+    fine = Mesh(out)
+    return fine, parents[: seg_mesh_info(fine)[0]].copy()
+
+
 def seg_mesh_info(mesh: Mesh):
     n, f = C.c_int64(), C.c_int64()
     _check(lib.seg_mesh_info(mesh.ptr, C.byref(n), C.byref(f)))
@@ -289,9 +323,18 @@ def seg_mesh_destroy(mesh: Mesh):
 # ---------------------------------------------------------------- assembly
 
 
+SEG_ASSEMBLE_LUMPED_MASS = 1
+
+
 def seg_assemble(mesh: Mesh, tau: float, precision: int = SEG_FP64) -> Problem:
     out = C.c_void_p()
     _check(lib.seg_assemble(mesh.ptr, tau, precision, C.byref(out)))
+    return Problem(out)
+
+
+def seg_assemble_ex(mesh: Mesh, tau: float, precision: int = SEG_FP64, flags: int = 0) -> Problem:
+    out = C.c_void_p()
+    _check(lib.seg_assemble_ex(mesh.ptr, tau, precision, flags, C.byref(out)))
     return Problem(out)
 
 
@@ -460,6 +503,29 @@ def seg_eigenvalue_estimates(state: State):
     lam_cl = np.empty(state.m, dtype=np.float64)
     _check(lib.seg_eigenvalue_estimates(state.ptr, _ptr(lam), _ptr(lam_cl)))
     return lam, lam_cl
+
+
+def seg_energy_p(state: State, p: float) -> float:
+    e = C.c_double()
+    _check(lib.seg_energy_p(state.ptr, p, C.byref(e)))
+    return e.value
+
+
+def seg_prolong(coarse: State, fine: State, parents):
+    parents = np.ascontiguousarray(parents, dtype=np.int32)
+    _check(lib.seg_prolong(coarse.ptr, fine.ptr, _ptr(parents)))
+
+
+def seg_continue(coarse: State, coarse_mesh: Mesh, surf: seg_surface, eps_next: float, tau_next: float,
+                 params: seg_params | None = None):
+    """Returns (fine mesh, fine problem, fine state)."""
+    fm, fp, fs = C.c_void_p(), C.c_void_p(), C.c_void_p()
+    _check(lib.seg_continue(coarse.ptr, coarse_mesh.ptr, C.byref(surf), eps_next, tau_next,
+                            C.byref(params) if params is not None else None, C.byref(fm), C.byref(fp),
+                            C.byref(fs)))
+    mesh = Mesh(fm)
+    prob = Problem(fp)
+    return mesh, prob, State(fs, prob, coarse.m)
 
 
 def seg_labels(state: State):

@@ -49,6 +49,7 @@ struct seg_problem {
   seg_precision prec = SEG_FP64;
   int device = 0;
   int ell_w = 8;
+  uint32_t flags = 0;  // seg_assemble_ex flags
   int* ell_col = nullptr;
   void* valA = nullptr;
   void* valM = nullptr;
@@ -103,6 +104,17 @@ struct seg_state {
 namespace {
 
 size_t vsize(seg_precision p) { return p == SEG_MIXED_FP32 ? sizeof(float) : sizeof(double); }
+
+// P1 interpolation onto a refined mesh (caller numbering, float64):
+// uf[z][i] = (uc[a][i] + uc[b][i]) / 2 with (a, b) = parents of z.
+__global__ void k_prolong(const double* uc, const int32_t* parents, double* uf, long long nf, int m) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nf * m) return;
+  const long long z = k / m;
+  const int i = (int)(k % m);
+  const long long a = parents[2 * z], b = parents[2 * z + 1];
+  uf[k] = 0.5 * (uc[a * m + i] + uc[b * m + i]);
+}
 
 // Bytes of the partial-sum buffer: up to kMaxDots * ms sums over `grid` row
 // blocks or one sum over `grid_e` triangle blocks, each followed by its
@@ -449,6 +461,40 @@ seg_status seg_mesh_torus(int32_t nu, int32_t nv, double R, double r, seg_mesh**
   return SEG_OK;
 }
 
+seg_status seg_mesh_dziuk(int32_t level, seg_mesh** out) {
+  if (!out) return fail(SEG_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (level < 0 || level > 10) return fail(SEG_ERR_ARG, "surface (D) level must be in [0, 10]");
+  seg_mesh* m = new (std::nothrow) seg_mesh;
+  if (!m) return fail(SEG_ERR_NO_MEMORY, "host allocation failed");
+  make_dziuk(level, &m->h);
+  *out = m;
+  return SEG_OK;
+}
+
+seg_status seg_mesh_refine(const seg_mesh* coarse, const seg_surface* surf, seg_mesh** fine, int32_t* parents) {
+  if (!fine) return fail(SEG_ERR_ARG, "fine is NULL");
+  *fine = nullptr;
+  if (!coarse || !surf) return fail(SEG_ERR_ARG, "coarse mesh or surface is NULL");
+  if (surf->reserved != 0) return fail(SEG_ERR_ARG, "surface.reserved must be 0");
+  if (surf->kind < SEG_SURFACE_NONE || surf->kind > SEG_SURFACE_DZIUK) return fail(SEG_ERR_ARG, "unknown surface kind");
+  if (surf->kind == SEG_SURFACE_ELLIPSOID && !(surf->p0 > 0 && surf->p1 > 0 && surf->p2 > 0))
+    return fail(SEG_ERR_ARG, "ellipsoid semi-axes must be positive");
+  if (surf->kind == SEG_SURFACE_TORUS && !(surf->p1 > 0 && surf->p0 > surf->p1))
+    return fail(SEG_ERR_ARG, "torus radii need p0 > p1 > 0");
+  const HostMesh& h = coarse->h;
+  // fine sizes: n + edges <= n + 3f, 4f triangles; keep 32-bit indices
+  if (h.n + 3 * h.f >= ((int64_t)1 << 31) || 4 * h.f >= ((int64_t)1 << 31))
+    return fail(SEG_ERR_ARG, "refined mesh would exceed 32-bit indices");
+  seg_mesh* m = new (std::nothrow) seg_mesh;
+  if (!m) return fail(SEG_ERR_NO_MEMORY, "host allocation failed");
+  std::vector<int32_t> par;
+  refine_mesh(h, SurfaceDesc{surf->kind, surf->p0, surf->p1, surf->p2}, &m->h, parents ? &par : nullptr);
+  if (parents) std::copy(par.begin(), par.end(), parents);
+  *fine = m;
+  return SEG_OK;
+}
+
 seg_status seg_mesh_info(const seg_mesh* mesh, int64_t* n_vert, int64_t* n_tri) {
   if (!mesh) return fail(SEG_ERR_ARG, "mesh is NULL");
   if (n_vert) *n_vert = mesh->h.n;
@@ -468,14 +514,28 @@ void seg_mesh_destroy(seg_mesh* mesh) { delete mesh; }
 // ---------------------------------------------------------------- assembly
 
 seg_status seg_assemble(const seg_mesh* mesh, double tau, seg_precision precision, seg_problem** out) {
+  return seg_assemble_ex(mesh, tau, precision, 0u, out);
+}
+
+seg_status seg_assemble_ex(const seg_mesh* mesh, double tau, seg_precision precision, uint32_t flags,
+                           seg_problem** out) {
   if (!out) return fail(SEG_ERR_ARG, "out is NULL");
   *out = nullptr;
   if (!mesh) return fail(SEG_ERR_ARG, "mesh is NULL");
   if (!(tau > 0) || !std::isfinite(tau)) return fail(SEG_ERR_ARG, "tau must be positive and finite");
   if (precision != SEG_FP64 && precision != SEG_MIXED_FP32) return fail(SEG_ERR_ARG, "unknown precision");
+  if (flags & ~(uint32_t)SEG_ASSEMBLE_LUMPED_MASS) return fail(SEG_ERR_ARG, "unknown assembly flag");
   HostCSR csr;
   assemble_p1(mesh->h, &csr);
   const int64_t n = csr.n;
+  if (flags & SEG_ASSEMBLE_LUMPED_MASS) {
+    // M_L = diag(row sums of M); the sparsity pattern stays (K uses it)
+    for (int64_t i = 0; i < n; ++i) {
+      double rs = 0.0;
+      for (int32_t e = csr.rowptr[i]; e < csr.rowptr[i + 1]; ++e) rs += csr.M[e];
+      for (int32_t e = csr.rowptr[i]; e < csr.rowptr[i + 1]; ++e) csr.M[e] = csr.col[e] == i ? rs : 0.0;
+    }
+  }
   std::vector<double> A(csr.nnz), dinv(n), diag(n);
   for (int64_t e = 0; e < csr.nnz; ++e) A[e] = csr.M[e] + tau * csr.K[e];
   for (int64_t i = 0; i < n; ++i) {
@@ -508,6 +568,7 @@ seg_status seg_assemble(const seg_mesh* mesh, double tau, seg_precision precisio
   seg_problem* p = new (std::nothrow) seg_problem;
   if (!p) return fail(SEG_ERR_NO_MEMORY, "host allocation failed");
   p->ell_w = W;
+  p->flags = flags;
   p->n = n;
   p->nnz = csr.nnz;
   p->f = mesh->h.f;
@@ -1065,6 +1126,90 @@ seg_status seg_eigenvalue_estimates(seg_state* s, double* lambda, double* lambda
     if (lambda_cl) lambda_cl[i] = c.lam[i] + 2.0 * c.coup[i] / (s->eps * s->eps);
   }
   return (c.status & 2) ? status_from_ctl(c) : SEG_OK;
+}
+
+seg_status seg_energy_p(seg_state* s, double p, double* e_p) {
+  if (!s || !e_p) return fail(SEG_ERR_ARG, "state or output is NULL");
+  if (!(p >= 1.0)) return fail(SEG_ERR_ARG, "p must be >= 1 (or +inf)");
+  seg_status st = evaluate_energy(s, false);
+  if (st != SEG_OK) return st;
+  const DevCtl& c = *s->hctl;
+  if (std::isinf(p)) {
+    double mx = c.lam[0];
+    for (int i = 1; i < s->m; ++i) mx = std::max(mx, c.lam[i]);
+    *e_p = mx;
+  } else {
+    // scaled by the largest value so that lambda^p cannot overflow
+    double top = c.lam[0];
+    for (int i = 1; i < s->m; ++i) top = std::max(top, c.lam[i]);
+    double acc = 0.0;
+    for (int i = 0; i < s->m; ++i) acc += top > 0.0 ? std::pow(c.lam[i] / top, p) : 0.0;
+    *e_p = top > 0.0 ? top * std::pow(acc / s->m, 1.0 / p) : 0.0;
+  }
+  return (c.status & 2) ? status_from_ctl(c) : SEG_OK;
+}
+
+seg_status seg_prolong(seg_state* coarse, seg_state* fine, const int32_t* parents) {
+  if (!coarse || !fine || !parents) return fail(SEG_ERR_ARG, "coarse, fine or parents is NULL");
+  if (coarse->m != fine->m) return fail(SEG_ERR_ARG, "coarse and fine states need the same m");
+  if (coarse->p->device != fine->p->device) return fail(SEG_ERR_ARG, "states live on different devices");
+  const int64_t nc = coarse->p->n, nf = fine->p->n;
+  for (int64_t k = 0; k < 2 * nf; ++k)
+    if (parents[k] < 0 || parents[k] >= nc) return fail(SEG_ERR_ARG, "parent index out of range");
+  SEG_CUDA(cudaSetDevice(fine->p->device));
+  const int m = fine->m;
+  double* uc = nullptr;
+  double* uf = nullptr;
+  int32_t* par = nullptr;
+  cudaError_t ce = cudaMalloc(&uc, (size_t)nc * m * sizeof(double));
+  if (ce == cudaSuccess) ce = cudaMalloc(&uf, (size_t)nf * m * sizeof(double));
+  if (ce == cudaSuccess) ce = cudaMalloc(&par, (size_t)nf * 2 * sizeof(int32_t));
+  seg_status st = SEG_OK;
+  if (ce != cudaSuccess) st = fail(SEG_ERR_NO_MEMORY, std::string("cudaMalloc: ") + cudaGetErrorString(ce));
+  if (st == SEG_OK) st = seg_get_u(coarse, uc, 1);  // caller numbering, synchronised
+  if (st == SEG_OK) {
+    ce = cudaMemcpyAsync(par, parents, (size_t)nf * 2 * sizeof(int32_t), cudaMemcpyHostToDevice, fine->stream);
+    if (ce == cudaSuccess) {
+      const long long total = (long long)nf * m;
+      k_prolong<<<(unsigned)((total + 255) / 256), 256, 0, fine->stream>>>(uc, par, uf, nf, m);
+      ce = cudaGetLastError();
+    }
+    if (ce != cudaSuccess) st = fail(SEG_ERR_CUDA, std::string("prolongation: ") + cudaGetErrorString(ce));
+  }
+  if (st == SEG_OK) st = seg_set_u(fine, uf, 1);  // synchronises fine's stream
+  cudaFree(uc);
+  cudaFree(uf);
+  cudaFree(par);
+  return st;
+}
+
+seg_status seg_continue(seg_state* coarse, const seg_mesh* coarse_mesh, const seg_surface* surf, double eps_next,
+                        double tau_next, const seg_params* opt, seg_mesh** fine_mesh, seg_problem** fine_problem,
+                        seg_state** fine_state) {
+  if (!fine_mesh || !fine_problem || !fine_state) return fail(SEG_ERR_ARG, "an output is NULL");
+  *fine_mesh = nullptr;
+  *fine_problem = nullptr;
+  *fine_state = nullptr;
+  if (!coarse || !coarse_mesh || !surf) return fail(SEG_ERR_ARG, "coarse state, mesh or surface is NULL");
+  if (coarse_mesh->h.n != coarse->p->n) return fail(SEG_ERR_ARG, "coarse mesh does not match the coarse state");
+  seg_mesh* fm = nullptr;
+  seg_problem* fp = nullptr;
+  seg_state* fs = nullptr;
+  std::vector<int32_t> parents(2 * (coarse_mesh->h.n + 3 * coarse_mesh->h.f));
+  seg_status st = seg_mesh_refine(coarse_mesh, surf, &fm, parents.data());
+  if (st == SEG_OK) st = seg_assemble_ex(fm, tau_next, coarse->prec, coarse->p->flags, &fp);
+  if (st == SEG_OK) st = seg_state_create(fp, coarse->m, eps_next, SEG_INIT_UNIFORM, 0, opt, nullptr, &fs);
+  if (st == SEG_OK) st = seg_prolong(coarse, fs, parents.data());
+  if (st != SEG_OK) {
+    seg_state_destroy(fs);
+    seg_problem_destroy(fp);
+    seg_mesh_destroy(fm);
+    return st;
+  }
+  *fine_mesh = fm;
+  *fine_problem = fp;
+  *fine_state = fs;
+  return SEG_OK;
 }
 
 seg_status seg_labels(seg_state* s, int32_t* argmax, uint8_t* v_positive) {

@@ -67,7 +67,7 @@ static void normalise3(double* p) {
   p[2] /= s;
 }
 
-void make_icosphere(int level, HostMesh* out) {
+static void make_icosahedral(int level, bool dziuk, HostMesh* out) {
   const double phi = (1.0 + std::sqrt(5.0)) / 2.0;
   std::vector<double> xyz;
   for (double s1 : {-1.0, 1.0}) {
@@ -107,47 +107,109 @@ void make_icosphere(int level, HostMesh* out) {
     }
   for (int v = 0; v < n0; ++v) normalise3(&xyz[3 * v]);
 
-  for (int l = 0; l < level; ++l) {
-    const int64_t n = (int64_t)xyz.size() / 3;
-    const int64_t f = (int64_t)tri.size() / 3;
-    std::vector<int64_t> keys(3 * f);
-    for (int64_t t = 0; t < f; ++t) {
-      for (int k = 0; k < 3; ++k) {
-        int64_t a = tri[3 * t + k], b = tri[3 * t + (k + 1) % 3];
-        int64_t lo = std::min(a, b), hi = std::max(a, b);
-        keys[k * f + t] = lo * n + hi;  // edge k of triangle t: (a,b), (b,c), (c,a)
-      }
-    }
-    std::vector<int64_t> ukeys(keys);
-    std::sort(ukeys.begin(), ukeys.end());
-    ukeys.erase(std::unique(ukeys.begin(), ukeys.end()), ukeys.end());
-    const int64_t ne = (int64_t)ukeys.size();
-    std::vector<double> nxyz(3 * (n + ne));
-    std::copy(xyz.begin(), xyz.end(), nxyz.begin());
-    for (int64_t e = 0; e < ne; ++e) {
-      int64_t lo = ukeys[e] / n, hi = ukeys[e] % n;
-      double* p = &nxyz[3 * (n + e)];
-      for (int k = 0; k < 3; ++k) p[k] = xyz[3 * lo + k] + xyz[3 * hi + k];
-      normalise3(p);
-    }
-    auto mid = [&](int64_t key) {
-      return (int32_t)(n + (std::lower_bound(ukeys.begin(), ukeys.end(), key) - ukeys.begin()));
-    };
-    std::vector<int32_t> ntri(12 * f);
-    for (int64_t t = 0; t < f; ++t) {
-      int32_t a = tri[3 * t], b = tri[3 * t + 1], c = tri[3 * t + 2];
-      int32_t ab = mid(keys[t]), bc = mid(keys[f + t]), ca = mid(keys[2 * f + t]);
-      int32_t blocks[4][3] = {{a, ab, ca}, {b, bc, ab}, {c, ca, bc}, {ab, bc, ca}};
-      for (int q = 0; q < 4; ++q)
-        for (int k = 0; k < 3; ++k) ntri[3 * (q * f + t) + k] = blocks[q][k];
-    }
-    xyz.swap(nxyz);
-    tri.swap(ntri);
+  HostMesh m;
+  m.xyz.swap(xyz);
+  m.tri.swap(tri);
+  m.n = (int64_t)m.xyz.size() / 3;
+  m.f = (int64_t)m.tri.size() / 3;
+  if (dziuk) {
+    for (int64_t v = 0; v < m.n; ++v) project_point(&m.xyz[3 * v], SurfaceDesc{SEG_SURFACE_DZIUK, 0, 0, 0});
   }
-  out->xyz.swap(xyz);
-  out->tri.swap(tri);
-  out->n = (int64_t)out->xyz.size() / 3;
-  out->f = (int64_t)out->tri.size() / 3;
+  const SurfaceDesc surf{dziuk ? SEG_SURFACE_DZIUK : SEG_SURFACE_ELLIPSOID, 1.0, 1.0, 1.0};
+  for (int l = 0; l < level; ++l) {
+    HostMesh fine;
+    refine_mesh(m, surf, &fine, nullptr);
+    m = std::move(fine);
+  }
+  *out = std::move(m);
+}
+
+void make_icosphere(int level, HostMesh* out) { make_icosahedral(level, false, out); }
+void make_dziuk(int level, HostMesh* out) { make_icosahedral(level, true, out); }
+
+void project_point(double* p, const SurfaceDesc& s) {
+  switch (s.kind) {
+    case SEG_SURFACE_ELLIPSOID: {
+      const double q0 = p[0] / s.p0, q1 = p[1] / s.p1, q2 = p[2] / s.p2;
+      const double q = std::sqrt(q0 * q0 + q1 * q1 + q2 * q2);
+      for (int k = 0; k < 3; ++k) p[k] /= q;
+      break;
+    }
+    case SEG_SURFACE_TORUS: {
+      // closest point: the nearest point of the core circle of radius R, then
+      // distance r from it towards p
+      const double R = s.p0, r = s.p1;
+      const double rho = std::sqrt(p[0] * p[0] + p[1] * p[1]);
+      const double c[3] = {R * p[0] / rho, R * p[1] / rho, 0.0};
+      const double d[3] = {p[0] - c[0], p[1] - c[1], p[2] - c[2]};
+      const double dn = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+      for (int k = 0; k < 3; ++k) p[k] = c[k] + r * d[k] / dn;
+      break;
+    }
+    case SEG_SURFACE_DZIUK: {
+      // Newton projection onto Phi = 0 along the gradient:
+      // x <- x - Phi(x) grad Phi(x) / |grad Phi(x)|^2 until |Phi| <= 1e-14
+      for (int it = 0; it < 50; ++it) {
+        const double w = p[0] - p[2] * p[2];
+        const double phi = w * w + p[1] * p[1] + p[2] * p[2] - 1.0;
+        if (!(std::fabs(phi) > 1e-14)) break;
+        const double g[3] = {2.0 * w, 2.0 * p[1], 2.0 * p[2] - 4.0 * p[2] * w};
+        const double g2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+        const double f = phi / g2;
+        for (int k = 0; k < 3; ++k) p[k] -= f * g[k];
+      }
+      break;
+    }
+    default:
+      break;  // SEG_SURFACE_NONE: keep the point
+  }
+}
+
+void refine_mesh(const HostMesh& in, const SurfaceDesc& surf, HostMesh* out, std::vector<int32_t>* parents) {
+  const int64_t n = in.n, f = in.f;
+  std::vector<int64_t> keys(3 * f);
+  for (int64_t t = 0; t < f; ++t) {
+    for (int k = 0; k < 3; ++k) {
+      int64_t a = in.tri[3 * t + k], b = in.tri[3 * t + (k + 1) % 3];
+      int64_t lo = std::min(a, b), hi = std::max(a, b);
+      keys[k * f + t] = lo * n + hi;  // edge k of triangle t: (a,b), (b,c), (c,a)
+    }
+  }
+  std::vector<int64_t> ukeys(keys);
+  std::sort(ukeys.begin(), ukeys.end());
+  ukeys.erase(std::unique(ukeys.begin(), ukeys.end()), ukeys.end());
+  const int64_t ne = (int64_t)ukeys.size();
+  HostMesh m;
+  m.n = n + ne;
+  m.f = 4 * f;
+  m.xyz.resize(3 * m.n);
+  std::copy(in.xyz.begin(), in.xyz.end(), m.xyz.begin());
+  if (parents) {
+    parents->resize(2 * m.n);
+    for (int64_t v = 0; v < n; ++v) (*parents)[2 * v] = (*parents)[2 * v + 1] = (int32_t)v;
+  }
+  for (int64_t e = 0; e < ne; ++e) {
+    const int64_t lo = ukeys[e] / n, hi = ukeys[e] % n;
+    double* p = &m.xyz[3 * (n + e)];
+    for (int k = 0; k < 3; ++k) p[k] = 0.5 * (in.xyz[3 * lo + k] + in.xyz[3 * hi + k]);
+    project_point(p, surf);
+    if (parents) {
+      (*parents)[2 * (n + e)] = (int32_t)lo;
+      (*parents)[2 * (n + e) + 1] = (int32_t)hi;
+    }
+  }
+  auto mid = [&](int64_t key) {
+    return (int32_t)(n + (std::lower_bound(ukeys.begin(), ukeys.end(), key) - ukeys.begin()));
+  };
+  m.tri.resize(12 * f);
+  for (int64_t t = 0; t < f; ++t) {
+    int32_t a = in.tri[3 * t], b = in.tri[3 * t + 1], c = in.tri[3 * t + 2];
+    int32_t ab = mid(keys[t]), bc = mid(keys[f + t]), ca = mid(keys[2 * f + t]);
+    int32_t blocks[4][3] = {{a, ab, ca}, {b, bc, ab}, {c, ca, bc}, {ab, bc, ca}};
+    for (int q = 0; q < 4; ++q)
+      for (int k = 0; k < 3; ++k) m.tri[3 * (q * f + t) + k] = blocks[q][k];
+  }
+  *out = std::move(m);
 }
 
 void make_torus(int nu, int nv, double R, double r, HostMesh* out) {

@@ -162,7 +162,16 @@ struct HostMesh {
 
 std::string validate_mesh(const HostMesh& m, seg_status* code);
 void make_icosphere(int level, HostMesh* out);
+void make_dziuk(int level, HostMesh* out);
 void make_torus(int nu, int nv, double R, double r, HostMesh* out);
+
+// Surface that refinement projects new vertices onto (seg_surface of seg.h).
+struct SurfaceDesc {
+  int kind;
+  double p0, p1, p2;
+};
+void project_point(double* p, const SurfaceDesc& s);
+void refine_mesh(const HostMesh& in, const SurfaceDesc& surf, HostMesh* out, std::vector<int32_t>* parents);
 
 struct HostCSR {
   int64_t n = 0, nnz = 0;

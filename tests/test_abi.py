@@ -54,6 +54,7 @@ def test_struct_layouts_match_header(seg):
     assert C.sizeof(seg.seg_request_info) == 64
     assert C.sizeof(seg.seg_stats) == 48
     assert C.sizeof(seg.seg_tune_result) == 136
+    assert C.sizeof(seg.seg_surface) == 32
 
 
 @pytest.mark.parametrize("level", [0, 1, 3, 5])
@@ -72,6 +73,33 @@ def test_native_torus_and_ellipsoid_equal_shared_generator(seg):
     xyz, tri = seg.seg_mesh_get(seg.seg_mesh_ellipsoid(3, 1.0, 0.8, 0.6))
     rx, rt = w.ellipsoid(3, 1.0, 0.8, 0.6)
     assert np.array_equal(tri, rt) and np.abs(xyz - rx).max() < 1e-14
+
+
+def test_native_dziuk_and_refinement_equal_shared_generator(seg):
+    for level in (0, 2, 3):
+        xyz, tri = seg.seg_mesh_get(seg.seg_mesh_dziuk(level))
+        rx, rt = w.dziuk(level)
+        assert np.array_equal(tri, rt) and np.abs(xyz - rx).max() < 1e-15
+    cases = [
+        (w.icosphere(2), ("sphere",), seg.surface(seg.SEG_SURFACE_ELLIPSOID, 1.0, 1.0, 1.0)),
+        (w.ellipsoid(2, 1.0, 0.8, 0.6), ("ellipsoid", 1.0, 0.8, 0.6),
+         seg.surface(seg.SEG_SURFACE_ELLIPSOID, 1.0, 0.8, 0.6)),
+        (w.torus(10, 6, 1.0, 0.4), ("torus", 1.0, 0.4), seg.surface(seg.SEG_SURFACE_TORUS, 1.0, 0.4)),
+        (w.dziuk(1), ("dziuk",), seg.surface(seg.SEG_SURFACE_DZIUK)),
+        (w.torus(7, 5, 1.0, 0.4), ("none",), seg.surface(seg.SEG_SURFACE_NONE)),
+    ]
+    for (x, t), wsurf, csurf in cases:
+        fine, parents = seg.seg_mesh_refine(seg.seg_create_mesh(x, t), csurf)
+        xyz, tri = seg.seg_mesh_get(fine)
+        rx, rt, rp = w.refine(x, t, wsurf)
+        assert np.array_equal(tri, rt) and np.array_equal(parents, rp), wsurf
+        assert np.abs(xyz - rx).max() < 1e-15, wsurf
+    with pytest.raises(seg.SegError) as e:
+        seg.seg_mesh_refine(seg.seg_mesh_icosphere(1), seg.surface(seg.SEG_SURFACE_TORUS, 0.3, 0.4))
+    assert e.value.status == seg.SEG_ERR_ARG
+    with pytest.raises(seg.SegError) as e:
+        seg.seg_mesh_refine(seg.seg_mesh_icosphere(1), seg.surface(7))
+    assert e.value.status == seg.SEG_ERR_ARG
 
 
 def test_mesh_validation_errors(seg):

@@ -113,3 +113,26 @@ def test_transposed_gradient_map_is_caught(monkeypatch):
     monkeypatch.setattr(o, "p1_gradients", wrong_grads)
     _, bad_K = o.assemble(xyz, tri)
     assert abs(bad_K - good_K).max() > 0.1 * abs(good_K).max()
+
+
+def test_planted_mistakes_in_the_variants_fail_their_pins(monkeypatch):
+    # prolongation taking one parent only: affine functions are no longer reproduced
+    x, t = w.torus(9, 7, 1.0, 0.4)
+    xf, tf, par = w.refine(x, t, ("none",))
+    U = x @ np.array([[0.5], [2.0], [-0.3]])
+    good = np.abs(o.prolong(U, par) - xf @ np.array([[0.5], [2.0], [-0.3]])).max()
+    monkeypatch.setattr(o, "prolong", lambda U, parents: U[parents[:, 0]])
+    bad = np.abs(o.prolong(U, par) - xf @ np.array([[0.5], [2.0], [-0.3]])).max()
+    assert good < 1e-14 and bad > 1e-2
+    monkeypatch.undo()
+    # lumped mass from the consistent diagonal instead of the row sums
+    xyz, tri = w.icosphere(2)
+    M, _ = o.assemble(xyz, tri)
+    rowsum = np.asarray(M.sum(axis=1)).ravel()
+    assert np.abs(o.lumped_mass(xyz, tri).diagonal() - rowsum).max() < 1e-16
+    assert np.abs(M.diagonal() - rowsum).max() > 1e-3
+    # E_p without the 1/m of the mean
+    lam = np.array([2.0, 6.0, 12.0])
+    wrong = float(np.sum(lam ** 2) ** 0.5)
+    assert abs(o.energy_p(lam, 2) - math.sqrt((lam ** 2).mean())) < 1e-14
+    assert abs(wrong - math.sqrt((lam ** 2).mean())) > 1.0

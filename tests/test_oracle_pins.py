@@ -332,3 +332,77 @@ def test_stop_rule_stops_at_first_quiet_check(sph3):
     assert o.check_interval(1e-2) == 10
     assert k == 10 and len(hist) == 2
     assert abs(hist[0] - o.constant_state_s_eps(3, area, 0.3)) < 1e-10
+
+
+# ------------------------------------------- variants and continuation pins
+
+
+def test_lumped_mass_is_vertex_quadrature(sph3):
+    """M_L = diag(|star(z)|/3) equals the row sums of the consistent mass
+    matrix (sum_b |T|(1 + delta_ab)/12 = |T|/3), integrates constants and
+    linear functions exactly on every flat triangle (vertex rule)."""
+    xyz, tri, M, K = sph3
+    ML = o.lumped_mass(xyz, tri)
+    assert np.abs(ML.diagonal() - np.asarray(M.sum(axis=1)).ravel()).max() < 1e-16
+    assert ML.nnz == xyz.shape[0]
+    one = np.ones(xyz.shape[0])
+    assert abs(one @ ML @ one - o.triangle_areas(xyz, tri).sum()) < 1e-13
+    # a linear function f = c.x: int_Gamma_h f by the exact centroid rule on each
+    # flat triangle equals 1^T M_L f
+    c = np.array([0.3, -0.7, 0.2])
+    f = xyz @ c
+    cent = xyz[tri].mean(1) @ c
+    assert abs(one @ ML @ f - (o.triangle_areas(xyz, tri) * cent).sum()) < 1e-14
+
+
+def test_energy_p_power_means():
+    lam = np.array([2.0, 6.0, 12.0, 20.0])
+    assert o.energy_p(lam, 1) == pytest.approx(lam.mean(), rel=1e-15)
+    assert o.energy_p(lam, 2) == pytest.approx(math.sqrt((lam ** 2).mean()), rel=1e-15)
+    assert o.energy_p(lam, math.inf) == 20.0
+    ps = [1, 1.5, 2, 4, 8, 32]
+    vals = [o.energy_p(lam, p) for p in ps]
+    assert all(a <= b for a, b in zip(vals, vals[1:]))  # power-mean inequality
+    assert o.energy_p(lam, 400) == pytest.approx(20.0 * 0.25 ** (1 / 400), rel=1e-3)
+    assert o.energy_p(np.full(5, 7.5), 3.7) == pytest.approx(7.5, rel=1e-14)
+    with pytest.raises(ValueError):
+        o.energy_p(lam, 0.5)
+
+
+def test_prolongation_is_p1_interpolation():
+    """Before projection the fine vertices are edge midpoints of the coarse
+    polyhedron, where a P1 function takes the mean of the edge's end values:
+    affine functions are reproduced exactly, constants stay constant."""
+    x, t = w.torus(9, 7, 1.0, 0.4)
+    xf, tf, par = w.refine(x, t, ("none",))
+    A = np.array([[0.5, -1.0], [2.0, 0.25], [-0.3, 0.8]])
+    b = np.array([1.5, -2.0])
+    U = x @ A + b
+    assert np.abs(o.prolong(U, par) - (xf @ A + b)).max() < 1e-14
+    assert np.array_equal(o.prolong(np.full((len(x), 3), 0.7), par), np.full((len(xf), 3), 0.7))
+    # on the sphere the values are those at the unprojected midpoints
+    x, t = w.icosphere(1)
+    xf, tf, par = w.refine(x, t, ("sphere",))
+    U = x @ A
+    mid = 0.5 * (x[par[:, 0]] + x[par[:, 1]])
+    assert np.abs(o.prolong(U, par) - mid @ A).max() < 1e-15
+
+
+def test_continuation_first_level_is_a_plain_run_and_levels_chain():
+    x0, t0 = w.icosphere(1)
+    x1, t1, p1 = w.refine(x0, t0, ("sphere",))
+    U0 = w.initial_values("uniform", 5, len(x0), 3)
+    eps, tau, steps = 0.2, 2e-3, 4
+    out = o.continuation([(x0, t0, None), (x1, t1, p1)], U0, eps, tau, steps)
+    M, K = o.assemble(x0, t0)
+    U = o.initial_state(M, U0)
+    for _ in range(steps):
+        U = o.step(M, K, tau, eps, U)
+    assert np.abs(out[0][0] - U).max() < 1e-13
+    # level 1 = a plain run from the normalised interpolant with eps/2, tau/2
+    M1, K1 = o.assemble(x1, t1)
+    V = o.normalise(M1, o.prolong(U, p1))
+    for _ in range(steps):
+        V = o.step(M1, K1, tau / 2, eps / 2, V)
+    assert np.abs(out[1][0] - V).max() < 1e-13
+    assert out[1][1]["total"] == pytest.approx(o.energy(x1, t1, K1, V, eps / 2)["total"], rel=1e-14)

@@ -99,3 +99,67 @@ def test_onehot_choice():
     u = w.initial_values("onehot", 3, 10000, m)
     assert np.array_equal(u.sum(1), np.ones(10000))
     assert np.array_equal(u.argmax(1), c)
+
+
+# --- refinement with projection, surface (D) (Sec. 3.3, Sec. 3.4) ----------
+
+
+@pytest.mark.parametrize("level", [0, 1, 2, 3])
+def test_refining_the_icosphere_gives_the_next_level(level):
+    x, t = w.icosphere(level)
+    xf, tf, par = w.refine(x, t, ("sphere",))
+    x1, t1 = w.icosphere(level + 1)
+    assert np.array_equal(xf, x1) and np.array_equal(tf, t1)
+    assert np.array_equal(par[: len(x)], np.stack([np.arange(len(x))] * 2, 1))
+
+
+def test_flat_refinement_midpoints_and_children():
+    x, t = w.torus(6, 5, 1.0, 0.4)
+    xf, tf, par = w.refine(x, t, ("none",))
+    n, f = len(x), len(t)
+    assert len(xf) == n + 3 * f // 2 and len(tf) == 4 * f  # closed surface: E = 3F/2
+    assert np.array_equal(xf[n:], 0.5 * (x[par[n:, 0]] + x[par[n:, 1]]))
+    assert (par[n:, 0] < par[n:, 1]).all()
+    # the four children of a triangle tile it: equal total area, shared corners
+    def area(p, tri):
+        return 0.5 * np.linalg.norm(np.cross(p[tri[:, 1]] - p[tri[:, 0]], p[tri[:, 2]] - p[tri[:, 0]]), axis=1)
+    a0 = area(x, t)
+    a1 = area(xf, tf).reshape(4, f).sum(0)
+    assert np.allclose(a0, a1, rtol=1e-13)
+    assert np.array_equal(tf[:f, 0], t[:, 0]) and np.array_equal(tf[f:2 * f, 0], t[:, 1])
+    # every edge of the fine mesh is shared by exactly two triangles
+    e = np.sort(np.concatenate([tf[:, [0, 1]], tf[:, [1, 2]], tf[:, [2, 0]]]), axis=1)
+    _, cnt = np.unique(e, axis=0, return_counts=True)
+    assert (cnt == 2).all()
+
+
+def test_refinement_projects_onto_torus_and_ellipsoid():
+    x, t = w.torus(12, 8, 1.0, 0.4)
+    xf, _, _ = w.refine(x, t, ("torus", 1.0, 0.4))
+    rho = np.sqrt(xf[:, 0] ** 2 + xf[:, 1] ** 2)
+    assert np.abs((rho - 1.0) ** 2 + xf[:, 2] ** 2 - 0.16).max() < 1e-14
+    x, t = w.ellipsoid(2, 1.0, 0.8, 0.6)
+    xf, _, _ = w.refine(x, t, ("ellipsoid", 1.0, 0.8, 0.6))
+    q = (xf[:, 0] / 1.0) ** 2 + (xf[:, 1] / 0.8) ** 2 + (xf[:, 2] / 0.6) ** 2
+    assert np.abs(q - 1.0).max() < 1e-14
+
+
+def test_dziuk_surface_mesh():
+    for level in range(4):
+        x, t = w.dziuk(level)
+        assert len(x) == 10 * 4 ** level + 2 and len(t) == 20 * 4 ** level
+        phi, grad = w.dziuk_phi(x)
+        assert np.abs(phi).max() <= 1e-14
+    # outward orientation kept: normals point away from the origin-star
+    nrm = np.cross(x[t[:, 1]] - x[t[:, 0]], x[t[:, 2]] - x[t[:, 0]])
+    assert (np.einsum("ij,ij->i", nrm, x[t].mean(1)) > 0).all()
+    # Newton projection of a point already on the surface is the identity;
+    # the unit circle x3 = 0 lies on (D)
+    s = np.array([[np.cos(0.3), np.sin(0.3), 0.0]])
+    assert np.array_equal(w.project_dziuk(s), s)
+    # the gradient formula matches central differences
+    p = np.array([[0.3, -0.4, 0.5]])
+    _, g = w.dziuk_phi(p)
+    h = 1e-6
+    fd = [(w.dziuk_phi(p + h * e)[0] - w.dziuk_phi(p - h * e)[0])[0] / (2 * h) for e in np.eye(3)]
+    assert np.allclose(g[0], fd, atol=1e-8)

@@ -8,5 +8,5 @@ oracle and the GPU path can consume identical inputs without sharing any code
 that computes results.
 """
 
-from .meshes import icosphere, ellipsoid, torus, mesh_by_name  # noqa: F401
+from .meshes import icosphere, ellipsoid, torus, dziuk, refine, project_dziuk, dziuk_phi, mesh_by_name  # noqa: F401
 from .rng import splitmix64, uniform01, onehot_choice, initial_values  # noqa: F401

@@ -13,6 +13,14 @@ used by the workloads:
   radius r around a circle of radius R, each grid quad split along one fixed
   diagonal.
 
+* ``dziuk(level)``: surface (D) of Sec. 3.4, {Phi = 0} with
+  Phi(x) = (x1 - x3^2)^2 + x2^2 + x3^2 - 1: the icosahedron's vertices moved
+  onto it by Newton projection, then ``level`` refinements whose new vertices
+  are projected the same way.
+* ``refine(xyz, tri, surface)``: one global refinement (every triangle into
+  four through its edge midpoints), each midpoint projected onto the named
+  surface; returns the parent edge of every fine vertex as well.
+
 All triangles are oriented with outward normals.  Vertex numbering is
 deterministic: the 12 icosahedron vertices first, then at each level the new
 midpoint vertices in increasing (min endpoint, max endpoint) order.
@@ -81,6 +89,87 @@ def _split_once(xyz, tri):
     return new_xyz, new_tri.astype(np.int32)
 
 
+def _project(p, surface):
+    """Move the points p[k, 3] onto a surface given as a tuple
+    ("none",) | ("sphere",) | ("ellipsoid", a, b, c) | ("torus", R, r) | ("dziuk",)."""
+    kind = surface[0]
+    if kind == "none":
+        return p
+    if kind == "sphere":
+        return p / np.sqrt(p[:, 0] * p[:, 0] + p[:, 1] * p[:, 1] + p[:, 2] * p[:, 2])[:, None]
+    if kind == "ellipsoid":
+        a, b, c = surface[1:4]
+        q = np.sqrt((p[:, 0] / a) ** 2 + (p[:, 1] / b) ** 2 + (p[:, 2] / c) ** 2)
+        return p / q[:, None]
+    if kind == "torus":
+        R, r = surface[1:3]
+        rho = np.sqrt(p[:, 0] ** 2 + p[:, 1] ** 2)
+        ctr = np.stack([R * p[:, 0] / rho, R * p[:, 1] / rho, np.zeros_like(rho)], 1)
+        d = p - ctr
+        return ctr + r * d / np.linalg.norm(d, axis=1)[:, None]
+    if kind == "dziuk":
+        return project_dziuk(p)
+    raise ValueError(f"unknown surface {surface!r}")
+
+
+def dziuk_phi(x):
+    """Phi of surface (D) and its gradient at the points x[k, 3]."""
+    w = x[:, 0] - x[:, 2] ** 2
+    phi = w * w + x[:, 1] ** 2 + x[:, 2] ** 2 - 1.0
+    grad = np.stack([2.0 * w, 2.0 * x[:, 1], 2.0 * x[:, 2] - 4.0 * x[:, 2] * w], 1)
+    return phi, grad
+
+
+def project_dziuk(x, tol=1e-14, maxit=50):
+    """Newton projection onto {Phi = 0}: x <- x - Phi grad / |grad|^2 until
+    |Phi| <= tol (at most maxit iterations per point)."""
+    x = np.array(x, dtype=np.float64, copy=True)
+    for _ in range(maxit):
+        phi, g = dziuk_phi(x)
+        act = np.abs(phi) > tol
+        if not act.any():
+            break
+        g2 = (g * g).sum(1)
+        x[act] -= (phi[act] / g2[act])[:, None] * g[act]
+    return x
+
+
+def refine(xyz, tri, surface):
+    """One global refinement with projection onto `surface`.
+
+    Returns (xyz_fine, tri_fine, parents[N_fine, 2]): the coarse vertices keep
+    their numbers (parents (z, z)), the midpoint of edge (lo, hi) becomes
+    vertex N + (rank of the edge in (lo, hi) order) with parents (lo, hi); the
+    children of triangle t are t, F + t, 2F + t (at its corners a, b, c) and
+    3F + t (the middle one).
+    """
+    n = xyz.shape[0]
+    a, b, c = tri[:, 0].astype(np.int64), tri[:, 1].astype(np.int64), tri[:, 2].astype(np.int64)
+    e = np.stack([np.stack([a, b], 1), np.stack([b, c], 1), np.stack([c, a], 1)], 0)
+    lo = e.min(axis=2)
+    hi = e.max(axis=2)
+    ukey, inv = np.unique((lo * n + hi).ravel(), return_inverse=True)
+    inv = inv.reshape(3, -1)
+    ulo, uhi = ukey // n, ukey % n
+    mid = _project(0.5 * (xyz[ulo] + xyz[uhi]), surface)
+    ab, bc, ca = n + inv[0], n + inv[1], n + inv[2]
+    new_tri = np.concatenate(
+        [np.stack([a, ab, ca], 1), np.stack([b, bc, ab], 1), np.stack([c, ca, bc], 1), np.stack([ab, bc, ca], 1)], 0)
+    parents = np.concatenate([np.stack([np.arange(n), np.arange(n)], 1), np.stack([ulo, uhi], 1)], 0)
+    return np.concatenate([xyz, mid], 0), new_tri.astype(np.int32), parents.astype(np.int32)
+
+
+def dziuk(level: int):
+    """Surface (D): projected icosahedron refined `level` times (Newton projection)."""
+    if level < 0:
+        raise ValueError("level must be >= 0")
+    xyz, tri = _icosahedron()
+    xyz = project_dziuk(xyz)
+    for _ in range(level):
+        xyz, tri, _ = refine(xyz, tri, ("dziuk",))
+    return xyz, tri
+
+
 def icosphere(level: int):
     """Unit sphere mesh: (xyz[N,3] float64, tri[F,3] int32)."""
     if level < 0:
@@ -121,9 +210,11 @@ def torus(nu: int, nv: int, R: float, r: float):
 
 
 def mesh_by_name(spec: str):
-    """'sphere:L', 'ellipsoid:L:a:b:c' or 'torus:nu:nv:R:r'."""
+    """'sphere:L', 'ellipsoid:L:a:b:c', 'torus:nu:nv:R:r' or 'dziuk:L'."""
     parts = spec.split(":")
     kind = parts[0]
+    if kind == "dziuk":
+        return dziuk(int(parts[1]))
     if kind == "sphere":
         return icosphere(int(parts[1]))
     if kind == "ellipsoid":
