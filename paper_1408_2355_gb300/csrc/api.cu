@@ -117,12 +117,9 @@ __global__ void k_prolong(const double* uc, const int32_t* parents, double* uf, 
 }
 
 // Bytes of the partial-sum buffer: up to kMaxDots * ms sums over `grid` row
-// blocks or one sum over `grid_e` triangle blocks, each followed by its
-// per-group-of-32 level (8-byte parts).
+// blocks or one sum over `grid_e` triangle blocks (8-byte parts).
 size_t partial_bytes(int ms, int grid, int grid_e) {
-  const size_t rows = (size_t)kMaxDots * ms * (grid + (grid + 31) / 32);
-  const size_t tris = (size_t)grid_e + (grid_e + 31) / 32;
-  return std::max(rows, tris) * 8;
+  return std::max((size_t)kMaxDots * ms * grid, (size_t)grid_e) * 8;
 }
 
 template <typename T>
@@ -307,8 +304,15 @@ seg_status build_graph_t(seg_state* s) {
   cp.conditional.size = 1;
   SEG_CUDA(cudaGraphAddNode(&n_loop, s->graph, &n_energy, nullptr, 1, &cp));
   cudaGraph_t body = cp.conditional.phGraph_out[0];
-  SEG_CUDA(add_kernel_node<T>(&n_a, body, nullptr, 0, s->ks.cg_a, s->grid, base, s->ks.smem_cg_a));
-  SEG_CUDA(add_kernel_node<T>(&n_b, body, &n_a, 1, s->ks.cg_b, s->grid, base, 0));
+  // kCgUnroll CG iterations per evaluation of the loop condition; passes of
+  // an iteration after the loop has ended return at once (ctl->cont == 0)
+  cudaGraphNode_t prev = nullptr;
+  for (int u = 0; u < kCgUnroll; ++u) {
+    SEG_CUDA(add_kernel_node<T>(&n_a, body, prev ? &prev : nullptr, prev ? 1 : 0, s->ks.cg_a, s->grid, base,
+                                s->ks.smem_cg_a));
+    SEG_CUDA(add_kernel_node<T>(&n_b, body, &n_a, 1, s->ks.cg_b, s->grid, base, 0));
+    prev = n_b;
+  }
   KArgs<T> fin = base;
   fin.apply_x = 1;
   fin.apply_ode = 1;
@@ -989,8 +993,13 @@ seg_status build_batch_t(seg_batch* b) {
   cp.conditional.size = 1;
   SEG_CUDA(cudaGraphAddNode(&n_loop, b->graph, &n_vote0, nullptr, 1, &cp));
   cudaGraph_t body = cp.conditional.phGraph_out[0];
-  SEG_CUDA(add_batch_node<T>(&n_a, body, nullptr, 0, b->ks.b_cg_a, rows, kBlockThreads, b->ks.smem_cg_a));
-  SEG_CUDA(add_batch_node<T>(&n_b, body, &n_a, 1, b->ks.b_cg_b, rows, kBlockThreads, 0));
+  cudaGraphNode_t prev = nullptr;
+  for (int u = 0; u < kCgUnroll; ++u) {
+    SEG_CUDA(add_batch_node<T>(&n_a, body, prev ? &prev : nullptr, prev ? 1 : 0, b->ks.b_cg_a, rows, kBlockThreads,
+                               b->ks.smem_cg_a));
+    SEG_CUDA(add_batch_node<T>(&n_b, body, &n_a, 1, b->ks.b_cg_b, rows, kBlockThreads, 0));
+    prev = n_b;
+  }
   SEG_CUDA(add_batch_node<T>(&n_vote, body, &n_b, 1, b->ks.b_vote, vote, kMaxBatch, 0));
   SEG_CUDA(add_batch_node<T>(&n_fin, b->graph, &n_loop, 1, b->ks.b_finish, rows, kBlockThreads, 0));
   SEG_CUDA(cudaGraphInstantiate(&b->exec, b->graph, 0));

@@ -140,73 +140,57 @@ __device__ __forceinline__ void shfl_add(AccD& a, int off) { a.v += __shfl_xor_s
 __device__ __forceinline__ void zero_part(float2& p) { p = make_float2(0.f, 0.f); }
 __device__ __forceinline__ void zero_part(double& p) { p = 0.0; }
 
-// Deterministic two-level sum over the G blocks of a grid of P partial sums:
+// Deterministic sum over the G blocks of a grid of P partial sums:
 // part[p * G + b] holds block b's partial of sum p (every block has written
-// its own before the call).  The last block of each group of 32 blocks to
-// arrive sums the group's partials in block order (a fixed shuffle tree) into
-// part[P * G + p * NG + group]; the last group to finish sums the NG group
-// partials the same way and calls out(p, total) from one lane per p.  Returns
-// true in that block only.  Must be reached by every block of the grid.
+// its own before the call).  The last block to arrive (ticket) sums them:
+// warp w takes sums w, w + NW, ... two at a time; lane l adds blocks l,
+// l + 32, ... in order (up to 2 x 8 loads in flight), then a fixed shuffle
+// tree; out(p, total) is called from lane 0.  Returns true in that block
+// only.  Must be reached by every block of the grid.
 template <typename Acc, typename Part, typename Out>
-__device__ __forceinline__ bool reduce_blocks(Part* part, unsigned int* gcount, unsigned int* count, int P, int vb,
-                                              int G, Out out) {
+__device__ __forceinline__ bool reduce_blocks(const Part* part, unsigned int* count, int P, int vb, int G, Out out) {
   constexpr int NW = kBlockThreads / 32;
-  constexpr int U = 4;  // sums per warp in flight
+  constexpr int U = 8;  // loads per lane and sum in flight
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   __shared__ unsigned int ticket;
-  const int NG = (G + 31) >> 5;
-  const int grp = vb >> 5, g0 = grp << 5, gn = min(32, G - g0);
-  Part* part1 = part + (size_t)P * G;
+  (void)vb;
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) ticket = atomicAdd(&gcount[grp], 1u);
+  if (threadIdx.x == 0) ticket = atomicAdd(count, 1u);
   __syncthreads();
-  if (ticket != (unsigned int)(gn - 1)) return false;
+  if (ticket != (unsigned int)(G - 1)) return false;
   __threadfence();
-  for (int p0 = warp * U; p0 < P; p0 += NW * U) {
-    Part v[U];
+  for (int p = warp; p < P; p += 2 * NW) {
+    const int q = p + NW;  // second sum of this pass (if any)
+    Acc s0, s1;
+    s0.zero();
+    s1.zero();
+    for (int b0 = 0; b0 < G; b0 += 32 * U) {
+      Part v0[U], v1[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      zero_part(v[u]);
-      if (p0 + u < P && lane < gn) v[u] = __ldcg(&part[(size_t)(p0 + u) * G + g0 + lane]);
+      for (int u = 0; u < U; ++u) {
+        const int b = b0 + u * 32 + lane;
+        zero_part(v0[u]);
+        zero_part(v1[u]);
+        if (b < G) {
+          v0[u] = __ldcg(&part[(size_t)p * G + b]);
+          if (q < P) v1[u] = __ldcg(&part[(size_t)q * G + b]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        add_part(s0, v0[u]);
+        add_part(s1, v1[u]);
+      }
     }
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      Acc s;
-      s.zero();
-      add_part(s, v[u]);
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) shfl_add(s, off);
-      if (lane == 0 && p0 + u < P) part1[(size_t)(p0 + u) * NG + grp] = to_part(s);
+    for (int off = 16; off > 0; off >>= 1) {
+      shfl_add(s0, off);
+      shfl_add(s1, off);
     }
-  }
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    gcount[grp] = 0u;  // every block of the group has arrived
-    ticket = atomicAdd(count, 1u);
-  }
-  __syncthreads();
-  if (ticket != (unsigned int)(NG - 1)) return false;
-  __threadfence();
-  for (int p0 = warp * U; p0 < P; p0 += NW * U) {
-    Part v[U], w[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      zero_part(v[u]);
-      zero_part(w[u]);
-      if (p0 + u < P && lane < NG) v[u] = __ldcg(&part1[(size_t)(p0 + u) * NG + lane]);
-      if (p0 + u < P && lane + 32 < NG) w[u] = __ldcg(&part1[(size_t)(p0 + u) * NG + lane + 32]);
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      Acc s;
-      s.zero();
-      add_part(s, v[u]);
-      add_part(s, w[u]);
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) shfl_add(s, off);
-      if (lane == 0 && p0 + u < P) out(p0 + u, s.value());
+    if (lane == 0) {
+      out(p, s0.value());
+      if (q < P) out(q, s1.value());
     }
   }
   __syncthreads();
@@ -250,7 +234,7 @@ __device__ __forceinline__ bool grid_reduce(typename AccOf<T>::type (&acc)[ND][V
     part[(size_t)(d * a.ms + c) * G + vb] = to_part(s);
   }
   const int ms = a.ms;
-  return reduce_blocks<Acc>(part, a.ctl->gcounters[slot], &a.ctl->counters[slot], ND * ms, vb, G,
+  return reduce_blocks<Acc>(part, &a.ctl->counters[slot], ND * ms, vb, G,
                             [&](int p, double v) { tot[p / ms][p % ms] = v; });
 }
 
@@ -485,19 +469,46 @@ __device__ __forceinline__ void report_timeout(DevCtl* ctl) {
   atomicExch(&ctl->halted, 2);
 }
 
-// Warp-level pipeline over the row groups of the block: group gi covers
-// rows [r0 + gi*RPW, ...); warp w takes groups w, w+NW, ...  The copies of
+// Row groups (RPW consecutive rows) of one block of the staged passes.  The
+// mesh's groups are cut into chunks of kChunkGroups groups dealt round-robin
+// to the blocks (chunk c to block c mod G), so that every block gets rows
+// from all over the mesh: the cost of a row depends on where it lies (the
+// locality of its neighbours), and contiguous ranges per block left some
+// blocks 10% slower than the median.  Local group k of block vb starts at
+// row row0(k).
+constexpr int kChunkGroups = 32;
+struct GroupMap {
+  int n, rpw, vb, vg, ngroups;
+  __device__ __forceinline__ int row0(int k) const {
+    return ((vb + (k / kChunkGroups) * vg) * kChunkGroups + k % kChunkGroups) * rpw;
+  }
+};
+__device__ __forceinline__ GroupMap group_map(int n, int rpw, int vb, int vg) {
+  GroupMap g{n, rpw, vb, vg, 0};
+  const int ngt = (n + rpw - 1) / rpw;
+  const int nch = (ngt + kChunkGroups - 1) / kChunkGroups;
+  if (vb < nch) {
+    const int mine = (nch - 1 - vb) / vg + 1;  // chunks vb, vb + vg, ...
+    const int last = vb + (mine - 1) * vg;
+    g.ngroups = (mine - 1) * kChunkGroups + (last == nch - 1 ? ngt - last * kChunkGroups : kChunkGroups);
+  }
+  return g;
+}
+
+// Warp-level pipeline over the row groups of the block (GroupMap); warp w
+// takes local groups w, w+NW, ...  The copies of
 // the warp's next Stage::kStages - 1 groups are in flight while one group is
 // processed.  `body(stage, row0, nr)` consumes a landed stage.  Returns false
 // if a wait timed out (the copies still in flight are waited for, bounded).
 template <typename Stage, typename Body>
-__device__ __forceinline__ bool row_pipeline(unsigned char* smem_warp, unsigned long long* bars, int r0, int r1,
+__device__ __forceinline__ bool row_pipeline(unsigned char* smem_warp, unsigned long long* bars, const GroupMap& gm,
                                              const typename Stage::Src& src, Body body) {
   constexpr int NW = kBlockThreads / 32;
   constexpr int RPW = Stage::RPW;
   constexpr int NS = Stage::kStages;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int ngroups = (r1 - r0 + RPW - 1) / RPW;
+  const int ngroups = gm.ngroups;
+  const int n = gm.n;
   if (lane == 0) {
 #pragma unroll
     for (int k = 0; k < NS; ++k) mbar_init(&bars[k], 1);
@@ -516,8 +527,8 @@ __device__ __forceinline__ bool row_pipeline(unsigned char* smem_warp, unsigned 
     const int g = warp + k * NW;
     if (g < ngroups) {
       if (lane == 0) {
-        const int row0 = r0 + g * RPW;
-        stage(k).issue(&bars[k], row0, min(RPW, r1 - row0), src);
+        const int row0 = gm.row0(g);
+        stage(k).issue(&bars[k], row0, min(RPW, n - row0), src);
       }
       pending |= 1u << k;
     }
@@ -532,8 +543,8 @@ __device__ __forceinline__ bool row_pipeline(unsigned char* smem_warp, unsigned 
     if (gn < ngroups) {
       if (lane == 0) {
         fence_proxy_async_smem();
-        const int row0 = r0 + gn * RPW;
-        stage(sn).issue(&bars[sn], row0, min(RPW, r1 - row0), src);
+        const int row0 = gm.row0(gn);
+        stage(sn).issue(&bars[sn], row0, min(RPW, n - row0), src);
       }
       pending |= 1u << sn;
     }
@@ -544,8 +555,8 @@ __device__ __forceinline__ bool row_pipeline(unsigned char* smem_warp, unsigned 
     }
     pending &= ~(1u << s);
     phase ^= 1u << s;
-    const int row0 = r0 + gi * RPW;
-    body(stage(s), row0, min(RPW, r1 - row0));
+    const int row0 = gm.row0(gi);
+    body(stage(s), row0, min(RPW, n - row0));
     __syncwarp();
     s = s == NS - 1 ? 0 : s + 1;
   }
@@ -592,7 +603,7 @@ __device__ __forceinline__ void body_start(const KArgs<T>& a, const int vb, cons
   src.val[1] = a.valM;
   src.vec[0] = a.X;
   const bool ok = row_pipeline<Stage>(
-      dyn_smem + warp * Stage::kStages * Stage::kBytes, bars[warp], r0, r1, src, [&](const Stage& sg, int row0, int nr) {
+      dyn_smem + warp * Stage::kStages * Stage::kBytes, bars[warp], group_map(a.n, RPW, vb, vg), src, [&](const Stage& sg, int row0, int nr) {
         if (rs >= nr) return;
         const unsigned row = row0 + rs;
         int cols[W];
@@ -689,6 +700,14 @@ __device__ __forceinline__ void body_cg_a(const KArgs<T>& a, const int vb, const
   extern __shared__ __align__(128) unsigned char dyn_smem[];
   __shared__ __align__(8) unsigned long long bars[NW][kPipeStages];
   const int it = ctl->it;
+  // read now what the last block needs after the grid sum (written only by
+  // other kernels), so that it does not wait for them at the end
+  __shared__ double pre_rz[kMaxCols];
+  __shared__ int pre_act[kMaxCols];
+  if ((int)threadIdx.x < a.ms) {
+    pre_rz[threadIdx.x] = ctl->rz[threadIdx.x];
+    pre_act[threadIdx.x] = ctl->active[threadIdx.x];
+  }
   const T* Pold = (it & 1) ? a.P1 : a.P0;
   T* Pnew = (it & 1) ? a.P0 : a.P1;
   const unsigned ms = a.ms;
@@ -708,7 +727,7 @@ __device__ __forceinline__ void body_cg_a(const KArgs<T>& a, const int vb, const
   src.vec[1] = Pold;
   src.vec[2] = a.X;
   const bool ok = row_pipeline<Stage>(
-      dyn_smem + warp * Stage::kStages * Stage::kBytes, bars[warp], r0, r1, src, [&](const Stage& sg, int row0, int nr) {
+      dyn_smem + warp * Stage::kStages * Stage::kBytes, bars[warp], group_map(a.n, RPW, vb, vg), src, [&](const Stage& sg, int row0, int nr) {
         if (rs >= nr) return;
         const unsigned row = row0 + rs;
         int cols[W];
@@ -752,7 +771,7 @@ __device__ __forceinline__ void body_cg_a(const KArgs<T>& a, const int vb, const
   const int c = threadIdx.x;
   if (c < a.ms) {
     const double pq = tot[0][c];
-    ctl->alpha[(it + 1) & 1][c] = (ctl->active[c] && pq > 0.0) ? ctl->rz[c] / pq : 0.0;
+    ctl->alpha[(it + 1) & 1][c] = (pre_act[c] && pq > 0.0) ? pre_rz[c] / pq : 0.0;
   }
 }
 
@@ -910,7 +929,7 @@ __device__ __forceinline__ bool grid_reduce_scalar(typename AccOf<T>::type acc, 
     for (int w = 0; w < NW; ++w) add_part(s, red[w]);
     part[vb] = to_part(s);
   }
-  return reduce_blocks<Acc>(part, ctl->gcounters[slot], &ctl->counters[slot], 1, vb, vg,
+  return reduce_blocks<Acc>(part, &ctl->counters[slot], 1, vb, vg,
                             [&](int, double v) { *tot = v; });
 }
 
@@ -1038,6 +1057,14 @@ __device__ __forceinline__ void body_cg_b(const KArgs<T>& a, const int vb, const
   if (!ctl->cont && !a.force) return;  // this instance's CG loop has ended (timing runs: force)
   SEG_ROW_SETUP
   const int it = ctl->it;
+  // read now what the last block needs after the grid sum
+  __shared__ double pre_rz[kMaxCols], pre_tol2[kMaxCols];
+  __shared__ int pre_act[kMaxCols];
+  if ((int)threadIdx.x < a.ms) {
+    pre_rz[threadIdx.x] = ctl->rz[threadIdx.x];
+    pre_tol2[threadIdx.x] = ctl->tol2[threadIdx.x];
+    pre_act[threadIdx.x] = ctl->active[threadIdx.x];
+  }
   const unsigned ms = a.ms;
   T al[VW];
 #pragma unroll
@@ -1089,10 +1116,10 @@ __device__ __forceinline__ void body_cg_b(const KArgs<T>& a, const int vb, const
   const int c = threadIdx.x;
   if (c < a.ms) {
     const double rzn = tot[0][c], rrn = tot[1][c];
-    act = ctl->active[c];
+    act = pre_act[c];
     if (c < a.m && !(isfinite(rzn) && isfinite(rrn))) bad = 1;
-    if (act && rrn <= ctl->tol2[c]) act = 0;
-    const double rzo = ctl->rz[c];
+    if (act && rrn <= pre_tol2[c]) act = 0;
+    const double rzo = pre_rz[c];
     ctl->beta[c] = rzo > 0.0 ? rzn / rzo : 0.0;
     ctl->rz[c] = rzn;
     ctl->active[c] = act;

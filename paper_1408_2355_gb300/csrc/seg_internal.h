@@ -18,8 +18,9 @@ constexpr int kMaxDots = 5;         // inner products fused into one pass
 // and launched with; the triangle passes use kTriBlocksPerSM.
 constexpr int kRowBlocksPerSM = 3;
 constexpr int kTriBlocksPerSM = 4;
-constexpr int kMaxGrid = 2048;  // blocks of one kernel of a state (two-level grid reduction)
+constexpr int kMaxGrid = 2048;  // blocks of one kernel of a state
 constexpr int kTuneWaves = 4;   // the autotuner tries up to this many waves of blocks
+constexpr int kCgUnroll = 2;    // CG iterations per evaluation of the step graph's loop condition
 constexpr int kNumCounters = 8;    // last-block tickets, one per kernel kind
 
 enum CounterSlot { kCtrStart = 0, kCtrCgA = 1, kCtrCgB = 2, kCtrEnergy = 3 };
@@ -55,7 +56,6 @@ struct DevCtl {
   int pad0;
   long long step_mark;        // ctl->step when the last batch of steps was enqueued
   unsigned int counters[kNumCounters];
-  unsigned int gcounters[kNumCounters][kMaxGrid / 32];  // per group of 32 blocks
 };
 
 // Arguments of every hot-path kernel (passed by value; identical struct for
