@@ -34,7 +34,7 @@ HBM_FALLBACK_GBS = 6800.0
 # DRAM bytes (read + write) per k_cg_a launch from the ncu capture summarised
 # in profiles/k_cg_a_sphere_L8_m16_mixed.md (level-8 sphere, m = 16, mixed);
 # valid for that workload and that version of the kernel only.
-TRAFFIC_CG_A = 271.1e6
+TRAFFIC_CG_A = 249.5e6
 METRIC = "DoF-steps/s (N*m*steps) sphere 655k m=16 FP32-mix vs FP64; p50/p99 latency"
 
 
@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch geometry")
+    ap.add_argument("--grid-blocks", type=int, default=0, help="row-kernel blocks (0: default / autotuned)")
     ap.add_argument("--serve-requests", type=int, default=256, help="0 disables the serving run")
     ap.add_argument("--serve-compare", type=int, default=24)
     ap.add_argument("--serve-rate", type=float, default=20.0)
@@ -261,6 +262,7 @@ def run_ours(a, rank, ws, local):
         prm.check_every = 1      # energy + stop-rule pass in every step
         prm.energy_tol = -1.0    # ... but never stop: time exactly K steps
         prm.launch_mode = 1 if a.launch_mode == "direct" else 0
+        prm.grid_blocks = a.grid_blocks
         st = seg.seg_state_create(prob, a.m, a.eps, seg.SEG_INIT_UNIFORM, a.seed, prm, stream.cuda_stream)
         if not a.no_autotune:  # launch geometry by measurement, after 3 steps (setup, not timed)
             seg.seg_step(st, 3)
@@ -293,7 +295,7 @@ def run_ours(a, rank, ws, local):
     clk = clocks.stop()
     ms = max_over_ranks(ms, ws)
     dcg = s1["cg_iterations"] - s0["cg_iterations"]
-    launches = 3 * a.steps + 2 * dcg
+    launches = s1["kernel_launches"] - s0["kernel_launches"]  # counted on the device
     value = ws * n * a.m * a.steps / (ms / 1e3)
     e_final = seg.seg_energy(st)
 

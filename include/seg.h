@@ -94,6 +94,9 @@ typedef struct {
   int32_t status_bits;      /* bit0: a solve hit cg_maxit; bit1: non-finite norm/energy; bit2: timeout */
   double last_check_total;  /* total energy at the latest stop-rule check */
   int64_t checks;           /* number of stop-rule checks evaluated */
+  int64_t kernel_launches;  /* hot-path kernel launches on this state (start, CG passes A and B
+                               including those that returned at once after the loop ended,
+                               finish, energy passes) */
 } seg_stats;
 
 /* ------------------------------------------------------------------ meshes */

@@ -84,6 +84,7 @@ class seg_stats(C.Structure):
         ("status_bits", C.c_int32),
         ("last_check_total", C.c_double),
         ("checks", C.c_int64),
+        ("kernel_launches", C.c_int64),
     ]
 
 

@@ -1250,6 +1250,7 @@ seg_status seg_get_stats(seg_state* s, seg_stats* out) {
   out->status_bits = c.status;
   out->last_check_total = c.e_prev;
   out->checks = c.checks;
+  out->kernel_launches = (int64_t)c.launches;
   return SEG_OK;
 }
 

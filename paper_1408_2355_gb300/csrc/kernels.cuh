@@ -463,6 +463,11 @@ __device__ __forceinline__ void lds_row(double (&d)[W], const double* p) {
   }
 }
 
+// Every hot-path launch is counted once per state (block 0 of the state).
+__device__ __forceinline__ void count_launch(DevCtl* ctl, int vb) {
+  if (vb == 0 && threadIdx.x == 0) atomicAdd(&ctl->launches, 1ull);
+}
+
 // Mark a timed-out wait: the block records the error and halts the run.
 __device__ __forceinline__ void report_timeout(DevCtl* ctl) {
   atomicOr(&ctl->status, 4);
@@ -583,6 +588,7 @@ __device__ __forceinline__ void body_start(const KArgs<T>& a, const int vb, cons
   typedef typename AccOf<T>::type Acc;
   typedef StartStage<T, LPR, W> Stage;
   DevCtl* ctl = a.ctl;
+  count_launch(ctl, vb);
   if (state_finished(a, ctl)) return;
   SEG_ROW_SETUP
   extern __shared__ __align__(128) unsigned char dyn_smem[];
@@ -694,6 +700,7 @@ __device__ __forceinline__ void body_cg_a(const KArgs<T>& a, const int vb, const
   typedef typename AccOf<T>::type Acc;
   typedef CgAStage<T, LPR, W> Stage;
   DevCtl* ctl = a.ctl;
+  count_launch(ctl, vb);
   if (state_finished(a, ctl)) return;
   if (!ctl->cont && !a.force) return;  // this instance's CG loop has ended (timing runs: force)
   SEG_ROW_SETUP
@@ -807,6 +814,7 @@ __device__ __forceinline__ void body_energy(const KArgs<T>& a, const int vb, con
   constexpr int RPW = 32 / LPR;
   constexpr int TU = 2;
   DevCtl* ctl = a.ctl;
+  count_launch(ctl, vb);
   if (state_finished(a, ctl)) return;
   if (!a.force) {
     if (a.check_every <= 0) return;
@@ -953,6 +961,7 @@ __device__ __forceinline__ void body_energy_check(const KArgs<T>& a, const int v
   constexpr int VW = VecW<T>::W;
   constexpr int MS = LPR * VW;
   DevCtl* ctl = a.ctl;
+  count_launch(ctl, vb);
   if (state_finished(a, ctl)) return;
   if (!a.force) {
     if (a.check_every <= 0) return;
@@ -1049,6 +1058,7 @@ __device__ __forceinline__ void body_cg_b(const KArgs<T>& a, const int vb, const
   typedef typename AccOf<T>::type Acc;
   constexpr int RU = kStreamRows;
   DevCtl* ctl = a.ctl;
+  count_launch(ctl, vb);
   if (state_finished(a, ctl)) {
     // a kernel of this iteration halted the run: end the CG loop
     if (a.set_cond && vb == 0 && threadIdx.x == 0) cudaGraphSetConditional(a.cond, 0);
@@ -1148,6 +1158,7 @@ template <typename T, int LPR>
 __device__ __forceinline__ void body_finish(const KArgs<T>& a, const int vb, const int vg) {
   constexpr int RU = kStreamRows;
   DevCtl* ctl = a.ctl;
+  count_launch(ctl, vb);
   if (state_finished(a, ctl)) return;
   SEG_ROW_SETUP
   const int lbase = lane - cg;

@@ -55,6 +55,7 @@ struct DevCtl {
   int have_prev;
   int pad0;
   long long step_mark;        // ctl->step when the last batch of steps was enqueued
+  unsigned long long launches;  // hot-path kernel launches (block 0 counts each)
   unsigned int counters[kNumCounters];
 };
 

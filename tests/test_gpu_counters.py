@@ -1,0 +1,31 @@
+"""The launch counter of seg_stats matches the step structure: per step the
+start, energy-check and finish passes, and the CG passes in pairs (the step
+graph runs two CG iterations per evaluation of its loop condition; direct
+launches run exactly one pair per iteration)."""
+
+import pytest
+
+import workload as w
+from tests.gpu_helpers import lib, make_state
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def seg():
+    return lib()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_kernel_launch_counter(seg, mode):
+    xyz, tri = w.icosphere(4)
+    st = make_state(seg, xyz, tri, 1e-4, 3, 1e-2, 1, 3, launch_mode=mode, check_every=1, energy_tol=-1.0)
+    seg.seg_step(st, 1)  # the first step also runs the pending normalisation
+    for _ in range(4):
+        s0 = seg.seg_get_stats(st)
+        seg.seg_step(st, 1)
+        s1 = seg.seg_get_stats(st)
+        k = s1["cg_last"]
+        assert k == s1["cg_iterations"] - s0["cg_iterations"] and k >= 1
+        pairs = k if mode == 1 else 2 * ((k + 1) // 2)
+        assert s1["kernel_launches"] - s0["kernel_launches"] == 3 + 2 * pairs
