@@ -1203,11 +1203,21 @@ __device__ __forceinline__ void body_finish(const KArgs<T>& a, const int vb, con
       if ((int)row < r1) st(a.X + (row * ms + c0), x[u]);
     }
   }
-  if (a.count_step && vb == 0 && threadIdx.x == 0) {
-    ctl->step += 1;
-    ctl->cg_last = it;
-    ctl->cg_total += it;
-    if (it > ctl->cg_max) ctl->cg_max = it;
+  if (a.count_step) {
+    // the step is counted by the last block to finish, after every block has
+    // passed its own state_finished() test (a block that started after an
+    // early increment would otherwise see the step limit and skip its rows)
+    __shared__ unsigned int fin_ticket;
+    __syncthreads();
+    if (threadIdx.x == 0) fin_ticket = atomicAdd(&ctl->counters[kCtrFinish], 1u);
+    __syncthreads();
+    if (threadIdx.x == 0 && fin_ticket == (unsigned int)(vg - 1)) {
+      ctl->counters[kCtrFinish] = 0u;
+      ctl->step += 1;
+      ctl->cg_last = it;
+      ctl->cg_total += it;
+      if (it > ctl->cg_max) ctl->cg_max = it;
+    }
   }
 }
 

@@ -29,3 +29,18 @@ def test_kernel_launch_counter(seg, mode):
         assert k == s1["cg_iterations"] - s0["cg_iterations"] and k >= 1
         pairs = k if mode == 1 else 2 * ((k + 1) // 2)
         assert s1["kernel_launches"] - s0["kernel_launches"] == 3 + 2 * pairs
+
+
+def test_step_limit_with_more_blocks_than_resident(seg):
+    """The last step under a step limit updates every row even when the grid
+    runs in several waves (later blocks start after earlier ones finished)."""
+    import numpy as np
+
+    xyz, tri = w.icosphere(6)
+    a = make_state(seg, xyz, tri, 1e-4, 8, 2e-2, 0, 5, check_every=-1, max_steps=3, grid_blocks=2048)
+    b = make_state(seg, xyz, tri, 1e-4, 8, 2e-2, 0, 5, check_every=-1)
+    assert seg.seg_step(a, 10) == 3
+    assert seg.seg_get_stats(a)["steps"] == 3
+    assert seg.seg_step(b, 3) == 3
+    ua, ub = seg.seg_get_u(a), seg.seg_get_u(b)
+    assert np.abs(ua - ub).max() <= 1e-12 * np.abs(ub).max()
