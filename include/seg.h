@@ -363,7 +363,9 @@ const char* seg_last_error(void);
  * afterwards: call seg_set_u before using it. */
 seg_status seg_time_kernel(seg_state* s, int32_t which, int32_t reps, double* ms_per_launch);
 
-/* Launch geometry of the row kernels of a state (nullable outputs). */
+/* Launch geometry of the row kernels of a state (nullable outputs);
+ * grid_blocks is the grid of CG pass A (the autotuner may give each pass its
+ * own). */
 seg_status seg_launch_info(seg_state* s, int32_t* grid_blocks, int32_t* block_threads,
                            int32_t* lanes_per_row, int32_t* padded_m);
 
@@ -380,16 +382,20 @@ typedef struct {
   double ms_model;             /* modelled step time of the chosen row grid */
   double ms_energy;            /* one energy check with the chosen grid, ms */
   double cg_weight;            /* CG iterations per step used in the model */
+  int32_t grid_pass[4];        /* chosen blocks of the start pass, CG pass A, CG pass B, finish */
 } seg_tune_result;
 
 /* Pick the launch geometry of a state by measurement (no counterpart in the
  * paper; the arithmetic of Algorithm 2.2 is unchanged).  The row grid (and
  * with it the block of rows each CUDA block owns) is chosen among 1 ..
  * 3 blocks per SM and 2 or 4 waves of 3 blocks per SM (at most one block per
- * 256 rows, at most 2048 blocks), by the modelled step time
- *     t_start + k (t_cgA + t_cgB) + t_finish,
- * each t the mean of `reps` (<= 0: 10) timed launches and k the state's CG
- * iterations per step so far (8 before its first step); the energy-check grid
+ * 256 rows, at most 2048 blocks), separately for each of the four row
+ * passes (start, CG pass A, CG pass B, finish): each pass keeps the candidate
+ * with its shortest time, the mean of `reps` (<= 0: 10) timed launches.
+ * cand_ms[c] is the modelled step time t_start + k (t_cgA + t_cgB) + t_finish
+ * with all passes on candidate c, ms_model the same with each pass on its
+ * chosen grid, k the state's CG iterations per step so far (8 before its
+ * first step); grid_blocks is CG pass A's grid.  The energy-check grid
  * among 1 .. 4 blocks per SM and 2 or 4 waves of 4 blocks per SM by its own
  * time.  The state's data and
  * counters are saved before and restored bitwise after the timing launches,

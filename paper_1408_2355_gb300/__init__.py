@@ -110,6 +110,7 @@ class seg_tune_result(C.Structure):
         ("ms_model", C.c_double),
         ("ms_energy", C.c_double),
         ("cg_weight", C.c_double),
+        ("grid_pass", C.c_int32 * 4),
     ]
 
 
@@ -561,7 +562,9 @@ def seg_autotune(state: State, reps: int = 10) -> dict:
     k = r.n_candidates
     return {"grid_blocks": r.grid_blocks, "grid_blocks_energy": r.grid_blocks_energy,
             "candidates": [(r.cand_grid[i], r.cand_ms[i]) for i in range(k)], "ms_model": r.ms_model,
-            "ms_energy": r.ms_energy, "cg_weight": r.cg_weight}
+            "ms_energy": r.ms_energy, "cg_weight": r.cg_weight,
+            "grid_pass": {"start": r.grid_pass[0], "cg_a": r.grid_pass[1], "cg_b": r.grid_pass[2],
+                          "finish": r.grid_pass[3]}}
 
 
 def seg_s_eps_noalloc(u, xyz, tri, eps: float, out, cuda_stream: int | None = None):

@@ -75,7 +75,7 @@ struct seg_state {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int launch_mode = 0;
-  int grid = 0;     // blocks of the row kernels
+  int grid[4] = {0, 0, 0, 0};  // blocks of the row kernels: start, CG pass A, CG pass B, finish
   int grid_e = 0;   // blocks of the S_eps check kernel
   int grid_cap = 0;    // the partial-sum buffer holds this many row blocks
   int grid_e_cap = 0;  // ... and this many triangle blocks
@@ -153,7 +153,13 @@ unsigned smem_of(const seg_state* s, void* fn) {
   return 0;
 }
 
-int grid_of(const seg_state* s, void* fn) { return fn == s->ks.energy_check ? s->grid_e : s->grid; }
+int grid_of(const seg_state* s, void* fn) {
+  if (fn == s->ks.energy_check || fn == s->ks.energy) return s->grid_e;
+  if (fn == s->ks.start) return s->grid[kPassStart];
+  if (fn == s->ks.cg_a) return s->grid[kPassCgA];
+  if (fn == s->ks.cg_b) return s->grid[kPassCgB];
+  return s->grid[kPassFinish];
+}
 
 // Launch one row kernel with the state's arguments.
 seg_status launch_row(seg_state* s, void* fn, const Launch& l) {
@@ -295,7 +301,8 @@ seg_status build_graph_t(seg_state* s) {
   l.ignore_halt = 0;
   KArgs<T> base = make_args<T>(s, l);
   cudaGraphNode_t n_start, n_energy, n_loop, n_a, n_b, n_fin;
-  SEG_CUDA(add_kernel_node<T>(&n_start, s->graph, nullptr, 0, s->ks.start, s->grid, base, s->ks.smem_start));
+  SEG_CUDA(add_kernel_node<T>(&n_start, s->graph, nullptr, 0, s->ks.start, s->grid[kPassStart], base,
+                              s->ks.smem_start));
   SEG_CUDA(add_kernel_node<T>(&n_energy, s->graph, &n_start, 1, s->ks.energy_check, s->grid_e, base, 0));
   cudaGraphNodeParams cp{};
   cp.type = cudaGraphNodeTypeConditional;
@@ -308,16 +315,16 @@ seg_status build_graph_t(seg_state* s) {
   // an iteration after the loop has ended return at once (ctl->cont == 0)
   cudaGraphNode_t prev = nullptr;
   for (int u = 0; u < kCgUnroll; ++u) {
-    SEG_CUDA(add_kernel_node<T>(&n_a, body, prev ? &prev : nullptr, prev ? 1 : 0, s->ks.cg_a, s->grid, base,
-                                s->ks.smem_cg_a));
-    SEG_CUDA(add_kernel_node<T>(&n_b, body, &n_a, 1, s->ks.cg_b, s->grid, base, 0));
+    SEG_CUDA(add_kernel_node<T>(&n_a, body, prev ? &prev : nullptr, prev ? 1 : 0, s->ks.cg_a, s->grid[kPassCgA],
+                                base, s->ks.smem_cg_a));
+    SEG_CUDA(add_kernel_node<T>(&n_b, body, &n_a, 1, s->ks.cg_b, s->grid[kPassCgB], base, 0));
     prev = n_b;
   }
   KArgs<T> fin = base;
   fin.apply_x = 1;
   fin.apply_ode = 1;
   fin.count_step = 1;
-  SEG_CUDA(add_kernel_node<T>(&n_fin, s->graph, &n_loop, 1, s->ks.finish, s->grid, fin, 0));
+  SEG_CUDA(add_kernel_node<T>(&n_fin, s->graph, &n_loop, 1, s->ks.finish, s->grid[kPassFinish], fin, 0));
   SEG_CUDA(cudaGraphInstantiate(&s->exec, s->graph, 0));
   return SEG_OK;
 }
@@ -691,10 +698,12 @@ seg_status seg_state_create(const seg_problem* p, int32_t m, double eps, seg_ini
   // blocks of at least 256 rows (1024 triangles), at most kRowBlocksPerSM
   // (kTriBlocksPerSM) per SM; the geometry is part of the state, so results
   // do not depend on whether the state runs alone or in a batch
-  s->grid = prm.grid_blocks > 0 ? prm.grid_blocks
-                                : (int)std::min<int64_t>(kRowBlocksPerSM * nsm, std::max<int64_t>(1, (p->n + 255) / 256));
+  const int g0 = prm.grid_blocks > 0
+                     ? prm.grid_blocks
+                     : (int)std::min<int64_t>(kRowBlocksPerSM * nsm, std::max<int64_t>(1, (p->n + 255) / 256));
+  for (int k = 0; k < 4; ++k) s->grid[k] = g0;
   s->grid_e = (int)std::min<int64_t>(kTriBlocksPerSM * nsm, std::max<int64_t>(1, (p->f + 1023) / 1024));
-  s->grid_cap = std::max(s->grid, std::min(kMaxGrid, kTuneWaves * kRowBlocksPerSM * nsm));
+  s->grid_cap = std::max(g0, std::min(kMaxGrid, kTuneWaves * kRowBlocksPerSM * nsm));
   s->grid_e_cap = std::max(s->grid_e, std::min(kMaxGrid, kTuneWaves * kTriBlocksPerSM * nsm));
   if (cuda_stream) {
     s->stream = (cudaStream_t)cuda_stream;
@@ -960,7 +969,7 @@ template <typename T>
 seg_status build_batch_t(seg_batch* b) {
   const int n = (int)b->members.size();
   std::vector<KArgs<T>> tab(n);
-  BatchArgs<T> rows{}, tris{}, vote{};
+  BatchArgs<T> rows[4] = {}, tris{}, vote{};
   for (int i = 0; i < n; ++i) {
     seg_state* s = b->members[i];
     Launch l;
@@ -969,21 +978,22 @@ seg_status build_batch_t(seg_batch* b) {
     l.apply_ode = 1;
     l.count_step = 1;
     tab[i] = make_args<T>(s, l);
-    rows.off[i + 1] = rows.off[i] + s->grid;
+    for (int k = 0; k < 4; ++k) rows[k].off[i + 1] = rows[k].off[i] + s->grid[k];
     tris.off[i + 1] = tris.off[i] + s->grid_e;
   }
   SEG_CUDA(cudaMalloc(&b->tab, n * sizeof(KArgs<T>)));
   SEG_CUDA(cudaMemcpy(b->tab, tab.data(), n * sizeof(KArgs<T>), cudaMemcpyHostToDevice));
   SEG_CUDA(cudaGraphCreate(&b->graph, 0));
   SEG_CUDA(cudaGraphConditionalHandleCreate(&b->cond, b->graph, 0, cudaGraphCondAssignDefault));
-  for (BatchArgs<T>* x : {&rows, &tris, &vote}) {
+  for (BatchArgs<T>* x : {&rows[0], &rows[1], &rows[2], &rows[3], &tris, &vote}) {
     x->tab = (const KArgs<T>*)b->tab;
     x->ninst = n;
     x->cond = (unsigned long long)b->cond;
   }
   vote.off[n] = 1;  // one block
   cudaGraphNode_t n_start, n_energy, n_vote0, n_loop, n_a, n_b, n_vote, n_fin;
-  SEG_CUDA(add_batch_node<T>(&n_start, b->graph, nullptr, 0, b->ks.b_start, rows, kBlockThreads, b->ks.smem_start));
+  SEG_CUDA(add_batch_node<T>(&n_start, b->graph, nullptr, 0, b->ks.b_start, rows[kPassStart], kBlockThreads,
+                             b->ks.smem_start));
   SEG_CUDA(add_batch_node<T>(&n_energy, b->graph, &n_start, 1, b->ks.b_energy_check, tris, kBlockThreads, 0));
   SEG_CUDA(add_batch_node<T>(&n_vote0, b->graph, &n_energy, 1, b->ks.b_vote, vote, kMaxBatch, 0));
   cudaGraphNodeParams cp{};
@@ -995,13 +1005,13 @@ seg_status build_batch_t(seg_batch* b) {
   cudaGraph_t body = cp.conditional.phGraph_out[0];
   cudaGraphNode_t prev = nullptr;
   for (int u = 0; u < kCgUnroll; ++u) {
-    SEG_CUDA(add_batch_node<T>(&n_a, body, prev ? &prev : nullptr, prev ? 1 : 0, b->ks.b_cg_a, rows, kBlockThreads,
-                               b->ks.smem_cg_a));
-    SEG_CUDA(add_batch_node<T>(&n_b, body, &n_a, 1, b->ks.b_cg_b, rows, kBlockThreads, 0));
+    SEG_CUDA(add_batch_node<T>(&n_a, body, prev ? &prev : nullptr, prev ? 1 : 0, b->ks.b_cg_a, rows[kPassCgA],
+                               kBlockThreads, b->ks.smem_cg_a));
+    SEG_CUDA(add_batch_node<T>(&n_b, body, &n_a, 1, b->ks.b_cg_b, rows[kPassCgB], kBlockThreads, 0));
     prev = n_b;
   }
   SEG_CUDA(add_batch_node<T>(&n_vote, body, &n_b, 1, b->ks.b_vote, vote, kMaxBatch, 0));
-  SEG_CUDA(add_batch_node<T>(&n_fin, b->graph, &n_loop, 1, b->ks.b_finish, rows, kBlockThreads, 0));
+  SEG_CUDA(add_batch_node<T>(&n_fin, b->graph, &n_loop, 1, b->ks.b_finish, rows[kPassFinish], kBlockThreads, 0));
   SEG_CUDA(cudaGraphInstantiate(&b->exec, b->graph, 0));
   return SEG_OK;
 }
@@ -1289,14 +1299,16 @@ seg_status seg_autotune(seg_state* s, int32_t reps, seg_tune_result* out) {
     return fail(SEG_ERR_NO_MEMORY, std::string("cudaMalloc: ") + cudaGetErrorString(ce));
   }
   const bool pending = s->pending;
-  const int grid0 = s->grid, grid_e0 = s->grid_e;
+  int grid0[4];
+  for (int w = 0; w < 4; ++w) grid0[w] = s->grid[w];
+  const int grid_e0 = s->grid_e;
   ce = cudaMemcpyAsync(saved_x, s->X, vbytes, cudaMemcpyDeviceToDevice, s->stream);
   if (ce == cudaSuccess) ce = cudaMemcpyAsync(saved_ctl, s->ctl, sizeof(DevCtl), cudaMemcpyDeviceToDevice, s->stream);
   if (ce != cudaSuccess) st = fail(SEG_ERR_CUDA, std::string("save: ") + cudaGetErrorString(ce));
   // candidate row grids: 1 .. kRowBlocksPerSM blocks per SM (one wave), and
   // 2 .. kTuneWaves waves of them (the hardware hands out the later blocks as
-  // earlier ones finish, which evens out blocks that run slower), at most one
-  // block per 256 rows; triangle grids likewise with kTriBlocksPerSM
+  // earlier ones finish), at most one block per 256 rows; triangle grids
+  // likewise with kTriBlocksPerSM.  Each pass gets its own grid.
   std::vector<int> rows_c, tris_c;
   const int64_t n_cap = std::max<int64_t>(1, (s->p->n + 255) / 256);
   const int64_t f_cap = std::max<int64_t>(1, (s->p->f + 1023) / 1024);
@@ -1306,18 +1318,24 @@ seg_status seg_autotune(seg_state* s, int32_t reps, seg_tune_result* out) {
     rows_c.push_back((int)std::min<int64_t>((int64_t)w * kRowBlocksPerSM * nsm, n_cap));
     tris_c.push_back((int)std::min<int64_t>((int64_t)w * kTriBlocksPerSM * nsm, f_cap));
   }
-  rows_c.push_back(grid0);
+  for (int w = 0; w < 4; ++w) rows_c.push_back(grid0[w]);
   tris_c.push_back(grid_e0);
   for (auto* v : {&rows_c, &tris_c}) {
     std::sort(v->begin(), v->end());
     v->erase(std::unique(v->begin(), v->end()), v->end());
   }
-  int best = grid0, best_e = grid_e0;
-  double best_ms = 1e300, best_e_ms = 1e300;
+  int best[4];
+  double best_t[4];
+  for (int w = 0; w < 4; ++w) {
+    best[w] = grid0[w];
+    best_t[w] = 1e300;
+  }
+  int best_e = grid_e0;
+  double best_e_ms = 1e300;
   for (size_t c = 0; c < rows_c.size() && st == SEG_OK; ++c) {
     const int g = rows_c[c];
     if (g > s->grid_cap) continue;
-    s->grid = g;
+    for (int w = 0; w < 4; ++w) s->grid[w] = g;
     double t[4] = {0, 0, 0, 0};
     for (int w = 0; w < 4 && st == SEG_OK; ++w) st = time_launches(s, w, reps, &t[w]);
     if (st != SEG_OK) break;
@@ -1327,11 +1345,13 @@ seg_status seg_autotune(seg_state* s, int32_t reps, seg_tune_result* out) {
       out->cand_ms[out->n_candidates] = model;
       out->n_candidates += 1;
     }
-    if (model < best_ms) {
-      best_ms = model;
-      best = g;
-    }
+    for (int w = 0; w < 4; ++w)
+      if (t[w] < best_t[w]) {
+        best_t[w] = t[w];
+        best[w] = g;
+      }
   }
+  const double best_ms = best_t[0] + k * (best_t[1] + best_t[2]) + best_t[3];
   for (size_t c = 0; c < tris_c.size() && st == SEG_OK; ++c) {
     const int g = tris_c[c];
     if (g > s->grid_e_cap) continue;
@@ -1353,9 +1373,12 @@ seg_status seg_autotune(seg_state* s, int32_t reps, seg_tune_result* out) {
   cudaFree(saved_ctl);
   if (st == SEG_OK && ce != cudaSuccess) st = fail(SEG_ERR_CUDA, std::string("restore: ") + cudaGetErrorString(ce));
   s->pending = pending;
-  s->grid = st == SEG_OK ? best : grid0;
+  for (int w = 0; w < 4; ++w) {
+    s->grid[w] = st == SEG_OK ? best[w] : grid0[w];
+    out->grid_pass[w] = s->grid[w];
+  }
   s->grid_e = st == SEG_OK ? best_e : grid_e0;
-  out->grid_blocks = s->grid;
+  out->grid_blocks = s->grid[kPassCgA];
   out->grid_blocks_energy = s->grid_e;
   out->ms_model = st == SEG_OK ? best_ms : 0.0;
   out->ms_energy = st == SEG_OK ? best_e_ms : 0.0;
@@ -1372,7 +1395,7 @@ seg_status seg_autotune(seg_state* s, int32_t reps, seg_tune_result* out) {
 seg_status seg_launch_info(seg_state* s, int32_t* grid_blocks, int32_t* block_threads, int32_t* lanes_per_row,
                            int32_t* padded_m) {
   if (!s) return fail(SEG_ERR_ARG, "state is NULL");
-  if (grid_blocks) *grid_blocks = s->grid;
+  if (grid_blocks) *grid_blocks = s->grid[kPassCgA];
   if (block_threads) *block_threads = kBlockThreads;
   if (lanes_per_row) *lanes_per_row = s->lpr;
   if (padded_m) *padded_m = s->ms;

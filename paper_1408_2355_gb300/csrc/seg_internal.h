@@ -23,6 +23,7 @@ constexpr int kTuneWaves = 4;   // the autotuner tries up to this many waves of 
 constexpr int kCgUnroll = 2;    // CG iterations per evaluation of the step graph's loop condition
 constexpr int kNumCounters = 8;    // last-block tickets, one per kernel kind
 
+enum RowPass { kPassStart = 0, kPassCgA = 1, kPassCgB = 2, kPassFinish = 3 };
 enum CounterSlot { kCtrStart = 0, kCtrCgA = 1, kCtrCgB = 2, kCtrEnergy = 3, kCtrFinish = 4 };
 
 // Device-resident control block: per-component scalars of the solve and the
