@@ -34,7 +34,7 @@ HBM_FALLBACK_GBS = 6800.0
 # DRAM bytes (read + write) per k_cg_a launch from the ncu capture summarised
 # in profiles/k_cg_a_sphere_L8_m16_mixed.md (level-8 sphere, m = 16, mixed);
 # valid for that workload and that version of the kernel only.
-TRAFFIC_CG_A = 249.5e6
+TRAFFIC_CG_A = None  # re-measure after a change of k_cg_a
 METRIC = "DoF-steps/s (N*m*steps) sphere 655k m=16 FP32-mix vs FP64; p50/p99 latency"
 
 
@@ -222,9 +222,9 @@ def kernel_bytes(n, ntri, m_pad, s, W=8):
     V = N * m_pad * s is one state-sized vector.  Gathered neighbour rows
     count once (each unique row is needed once); the padded-ELL matrix rows
     are W int32 columns plus W values per vertex, the Jacobi diagonal N * s.
-      k_start  read X, write R, columns + K + M values, diagonal
-      k_cg_a   read R, p_old, X; write X, p_new, q; columns + A values, diagonal
-      k_cg_b   read R, q; write R; diagonal
+      k_start  read X, write Z, columns + K + M values, Jacobi inverse diagonal
+      k_cg_a   read Z, p_old, X, q_old; write X, p_new, q; columns + A values
+      k_cg_b   read Z, q; write Z; diagonal of A and its inverse
       k_finish read X, p; write X
       k_energy_check / k_energy  read X, triangle corners (3 int32) and areas
     """
@@ -232,8 +232,8 @@ def kernel_bytes(n, ntri, m_pad, s, W=8):
     ell = n * W * 4
     return {
         "k_start": 2 * V + ell + 2 * n * W * s + n * s,
-        "k_cg_a": 6 * V + ell + n * W * s + n * s,
-        "k_cg_b": 3 * V + n * s,
+        "k_cg_a": 7 * V + ell + n * W * s,
+        "k_cg_b": 3 * V + 2 * n * s,
         "k_finish": 3 * V,
         "k_energy_check": V + ntri * (12 + s),
         "k_energy": V + ntri * (12 + s),
@@ -347,7 +347,7 @@ def run_ours(a, rank, ws, local):
         "clocks": clk,
         "roofline": {
             "bound": "hbm",
-            "kernel": "k_cg_a (CG pass A: p = D^-1 r + beta p, q = A p, p.q, lagged x update)",
+            "kernel": "k_cg_a (CG pass A: p = z + beta p, q = A z + beta q, p.q, lagged x update)",
             "achieved": achieved,
             "peak": peak,
             "peak_kind": peak_kind,

@@ -829,6 +829,11 @@ seg_status seg_set_u(seg_state* s, const double* u, int32_t is_device) {
   }
   seg_status st = reset_ctl(s);
   if (st != SEG_OK) return st;
+  // the first CG iteration multiplies the old search direction and its image
+  // by beta = 0: clear them so that values left by a failed run cannot turn
+  // into NaN
+  const size_t vbytes = (size_t)s->p->n * s->ms * vsize(s->prec);
+  for (void* b : {s->P0, s->P1, s->Q}) SEG_CUDA(cudaMemsetAsync(b, 0, vbytes, s->stream));
   const int* perm = s->p->perm;
   st = launch_aux(s, s->ks.scatter_in, (long long)s->p->n * s->ms, src, perm);
   if (st != SEG_OK) return st;

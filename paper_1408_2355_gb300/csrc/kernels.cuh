@@ -576,7 +576,7 @@ __device__ __forceinline__ bool row_pipeline(unsigned char* smem_warp, unsigned 
 template <typename T, int LPR, int W>
 using StartStage = RowStage<T, LPR, W, 2, 1>;
 template <typename T, int LPR, int W>
-using CgAStage = RowStage<T, LPR, W, 1, 3>;
+using CgAStage = RowStage<T, LPR, W, 1, 4>;
 
 // Start pass (warm start x0 = X of the CG solve of step 1, and the fused
 // renormalisation of the previous step):
@@ -691,9 +691,11 @@ __device__ __forceinline__ void body_start(const KArgs<T>& a, const int vb, cons
 }
 
 // CG pass A of iteration j (it = j - 1 iterations done):
-//   p_j = z_{j-1} + beta p_{j-1}   (own row, and on the fly for every neighbour)
-//   q_j = A p_j,  p_j . q_j  (float-float);
-//   lagged  x += alpha_{j-1} p_{j-1}  (own row).
+//   p_j = z_{j-1} + beta p_{j-1}                    (own row)
+//   q_j = A p_j = A z_{j-1} + beta q_{j-1}           (q_{j-1} = A p_{j-1} from the
+//         previous pass A, own row; only z is gathered from the neighbours)
+//   p_j . q_j  (float-float);  lagged  x += alpha_{j-1} p_{j-1}  (own row).
+// In the first iteration of a step beta = 0 (any finite q_{j-1} will do).
 // Padded ELL entries point at the row itself with value 0 (no branches).
 template <typename T, int LPR, int W>
 __device__ __forceinline__ void body_cg_a(const KArgs<T>& a, const int vb, const int vg) {
@@ -733,6 +735,7 @@ __device__ __forceinline__ void body_cg_a(const KArgs<T>& a, const int vb, const
   src.vec[0] = a.Z;
   src.vec[1] = Pold;
   src.vec[2] = a.X;
+  src.vec[3] = a.Q;
   const bool ok = row_pipeline<Stage>(
       dyn_smem + warp * Stage::kStages * Stage::kBytes, bars[warp], group_map(a.n, RPW, vb, vg), src, [&](const Stage& sg, int row0, int nr) {
         if (rs >= nr) return;
@@ -741,18 +744,15 @@ __device__ __forceinline__ void body_cg_a(const KArgs<T>& a, const int vb, const
         T av[W];
         lds_row<W>(cols, sg.cols() + rs * W);
         lds_row<W>(av, sg.vals(0) + rs * W);
-        // all neighbour rows of z and p_old in flight at once
-        T zj[W][VW], pj[W][VW];
+        // all neighbour rows of z in flight at once
+        T zj[W][VW];
 #pragma unroll
-        for (int k = 0; k < W; ++k) {
-          const unsigned oj = (unsigned)cols[k] * ms + c0;
-          ld_ro(zj[k], a.Z + oj);
-          ld_ro(pj[k], Pold + oj);
-        }
-        T zi[VW], po[VW], x[VW];
+        for (int k = 0; k < W; ++k) ld_ro(zj[k], a.Z + ((unsigned)cols[k] * ms + c0));
+        T zi[VW], po[VW], x[VW], qo[VW];
         lds(zi, sg.vec(0) + rs * ms + c0);
         lds(po, sg.vec(1) + rs * ms + c0);
         lds(x, sg.vec(2) + rs * ms + c0);
+        lds(qo, sg.vec(3) + rs * ms + c0);
         T pn[VW], q[VW];
 #pragma unroll
         for (int v = 0; v < VW; ++v) {
@@ -765,8 +765,10 @@ __device__ __forceinline__ void body_cg_a(const KArgs<T>& a, const int vb, const
         for (int k = 0; k < W; ++k) {
           const T ak = av[k];
 #pragma unroll
-          for (int v = 0; v < VW; ++v) q[v] = fma(ak, fma(beta[v], pj[k][v], zj[k][v]), q[v]);
+          for (int v = 0; v < VW; ++v) q[v] = fma(ak, zj[k][v], q[v]);
         }
+#pragma unroll
+        for (int v = 0; v < VW; ++v) q[v] = fma(beta[v], qo[v], q[v]);
         st(Pnew + (row * ms + c0), pn);
         st(a.Q + (row * ms + c0), q);
 #pragma unroll
