@@ -264,8 +264,8 @@ def run_ours(a, rank, ws, local):
         prm.launch_mode = 1 if a.launch_mode == "direct" else 0
         prm.grid_blocks = a.grid_blocks
         st = seg.seg_state_create(prob, a.m, a.eps, seg.SEG_INIT_UNIFORM, a.seed, prm, stream.cuda_stream)
-        if not a.no_autotune:  # launch geometry by measurement, after 3 steps (setup, not timed)
-            seg.seg_step(st, 3)
+        if not a.no_autotune:  # launch geometry by measurement, after 20 steps (setup, not timed)
+            seg.seg_step(st, 20)
             tunes[prec] = seg.seg_autotune(st, 10)
         return prob, st
 

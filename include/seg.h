@@ -376,7 +376,7 @@ typedef struct {
   int32_t grid_blocks;         /* chosen blocks of the row kernels */
   int32_t grid_blocks_energy;  /* chosen blocks of the energy-check kernel */
   int32_t n_candidates;        /* row grids tried (first SEG_TUNE_MAX listed) */
-  int32_t reserved;
+  int32_t cg_peel;             /* CG iterations the step graph now runs before its loop node */
   int32_t cand_grid[SEG_TUNE_MAX];
   double cand_ms[SEG_TUNE_MAX]; /* modelled step time of each row grid, ms */
   double ms_model;             /* modelled step time of the chosen row grid */
@@ -399,7 +399,11 @@ typedef struct {
  * among 1 .. 4 blocks per SM and 2 or 4 waves of 4 blocks per SM by its own
  * time.  The state's data and
  * counters are saved before and restored bitwise after the timing launches,
- * and its step graph is rebuilt with the chosen geometry.  Later steps give
+ * and its step graph is rebuilt with the chosen geometry and with cg_peel =
+ * the CG iterations of the state's latest step (1 .. 16; unchanged before
+ * the first step) as plain graph nodes ahead of the
+ * conditional loop node (passes after convergence return at once; an
+ * evaluation of the loop condition costs more).  Later steps give
  * the same results as without tuning up to the summation order of the
  * per-block partial inner products.  A batch built from the state earlier
  * keeps the geometry it was built with.  Needs device memory for one copy of

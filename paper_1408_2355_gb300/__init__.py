@@ -104,7 +104,7 @@ class seg_tune_result(C.Structure):
         ("grid_blocks", C.c_int32),
         ("grid_blocks_energy", C.c_int32),
         ("n_candidates", C.c_int32),
-        ("reserved", C.c_int32),
+        ("cg_peel", C.c_int32),
         ("cand_grid", C.c_int32 * SEG_TUNE_MAX),
         ("cand_ms", C.c_double * SEG_TUNE_MAX),
         ("ms_model", C.c_double),
@@ -562,7 +562,7 @@ def seg_autotune(state: State, reps: int = 10) -> dict:
     k = r.n_candidates
     return {"grid_blocks": r.grid_blocks, "grid_blocks_energy": r.grid_blocks_energy,
             "candidates": [(r.cand_grid[i], r.cand_ms[i]) for i in range(k)], "ms_model": r.ms_model,
-            "ms_energy": r.ms_energy, "cg_weight": r.cg_weight,
+            "ms_energy": r.ms_energy, "cg_weight": r.cg_weight, "cg_peel": r.cg_peel,
             "grid_pass": {"start": r.grid_pass[0], "cg_a": r.grid_pass[1], "cg_b": r.grid_pass[2],
                           "finish": r.grid_pass[3]}}
 

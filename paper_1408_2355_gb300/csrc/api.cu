@@ -99,6 +99,7 @@ struct seg_state {
   cudaGraphExec_t exec = nullptr;
   cudaGraphConditionalHandle cond = 0;
   bool pending = true;      // inv_n must be recomputed before use
+  int cg_peel = kCgPeelDefault;  // CG iterations of the step graph before its WHILE node
 };
 
 namespace {
@@ -304,12 +305,21 @@ seg_status build_graph_t(seg_state* s) {
   SEG_CUDA(add_kernel_node<T>(&n_start, s->graph, nullptr, 0, s->ks.start, s->grid[kPassStart], base,
                               s->ks.smem_start));
   SEG_CUDA(add_kernel_node<T>(&n_energy, s->graph, &n_start, 1, s->ks.energy_check, s->grid_e, base, 0));
+  // the first cg_peel CG iterations are plain graph nodes (a pass after the
+  // loop has ended returns at once), the rest a WHILE node: an evaluation of
+  // the loop condition costs more than a pass that returns at once
+  cudaGraphNode_t last = n_energy;
+  for (int u = 0; u < s->cg_peel; ++u) {
+    SEG_CUDA(add_kernel_node<T>(&n_a, s->graph, &last, 1, s->ks.cg_a, s->grid[kPassCgA], base, s->ks.smem_cg_a));
+    SEG_CUDA(add_kernel_node<T>(&n_b, s->graph, &n_a, 1, s->ks.cg_b, s->grid[kPassCgB], base, 0));
+    last = n_b;
+  }
   cudaGraphNodeParams cp{};
   cp.type = cudaGraphNodeTypeConditional;
   cp.conditional.handle = s->cond;
   cp.conditional.type = cudaGraphCondTypeWhile;
   cp.conditional.size = 1;
-  SEG_CUDA(cudaGraphAddNode(&n_loop, s->graph, &n_energy, nullptr, 1, &cp));
+  SEG_CUDA(cudaGraphAddNode(&n_loop, s->graph, &last, nullptr, 1, &cp));
   cudaGraph_t body = cp.conditional.phGraph_out[0];
   // kCgUnroll CG iterations per evaluation of the loop condition; passes of
   // an iteration after the loop has ended return at once (ctl->cont == 0)
@@ -1388,6 +1398,10 @@ seg_status seg_autotune(seg_state* s, int32_t reps, seg_tune_result* out) {
   out->ms_model = st == SEG_OK ? best_ms : 0.0;
   out->ms_energy = st == SEG_OK ? best_e_ms : 0.0;
   out->cg_weight = k;
+  // CG iterations as plain graph nodes before the WHILE node: the iteration
+  // count of the latest step (early steps from random data need more)
+  if (st == SEG_OK && s->hctl->step > 0) s->cg_peel = std::min(kCgPeelMax, std::max(1, s->hctl->cg_last));
+  out->cg_peel = s->cg_peel;
   // the step graph has the geometry baked in
   if (s->exec) cudaGraphExecDestroy(s->exec);
   if (s->graph) cudaGraphDestroy(s->graph);

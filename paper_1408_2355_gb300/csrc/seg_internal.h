@@ -21,6 +21,8 @@ constexpr int kTriBlocksPerSM = 4;
 constexpr int kMaxGrid = 2048;  // blocks of one kernel of a state
 constexpr int kTuneWaves = 4;   // the autotuner tries up to this many waves of blocks
 constexpr int kCgUnroll = 2;    // CG iterations per evaluation of the step graph's loop condition
+constexpr int kCgPeelDefault = 4;  // CG iterations placed before the loop (the autotuner adjusts it)
+constexpr int kCgPeelMax = 16;
 constexpr int kNumCounters = 8;    // last-block tickets, one per kernel kind
 
 enum RowPass { kPassStart = 0, kPassCgA = 1, kPassCgB = 2, kPassFinish = 3 };

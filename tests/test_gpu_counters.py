@@ -1,7 +1,8 @@
 """The launch counter of seg_stats matches the step structure: per step the
 start, energy-check and finish passes, and the CG passes in pairs (the step
-graph runs two CG iterations per evaluation of its loop condition; direct
-launches run exactly one pair per iteration)."""
+graph runs its first CG iterations as plain nodes and then two per
+evaluation of its loop condition; direct launches run exactly one pair per
+iteration)."""
 
 import pytest
 
@@ -27,7 +28,9 @@ def test_kernel_launch_counter(seg, mode):
         s1 = seg.seg_get_stats(st)
         k = s1["cg_last"]
         assert k == s1["cg_iterations"] - s0["cg_iterations"] and k >= 1
-        pairs = k if mode == 1 else 2 * ((k + 1) // 2)
+        # graph: 4 iterations as plain nodes (the untuned default), then the
+        # loop node with two iterations per evaluation
+        pairs = k if mode == 1 else 4 + (0 if k <= 4 else 2 * ((k - 4 + 1) // 2))
         assert s1["kernel_launches"] - s0["kernel_launches"] == 3 + 2 * pairs
 
 
