@@ -1010,7 +1010,18 @@ seg_status build_batch_t(seg_batch* b) {
   SEG_CUDA(add_batch_node<T>(&n_start, b->graph, nullptr, 0, b->ks.b_start, rows[kPassStart], kBlockThreads,
                              b->ks.smem_start));
   SEG_CUDA(add_batch_node<T>(&n_energy, b->graph, &n_start, 1, b->ks.b_energy_check, tris, kBlockThreads, 0));
-  SEG_CUDA(add_batch_node<T>(&n_vote0, b->graph, &n_energy, 1, b->ks.b_vote, vote, kMaxBatch, 0));
+  // as in the single-state graph: the first CG iterations (the largest
+  // peel count of the members) as plain nodes, then the vote and the loop
+  int peel = 0;
+  for (seg_state* m : b->members) peel = std::max(peel, m->cg_peel);
+  cudaGraphNode_t last = n_energy;
+  for (int u = 0; u < peel; ++u) {
+    SEG_CUDA(add_batch_node<T>(&n_a, b->graph, &last, 1, b->ks.b_cg_a, rows[kPassCgA], kBlockThreads,
+                               b->ks.smem_cg_a));
+    SEG_CUDA(add_batch_node<T>(&n_b, b->graph, &n_a, 1, b->ks.b_cg_b, rows[kPassCgB], kBlockThreads, 0));
+    last = n_b;
+  }
+  SEG_CUDA(add_batch_node<T>(&n_vote0, b->graph, &last, 1, b->ks.b_vote, vote, kMaxBatch, 0));
   cudaGraphNodeParams cp{};
   cp.type = cudaGraphNodeTypeConditional;
   cp.conditional.handle = b->cond;
