@@ -393,10 +393,16 @@ seg_status upload_ints(const std::vector<I>& src, I** dst) {
   return SEG_OK;
 }
 
-void free_state(seg_state* s) {
-  if (!s) return;
+void drop_graph(seg_state* s) {
   if (s->exec) cudaGraphExecDestroy(s->exec);
   if (s->graph) cudaGraphDestroy(s->graph);
+  s->exec = nullptr;
+  s->graph = nullptr;
+}
+
+void free_state(seg_state* s) {
+  if (!s) return;
+  drop_graph(s);
   void* bufs[] = {s->X, s->Z, s->P0, s->P1, s->Q, s->ctl, s->part, s->io, s->ones, s->scale_backup, s->am, s->vp};
   for (void* b : bufs)
     if (b) cudaFree(b);
@@ -769,13 +775,13 @@ seg_status seg_state_create(const seg_problem* p, int32_t m, double eps, seg_ini
       return fail(SEG_ERR_CUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(ce));
     }
   }
-  seg_status st;
+  // the step graph is built at the first graph-mode step (states that only
+  // run inside batches never need one)
+  seg_status st = SEG_OK;
   if (s->prec == SEG_MIXED_FP32) {
     fill_args<float>(s);
-    st = build_graph_t<float>(s);
   } else {
     fill_args<double>(s);
-    st = build_graph_t<double>(s);
   }
   if (st == SEG_OK) {
     const int* perm = p->perm;
@@ -880,6 +886,13 @@ seg_status seg_step_async(seg_state* s, int64_t nsteps) {
                            s->stream));
   SEG_CUDA(cudaMemsetAsync(&s->ctl->status, 0, sizeof(int), s->stream));
   if (s->launch_mode == 0) {
+    if (!s->exec) {
+      const seg_status gs = s->prec == SEG_MIXED_FP32 ? build_graph_t<float>(s) : build_graph_t<double>(s);
+      if (gs != SEG_OK) {
+        drop_graph(s);
+        return gs;
+      }
+    }
     for (int64_t k = 0; k < nsteps; ++k) SEG_CUDA(cudaGraphLaunch(s->exec, s->stream));
   } else {
     for (int64_t k = 0; k < nsteps; ++k) {
@@ -1413,13 +1426,10 @@ seg_status seg_autotune(seg_state* s, int32_t reps, seg_tune_result* out) {
   // count of the latest step (early steps from random data need more)
   if (st == SEG_OK && s->hctl->step > 0) s->cg_peel = std::min(kCgPeelMax, std::max(1, s->hctl->cg_last));
   out->cg_peel = s->cg_peel;
-  // the step graph has the geometry baked in
-  if (s->exec) cudaGraphExecDestroy(s->exec);
-  if (s->graph) cudaGraphDestroy(s->graph);
-  s->exec = nullptr;
-  s->graph = nullptr;
-  const seg_status gs = s->prec == SEG_MIXED_FP32 ? build_graph_t<float>(s) : build_graph_t<double>(s);
-  return st != SEG_OK ? st : gs;
+  // the step graph has the geometry baked in: drop it, the next graph-mode
+  // step builds it again
+  drop_graph(s);
+  return st;
 }
 
 seg_status seg_launch_info(seg_state* s, int32_t* grid_blocks, int32_t* block_threads, int32_t* lanes_per_row,
