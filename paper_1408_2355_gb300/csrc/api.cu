@@ -242,7 +242,16 @@ seg_status direct_step(seg_state* s) {
 // (0 start, 1 CG A, 2 CG B, 3 finish, 4 energy check, 5 energy) on the
 // state's buffers, after one warm-up launch.
 seg_status time_launches(seg_state* s, int which, int reps, double* ms_per_launch) {
-  void* fns[] = {s->ks.start, s->ks.cg_a, s->ks.cg_b, s->ks.finish, s->ks.energy_check, s->ks.energy};
+  void* fns[] = {s->ks.start, s->ks.cg_a,         s->ks.cg_b, s->ks.finish,
+                 s->ks.energy_check, s->ks.energy, s->ks.cg_a, s->ks.finish};
+  if (which == 1 || which == 6 || which == 3 || which == 7) {
+    // CG pass A and the finish pass run as after an even (1, 3) or odd (6, 7)
+    // iteration count: odd pass A also applies the two pending solution
+    // updates, the finish pass after an odd count applies two instead of one
+    const int it = (which == 6 || which == 7) ? 1 : 0;
+    SEG_CUDA(cudaMemcpyAsync(&s->ctl->it, &it, sizeof(int), cudaMemcpyHostToDevice, s->stream));
+    SEG_CUDA(cudaStreamSynchronize(s->stream));
+  }
   Launch l;
   l.force = 1;
   l.apply_x = 1;
@@ -1307,7 +1316,7 @@ seg_status seg_get_stats(seg_state* s, seg_stats* out) {
 
 seg_status seg_time_kernel(seg_state* s, int32_t which, int32_t reps, double* ms_per_launch) {
   if (!s || !ms_per_launch) return fail(SEG_ERR_ARG, "state or output is NULL");
-  if (which < 0 || which > 5 || reps < 1) return fail(SEG_ERR_ARG, "which must be 0..5 and reps >= 1");
+  if (which < 0 || which > 7 || reps < 1) return fail(SEG_ERR_ARG, "which must be 0..7 and reps >= 1");
   SEG_CUDA(cudaSetDevice(s->p->device));
   seg_status st = time_launches(s, which, reps, ms_per_launch);
   s->pending = true;
@@ -1377,7 +1386,10 @@ seg_status seg_autotune(seg_state* s, int32_t reps, seg_tune_result* out) {
     for (int w = 0; w < 4; ++w) s->grid[w] = g;
     double t[4] = {0, 0, 0, 0};
     for (int w = 0; w < 4 && st == SEG_OK; ++w) st = time_launches(s, w, reps, &t[w]);
+    double t_odd = 0;  // CG pass A alternates between its even and odd form
+    if (st == SEG_OK) st = time_launches(s, 6, reps, &t_odd);
     if (st != SEG_OK) break;
+    t[1] = 0.5 * (t[1] + t_odd);
     const double model = t[0] + k * (t[1] + t[2]) + t[3];
     if (out->n_candidates < SEG_TUNE_MAX) {
       out->cand_grid[out->n_candidates] = g;

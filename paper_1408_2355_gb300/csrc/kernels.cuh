@@ -388,6 +388,7 @@ struct RowStage {
   static constexpr unsigned kColBytes = RPW * W * 4;
   static constexpr unsigned kValBytes = RPW * W * sizeof(T);
   static constexpr unsigned kVecBytes = RPW * MS * sizeof(T);  // = 512
+  static constexpr int kNvec = NVEC;
   static constexpr unsigned kBytes = kColBytes + NVAL * kValBytes + NVEC * kVecBytes;
   // stages of each warp's copy ring (up to kStages - 1 row groups in flight
   // while one is consumed): as many as fit 64 KiB per block, 2 .. kPipeStages
@@ -575,8 +576,8 @@ __device__ __forceinline__ bool row_pipeline(unsigned char* smem_warp, unsigned 
 
 template <typename T, int LPR, int W>
 using StartStage = RowStage<T, LPR, W, 2, 1>;
-template <typename T, int LPR, int W>
-using CgAStage = RowStage<T, LPR, W, 1, 4>;
+template <typename T, int LPR, int W, bool XUP>
+using CgAStage = RowStage<T, LPR, W, 1, XUP ? 5 : 3>;
 
 // Start pass (warm start x0 = X of the CG solve of step 1, and the fused
 // renormalisation of the previous step):
@@ -694,21 +695,23 @@ __device__ __forceinline__ void body_start(const KArgs<T>& a, const int vb, cons
 //   p_j = z_{j-1} + beta p_{j-1}                    (own row)
 //   q_j = A p_j = A z_{j-1} + beta q_{j-1}           (q_{j-1} = A p_{j-1} from the
 //         previous pass A, own row; only z is gathered from the neighbours)
-//   p_j . q_j  (float-float);  lagged  x += alpha_{j-1} p_{j-1}  (own row).
-// In the first iteration of a step beta = 0 (any finite q_{j-1} will do).
+//   p_j . q_j  (float-float).
+// The solution is updated every second iteration, two terms at a time (the
+// search directions of the last two iterations are both still in the
+// ping-pong buffers): for even j,  x += alpha_{j-2} p_{j-2} + alpha_{j-1} p_{j-1},
+// the same sequence of operations as one lagged update per iteration, with
+// one read and write of x saved per two iterations; the finish pass applies
+// what is left.  In the first iteration of a step beta = 0 and alpha = 0
+// (any finite old values will do).
 // Padded ELL entries point at the row itself with value 0 (no branches).
-template <typename T, int LPR, int W>
-__device__ __forceinline__ void body_cg_a(const KArgs<T>& a, const int vb, const int vg) {
+template <typename T, int LPR, int W, bool XUP>
+__device__ __forceinline__ void body_cg_a_rows(const KArgs<T>& a, const int vb, const int vg, const int it) {
   typedef typename AccOf<T>::type Acc;
-  typedef CgAStage<T, LPR, W> Stage;
+  typedef CgAStage<T, LPR, W, XUP> Stage;
   DevCtl* ctl = a.ctl;
-  count_launch(ctl, vb);
-  if (state_finished(a, ctl)) return;
-  if (!ctl->cont && !a.force) return;  // this instance's CG loop has ended (timing runs: force)
   SEG_ROW_SETUP
   extern __shared__ __align__(128) unsigned char dyn_smem[];
   __shared__ __align__(8) unsigned long long bars[NW][kPipeStages];
-  const int it = ctl->it;
   // read now what the last block needs after the grid sum (written only by
   // other kernels), so that it does not wait for them at the end
   __shared__ double pre_rz[kMaxCols];
@@ -720,11 +723,12 @@ __device__ __forceinline__ void body_cg_a(const KArgs<T>& a, const int vb, const
   const T* Pold = (it & 1) ? a.P1 : a.P0;
   T* Pnew = (it & 1) ? a.P0 : a.P1;
   const unsigned ms = a.ms;
-  T beta[VW], alx[VW];
+  T beta[VW], al1[VW], al2[VW];
 #pragma unroll
   for (int v = 0; v < VW; ++v) {
     beta[v] = (T)ctl->beta[c0 + v];
-    alx[v] = (T)ctl->alpha[it & 1][c0 + v];
+    al1[v] = (T)ctl->alpha[it & 1][c0 + v];        // alpha_{j-1}
+    al2[v] = (T)ctl->alpha[(it + 1) & 1][c0 + v];  // alpha_{j-2} (this pass overwrites it with alpha_j)
   }
   Acc acc[1][VW];
 #pragma unroll
@@ -734,8 +738,11 @@ __device__ __forceinline__ void body_cg_a(const KArgs<T>& a, const int vb, const
   src.val[0] = a.valA;
   src.vec[0] = a.Z;
   src.vec[1] = Pold;
-  src.vec[2] = a.X;
-  src.vec[3] = a.Q;
+  src.vec[2] = a.Q;
+  if (XUP) {
+    src.vec[3 % Stage::kNvec] = a.X;
+    src.vec[4 % Stage::kNvec] = Pnew;  // still p_{j-2}
+  }
   const bool ok = row_pipeline<Stage>(
       dyn_smem + warp * Stage::kStages * Stage::kBytes, bars[warp], group_map(a.n, RPW, vb, vg), src, [&](const Stage& sg, int row0, int nr) {
         if (rs >= nr) return;
@@ -748,19 +755,24 @@ __device__ __forceinline__ void body_cg_a(const KArgs<T>& a, const int vb, const
         T zj[W][VW];
 #pragma unroll
         for (int k = 0; k < W; ++k) ld_ro(zj[k], a.Z + ((unsigned)cols[k] * ms + c0));
-        T zi[VW], po[VW], x[VW], qo[VW];
+        T zi[VW], po[VW], qo[VW];
         lds(zi, sg.vec(0) + rs * ms + c0);
         lds(po, sg.vec(1) + rs * ms + c0);
-        lds(x, sg.vec(2) + rs * ms + c0);
-        lds(qo, sg.vec(3) + rs * ms + c0);
+        lds(qo, sg.vec(2) + rs * ms + c0);
+        if (XUP) {
+          T x[VW], pp[VW];
+          lds(x, sg.vec(3 % Stage::kNvec) + rs * ms + c0);
+          lds(pp, sg.vec(4 % Stage::kNvec) + rs * ms + c0);
+#pragma unroll
+          for (int v = 0; v < VW; ++v) x[v] = fma(al1[v], po[v], fma(al2[v], pp[v], x[v]));
+          st(a.X + (row * ms + c0), x);
+        }
         T pn[VW], q[VW];
 #pragma unroll
         for (int v = 0; v < VW; ++v) {
           pn[v] = fma(beta[v], po[v], zi[v]);
-          x[v] = fma(alx[v], po[v], x[v]);
           q[v] = T(0);
         }
-        st(a.X + (row * ms + c0), x);
 #pragma unroll
         for (int k = 0; k < W; ++k) {
           const T ak = av[k];
@@ -782,6 +794,19 @@ __device__ __forceinline__ void body_cg_a(const KArgs<T>& a, const int vb, const
     const double pq = tot[0][c];
     ctl->alpha[(it + 1) & 1][c] = (pre_act[c] && pq > 0.0) ? pre_rz[c] / pq : 0.0;
   }
+}
+
+template <typename T, int LPR, int W>
+__device__ __forceinline__ void body_cg_a(const KArgs<T>& a, const int vb, const int vg) {
+  DevCtl* ctl = a.ctl;
+  count_launch(ctl, vb);
+  if (state_finished(a, ctl)) return;
+  if (!ctl->cont && !a.force) return;  // this instance's CG loop has ended (timing runs: force)
+  const int it = ctl->it;
+  if (it & 1)
+    body_cg_a_rows<T, LPR, W, true>(a, vb, vg, it);
+  else
+    body_cg_a_rows<T, LPR, W, false>(a, vb, vg, it);
 }
 
 // Per-component coupling integral on one flat triangle: with a = (u_i at the
@@ -1165,32 +1190,41 @@ __device__ __forceinline__ void body_finish(const KArgs<T>& a, const int vb, con
   SEG_ROW_SETUP
   const int lbase = lane - cg;
   const int it = ctl->it;
+  // the solution updates CG pass A has not applied yet: alpha_k p_k, and
+  // alpha_{k-1} p_{k-1} before it when the iteration count k is odd
   const T* P = (it & 1) ? a.P1 : a.P0;
+  const T* P2 = (it & 1) ? a.P0 : a.P1;
+  const bool two = a.apply_x && (it & 1);
   const unsigned ms = a.ms;
-  T al[VW], invn[VW];
+  T al[VW], al2[VW], invn[VW];
 #pragma unroll
   for (int v = 0; v < VW; ++v) {
     al[v] = a.apply_x ? (T)ctl->alpha[it & 1][c0 + v] : T(0);
+    al2[v] = two ? (T)ctl->alpha[(it + 1) & 1][c0 + v] : T(0);
     invn[v] = (T)ctl->inv_n[c0 + v];
   }
   const T mcoef = -(T)a.coef;
   for (int base = r0 + warp * RPW * RU; base < r1; base += NW * RPW * RU) {
-    T x[RU][VW], p[RU][VW];
+    T x[RU][VW], p[RU][VW], p2[RU][VW];
 #pragma unroll
     for (int u = 0; u < RU; ++u) {
       const unsigned row = base + u * RPW + rs;
 #pragma unroll
-      for (int v = 0; v < VW; ++v) x[u][v] = p[u][v] = T(0);
+      for (int v = 0; v < VW; ++v) x[u][v] = p[u][v] = p2[u][v] = T(0);
       if ((int)row < r1) {
         ld(x[u], a.X + (row * ms + c0));
         if (a.apply_x) ld_ro(p[u], P + (row * ms + c0));
+        if (two) ld_ro(p2[u], P2 + (row * ms + c0));
       }
     }
 #pragma unroll
     for (int u = 0; u < RU; ++u) {
       const unsigned row = base + u * RPW + rs;
 #pragma unroll
-      for (int v = 0; v < VW; ++v) x[u][v] = fma(al[v], p[u][v], x[u][v]);
+      for (int v = 0; v < VW; ++v) {
+        if (two) x[u][v] = fma(al2[v], p2[u][v], x[u][v]);
+        x[u][v] = fma(al[v], p[u][v], x[u][v]);
+      }
       if (a.apply_ode) {
         T sq[1][VW], ex[1][VW], ut[VW];
 #pragma unroll
@@ -1367,7 +1401,9 @@ bool fill_kernels(KernelSet* ks) {
   ks->b_energy_check = (void*)kb_energy_check<T, LPR>;
   ks->b_vote = (void*)k_batch_vote<T>;
   ks->smem_start = row_stage_smem<StartStage<T, LPR, W>>();
-  ks->smem_cg_a = row_stage_smem<CgAStage<T, LPR, W>>();
+  ks->smem_cg_a = row_stage_smem<CgAStage<T, LPR, W, true>>() > row_stage_smem<CgAStage<T, LPR, W, false>>()
+                      ? row_stage_smem<CgAStage<T, LPR, W, true>>()
+                      : row_stage_smem<CgAStage<T, LPR, W, false>>();
   return true;
 }
 
