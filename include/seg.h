@@ -76,10 +76,11 @@ typedef struct {
                             the energy check is skipped entirely if set < 0 */
   double energy_tol;     /* stop when |total_k - total_{k - M_tau}| < energy_tol; default
                             1e-6 (Sec. 2.2); a negative value disables stopping */
-  int32_t launch_mode;   /* 0 (default): each step is one CUDA graph whose CG loop is a
-                            device-controlled WHILE node; 1: the same kernels launched one
-                            by one with a host check per CG iteration (slower; for tools
-                            that cannot look inside graphs with conditional nodes) */
+  int32_t launch_mode;   /* 0 (default): each step is one CUDA graph (built at the first
+                            step) whose CG loop runs its first iterations as plain nodes and
+                            the rest in a device-controlled WHILE node; 1: the same kernels
+                            launched one by one with a host check per CG iteration (slower;
+                            for tools that cannot look inside graphs with conditional nodes) */
   int32_t reserved;      /* must be 0 */
   int64_t max_steps;     /* the state stops for good after this many steps (0: no limit); unlike
                             seg_step's nsteps this also holds inside batches and the server */

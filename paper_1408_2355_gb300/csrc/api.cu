@@ -1,12 +1,15 @@
 // C ABI of the library (declared in include/seg.h): handles, validation,
-// device buffers, and the CUDA graph of one step of Algorithm 2.2.
+// device buffers, the CUDA graph of one step of Algorithm 2.2, batches and the
+// launch-geometry autotuner.
 //
 // The step graph is
-//     k_start -> k_energy -> WHILE(cond) { k_cg_a -> k_cg_b } -> k_finish
+//     k_start -> k_energy_check -> (k_cg_a -> k_cg_b) x cg_peel
+//             -> WHILE(cond) { (k_cg_a -> k_cg_b) x kCgUnroll } -> k_finish
 // where the WHILE node's condition is set on the device by the last block of
-// k_start (any component still above tolerance), k_energy (stop rule) and
-// k_cg_b (convergence / iteration cap), so a whole step -- including the
-// data-dependent CG iteration count -- runs without a host round trip.
+// k_start (any component still above tolerance), k_energy_check (stop rule)
+// and k_cg_b (convergence / iteration cap); passes after the loop has ended
+// return at once.  A whole step -- including the data-dependent CG iteration
+// count -- runs without a host round trip.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -694,6 +697,10 @@ seg_status seg_state_create(const seg_problem* p, int32_t m, double eps, seg_ini
   if (prm.grid_blocks > kMaxGrid) {
     delete s;
     return fail(SEG_ERR_ARG, "grid_blocks must be at most 2048");
+  }
+  if (prm.reserved != 0) {
+    delete s;
+    return fail(SEG_ERR_ARG, "seg_params.reserved must be 0");
   }
   s->launch_mode = prm.launch_mode;
   bool ok = s->prec == SEG_MIXED_FP32 ? get_kernels_f32(s->lpr, p->ell_w, &s->ks)

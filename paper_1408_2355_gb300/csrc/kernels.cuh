@@ -7,17 +7,20 @@
 // read of a padded-ELL matrix row (W column indices + W values) serves all m
 // components.
 //
-// Per step the kernels run in this order (one CUDA graph per step, the CG
-// loop is a device-controlled conditional WHILE node):
-//   k_start   r0 = -tau K X (warm start x0 = X: M X - A X = -tau K X),
-//             z0 = D^-1 r0, and the per-component sums ||X||_M^2, X^T K X,
-//             r0.z0, ||M X||^2, ||r0||^2 -- the renormalisation of the
-//             previous step (step 3) is fused here
-//   k_energy  (every check_every steps) S_eps and the coupling integrals
-//   k_cg_a    p = z + beta p_old, q = A p, p.q; lagged x += alpha p_old
-//   k_cg_b    z -= alpha D^-1 q, r.z and r.r (r = D z); convergence and beta
-//   k_finish  last x += alpha p, then the exact nodal ODE of step 2
-// The two gather kernels stage each warp's next group of rows (ELL indices,
+// Per step the kernels run in this order (one CUDA graph per step: the first
+// CG iterations as plain nodes, the rest in a device-controlled conditional
+// WHILE node):
+//   k_start         r0 = -tau K X (warm start x0 = X: M X - A X = -tau K X),
+//                   z0 = D^-1 r0, and the per-component sums ||X||_M^2,
+//                   X^T K X, r0.z0, ||M X||^2, ||r0||^2 -- the
+//                   renormalisation of the previous step (step 3) is fused here
+//   k_energy_check  (every check_every steps) S_eps and the stop rule
+//   k_cg_a          p = z + beta p_old, q = A z + beta q_old, p.q; every second
+//                   iteration x += the two pending alpha p terms
+//   k_cg_b          z -= alpha D^-1 q, r.z and r.r (r = D z); convergence, beta
+//   k_finish        the solution updates still pending, then the exact nodal
+//                   ODE of step 2
+// The two gather kernels stage each warp's next groups of rows (ELL indices,
 // values and own vector rows) in shared memory with TMA bulk copies while the
 // current group's neighbour rows are gathered.
 //
@@ -28,7 +31,7 @@
 // sums that only set the CG tolerance accumulate in float per lane.  For
 // double data everything is float64.  The grid reduction is done by the last
 // block to finish (ticket counter), in a fixed order, so results are bitwise
-// reproducible for a fixed launch geometry.
+// reproducible for a fixed launch geometry, alone or in a batch.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -501,9 +504,9 @@ __device__ __forceinline__ GroupMap group_map(int n, int rpw, int vb, int vg) {
   return g;
 }
 
-// Warp-level pipeline over the row groups of the block (GroupMap); warp w
-// takes local groups w, w+NW, ...  The copies of
-// the warp's next Stage::kStages - 1 groups are in flight while one group is
+// Warp-level pipeline over the row groups of the block (GroupMap, groups of
+// Stage::RPW rows); warp w takes local groups w, w+NW, ...  The copies of the
+// warp's next Stage::kStages - 1 groups are in flight while one group is
 // processed.  `body(stage, row0, nr)` consumes a landed stage.  Returns false
 // if a wait timed out (the copies still in flight are waited for, bounded).
 template <typename Stage, typename Body>
@@ -512,6 +515,7 @@ __device__ __forceinline__ bool row_pipeline(unsigned char* smem_warp, unsigned 
   constexpr int NW = kBlockThreads / 32;
   constexpr int RPW = Stage::RPW;
   constexpr int NS = Stage::kStages;
+  static_assert(RPW >= 1 && NS >= 2, "pipeline shape");
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int ngroups = gm.ngroups;
   const int n = gm.n;
