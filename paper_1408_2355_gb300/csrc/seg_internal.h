@@ -12,12 +12,12 @@
 namespace segimpl {
 
 constexpr int kMaxCols = 32;       // padded components per vertex row
-constexpr int kBlockThreads = 256;  // threads per block of every row kernel
+constexpr int kBlockThreads = 384;  // threads per block of every row kernel
 constexpr int kMaxDots = 5;         // inner products fused into one pass
 // Resident blocks per SM the row passes are compiled for (register bound)
 // and launched with; the triangle passes use kTriBlocksPerSM.
-constexpr int kRowBlocksPerSM = 3;
-constexpr int kTriBlocksPerSM = 4;
+constexpr int kRowBlocksPerSM = 2;
+constexpr int kTriBlocksPerSM = 2;
 constexpr int kMaxGrid = 2048;  // blocks of one kernel of a state
 constexpr int kTuneWaves = 4;   // the autotuner tries up to this many waves of blocks
 constexpr int kCgUnroll = 2;    // CG iterations per evaluation of the step graph's loop condition
