@@ -71,7 +71,7 @@ typedef struct {
   double cg_rtol;        /* step-1 CG stops at ||r||_2 <= cg_rtol ||M u||_2 per component;
                             default 1e-12 (SEG_FP64), 1e-7 (SEG_MIXED_FP32) */
   int32_t cg_maxit;      /* default 1000 */
-  int32_t grid_blocks;   /* CUDA blocks of the row kernels (<= 2048); default 3 per SM */
+  int32_t grid_blocks;   /* CUDA blocks of the row kernels (<= 2048); default 2 per SM */
   int64_t check_every;   /* Sec. 2.2 stop rule cadence M_tau; default round(0.1 / tau);
                             the energy check is skipped entirely if set < 0 */
   double energy_tol;     /* stop when |total_k - total_{k - M_tau}| < energy_tol; default
@@ -391,8 +391,8 @@ typedef struct {
 
 /* Pick the launch geometry of a state by measurement (no counterpart in the
  * paper; the arithmetic of Algorithm 2.2 is unchanged).  The row grid (and
- * with it the block of rows each CUDA block owns) is chosen among 1 ..
- * 3 blocks per SM and 2 or 4 waves of 3 blocks per SM (at most one block per
+ * with it the block of rows each CUDA block owns) is chosen among 1 or 2
+ * blocks per SM and 2 or 4 waves of 2 blocks per SM (at most one block per
  * 256 rows, at most 2048 blocks), separately for each of the four row
  * passes (start, CG pass A, CG pass B, finish): each pass keeps the candidate
  * with its shortest time, the mean of `reps` (<= 0: 10) timed launches.
@@ -400,7 +400,7 @@ typedef struct {
  * with all passes on candidate c, ms_model the same with each pass on its
  * chosen grid, k the state's CG iterations per step so far (8 before its
  * first step); grid_blocks is CG pass A's grid.  The energy-check grid
- * among 1 .. 4 blocks per SM and 2 or 4 waves of 4 blocks per SM by its own
+ * among 1 or 2 blocks per SM and 2 or 4 waves of 2 blocks per SM by its own
  * time.  The state's data and
  * counters are saved before and restored bitwise after the timing launches,
  * and its step graph is rebuilt with the chosen geometry and with cg_peel =
