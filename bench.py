@@ -607,7 +607,7 @@ def main():
     if rank == 0:
         if a.serve_requests > 0 and ws == 1:
             out["serving"] = serving_section(a)
-        if not a.no_cpu_baseline and ws >= 1:
+        if not a.no_cpu_baseline and ws == 1:  # the oracle baseline at N = 1 only
             out["cpu_baseline"] = cpu_baseline(a)
         print(json.dumps(out), flush=True)
     if ws > 1:
