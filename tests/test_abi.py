@@ -102,6 +102,25 @@ def test_native_dziuk_and_refinement_equal_shared_generator(seg):
     assert e.value.status == seg.SEG_ERR_ARG
 
 
+def test_degenerate_meshes(seg):
+    xyz, tri = w.icosphere(1)
+    with pytest.raises(seg.SegError) as e:  # no triangles
+        seg.seg_create_mesh(xyz, tri[:0])
+    assert e.value.status == seg.SEG_ERR_ARG
+    with pytest.raises(seg.SegError) as e:  # fewer than 3 vertices
+        seg.seg_create_mesh(xyz[:2], np.zeros((0, 3), dtype=np.int32))
+    assert e.value.status == seg.SEG_ERR_ARG
+    # a vertex in no triangle has no mass: the step-1 matrix would be singular
+    extra = np.concatenate([xyz, [[0.0, 0.0, 2.0]]])
+    with pytest.raises(seg.SegError) as e:
+        seg.seg_assemble(seg.seg_create_mesh(extra, tri), 1e-3, 1)
+    assert e.value.status == seg.SEG_ERR_MESH
+    for tau in (0.0, -1.0, float("nan"), float("inf")):
+        with pytest.raises(seg.SegError) as e:
+            seg.seg_assemble(seg.seg_create_mesh(xyz, tri), tau, 1)
+        assert e.value.status == seg.SEG_ERR_ARG
+
+
 def test_mesh_validation_errors(seg):
     xyz, tri = w.icosphere(1)
     m = seg.seg_create_mesh(xyz, tri)
