@@ -198,6 +198,10 @@ def test_error_statuses(seg):
     with pytest.raises(seg.SegError) as e:
         seg.seg_step(st, 1)
     assert e.value.status == seg.SEG_ERR_NONFINITE
+    # new data recovers the state (no NaN left in its CG work vectors)
+    seg.seg_set_u(st, w.initial_values("uniform", 3, xyz.shape[0], 3))
+    assert seg.seg_step(st, 3) == 3
+    assert np.isfinite(seg.seg_get_u(st)).all() and np.isfinite(seg.seg_energy(st)["total"])
     with pytest.raises(seg.SegError) as e:
         make_state(seg, xyz, tri, 1e-2, 33, 0.1, 0)
     assert e.value.status == seg.SEG_ERR_UNSUPPORTED
