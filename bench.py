@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch geometry")
     ap.add_argument("--grid-blocks", type=int, default=0, help="row-kernel blocks (0: default / autotuned)")
+    ap.add_argument("--batch-steps", type=int, default=200, help="0 disables the two-instance batch run")
     ap.add_argument("--serve-requests", type=int, default=256, help="0 disables the serving run")
     ap.add_argument("--serve-compare", type=int, default=24)
     ap.add_argument("--serve-rate", type=float, default=20.0)
@@ -537,6 +538,50 @@ def run_alone(a, seg, prec):
             "converged_fraction": conv / len(reqs)}
 
 
+def batched_section(a):
+    """Two instances in one launch per pass: torus 1024 x 512 (R = 1, r = 0.4)
+    and the level-8 ellipsoid (semi-axes 1, 0.8, 0.6), m = 12, eps = 1e-3,
+    tau = 5e-6, mixed precision; each member autotuned first.  DoF-steps/s of
+    the batch against the two states stepped one after the other."""
+    import torch
+
+    import paper_1408_2355_gb300 as seg
+    import workload as w
+
+    meshes = [w.torus(1024, 512, 1.0, 0.4), w.ellipsoid(a.level, 1.0, 0.8, 0.6)]
+    m, steps = 12, a.batch_steps
+    prm = seg.seg_params()
+    prm.check_every = 1
+    prm.energy_tol = -1.0
+    states, probs, dof = [], [], 0
+    for k, (xyz, tri) in enumerate(meshes):
+        prob = seg.seg_assemble(seg.seg_create_mesh(xyz, tri), a.tau, seg.SEG_MIXED_FP32)
+        st = seg.seg_state_create(prob, m, a.eps, seg.SEG_INIT_UNIFORM, a.seed + 10 + k, prm)
+        seg.seg_step(st, 20)
+        seg.seg_autotune(st, 5)
+        probs.append(prob)
+        states.append(st)
+        dof += xyz.shape[0] * m
+    batch = seg.seg_batch_create(states)
+    seg.seg_batch_step(batch, 3)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    seg.seg_batch_step(batch, steps)
+    t_batch = time.perf_counter() - t0
+    del batch
+    for st in states:
+        seg.seg_step(st, 3)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for st in states:
+        seg.seg_step(st, steps)
+    t_alone = time.perf_counter() - t0
+    return {"workload": "torus 1024x512 + ellipsoid level %d, m = 12, eps = %g, tau = %g, mixed" % (a.level, a.eps, a.tau),
+            "steps": steps, "value": dof * steps / t_batch, "unit": "DoF-steps/s",
+            "alone_one_after_the_other": dof * steps / t_alone, "batch_over_alone": t_alone / t_batch,
+            "timing": "host clock around synchronous calls, energy check every step"}
+
+
 def serving_section(a):
     """Serving benchmark: the Poisson stream (latency), and the first
     --serve-compare requests as a burst through the server in mixed precision
@@ -605,6 +650,8 @@ def main():
         return
     out = run_ours(a, rank, ws, local)
     if rank == 0:
+        if a.batch_steps > 0 and ws == 1:
+            out["batched"] = batched_section(a)
         if a.serve_requests > 0 and ws == 1:
             out["serving"] = serving_section(a)
         if not a.no_cpu_baseline and ws == 1:  # the oracle baseline at N = 1 only
