@@ -147,13 +147,13 @@ __device__ __forceinline__ void zero_part(double& p) { p = 0.0; }
 // part[p * G + b] holds block b's partial of sum p (every block has written
 // its own before the call).  The last block to arrive (ticket) sums them:
 // warp w takes sums w, w + NW, ... two at a time; lane l adds blocks l,
-// l + 32, ... in order (up to 2 x 8 loads in flight), then a fixed shuffle
+// l + 32, ... in order (up to 2 x 10 loads in flight), then a fixed shuffle
 // tree; out(p, total) is called from lane 0.  Returns true in that block
 // only.  Must be reached by every block of the grid.
 template <typename Acc, typename Part, typename Out>
 __device__ __forceinline__ bool reduce_blocks(const Part* part, unsigned int* count, int P, int vb, int G, Out out) {
   constexpr int NW = kBlockThreads / 32;
-  constexpr int U = 8;  // loads per lane and sum in flight
+  constexpr int U = 10;  // loads per lane and sum in flight (one pass covers 320 blocks)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   __shared__ unsigned int ticket;
   (void)vb;
