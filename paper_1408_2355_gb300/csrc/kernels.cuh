@@ -354,17 +354,33 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
-// Bounded wait for the phase `parity` of `bar`: false after kWaitPolls tries.
-constexpr unsigned kWaitPolls = 1u << 24;
+// Bounded wait for the phase `parity` of `bar`: false once kWaitNs have
+// passed (globaltimer).  Each try may suspend the warp for up to kSuspendNs
+// until the phase completes, so a waiting warp does not spin on the issue
+// slots that the other warps of the SM need.
+constexpr unsigned kSuspendNs = 2000;
+constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3; selp.u32 %0, 1, 0, p; }"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendNs)
+      : "memory");
+  return ok != 0;
+}
 __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
-  for (unsigned n = 0; n < kWaitPolls; ++n) {
-    unsigned ok;
-    asm volatile(
-        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    if (ok) return true;
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  // bounded by time and, as a backstop, by the number of tries
+  for (unsigned n = 0; n < (1u << 26); ++n) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > kWaitNs) return false;
   }
   return false;
 }
