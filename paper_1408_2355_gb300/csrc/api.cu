@@ -1025,12 +1025,11 @@ seg_status build_batch_t(seg_batch* b) {
     for (int k = 0; k < 4; ++k) rows[k].off[i + 1] = rows[k].off[i] + s->grid[k];
     tris.off[i + 1] = tris.off[i] + s->grid_e;
   }
-  SEG_CUDA(cudaMalloc(&b->tab, n * sizeof(KArgs<T>)));
-  SEG_CUDA(cudaMemcpy(b->tab, tab.data(), n * sizeof(KArgs<T>), cudaMemcpyHostToDevice));
+
   SEG_CUDA(cudaGraphCreate(&b->graph, 0));
   SEG_CUDA(cudaGraphConditionalHandleCreate(&b->cond, b->graph, 0, cudaGraphCondAssignDefault));
   for (BatchArgs<T>* x : {&rows[0], &rows[1], &rows[2], &rows[3], &tris, &vote}) {
-    x->tab = (const KArgs<T>*)b->tab;
+    for (int i = 0; i < n; ++i) x->tab[i] = tab[i];
     x->ninst = n;
     x->cond = (unsigned long long)b->cond;
   }

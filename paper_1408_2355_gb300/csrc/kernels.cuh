@@ -1297,7 +1297,7 @@ __device__ __forceinline__ int batch_slot(const BatchArgs<T>& b) {
   }                                                                                                 \
   TPL __global__ void __launch_bounds__(kBlockThreads, MINB) kb_##NAME(const BatchArgs<T> b) {         \
     const int i = batch_slot(b);                                                                    \
-    const KArgs<T> a = b.tab[i];                                                                    \
+    const KArgs<T>& a = b.tab[i];                                                                   \
     body_##NAME<__VA_ARGS__>(a, (int)blockIdx.x - b.off[i], b.off[i + 1] - b.off[i]);               \
   }
 

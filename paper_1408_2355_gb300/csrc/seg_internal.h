@@ -118,7 +118,7 @@ __device__ __forceinline__ bool state_finished(const KArgs<T>& a, const DevCtl* 
 constexpr int kMaxBatch = 32;
 template <typename T>
 struct BatchArgs {
-  const KArgs<T>* tab;
+  KArgs<T> tab[kMaxBatch];  // in the kernel's parameter space (read through the constant cache)
   int ninst;
   int off[kMaxBatch + 1];
   unsigned long long cond;  // conditional handle of the batch's CG loop
