@@ -224,22 +224,23 @@ def kernel_bytes(n, ntri, m_pad, s, W=8):
     V = N * m_pad * s is one state-sized vector.  Gathered neighbour rows
     count once (each unique row is needed once); the padded-ELL matrix rows
     are W int32 columns plus W values per vertex, the Jacobi diagonal N * s.
-      k_start  read X, write Z, columns + K + M values, Jacobi inverse diagonal
+      k_start  read X and the carried correction Y, write Z, columns + K + M + A values,
+               Jacobi inverse diagonal
       k_cg_a   even iterations: read Z, p_old, q_old; write p_new, q; columns + A values;
-               odd iterations also read X and p_{j-2} and write X (two solution updates)
+               odd iterations also read Y and p_{j-2} and write Y (two solution updates)
       k_cg_b   read Z, q; write Z; diagonal of A and its inverse
-      k_finish read X, p (and p of the iteration before after an odd count); write X
+      k_finish read X, Y, p (and p of the iteration before after an odd count); write X
       k_energy_check / k_energy  read X, triangle corners (3 int32) and areas
     """
     V = n * m_pad * s
     ell = n * W * 4
     return {
-        "k_start": 2 * V + ell + 2 * n * W * s + n * s,
+        "k_start": 3 * V + ell + 3 * n * W * s + n * s,
         "k_cg_a_even": 5 * V + ell + n * W * s,
         "k_cg_a_odd": 8 * V + ell + n * W * s,
         "k_cg_b": 3 * V + 2 * n * s,
-        "k_finish_even": 3 * V,
-        "k_finish_odd": 4 * V,
+        "k_finish_even": 4 * V,
+        "k_finish_odd": 5 * V,
         "k_energy_check": V + ntri * (12 + s),
         "k_energy": V + ntri * (12 + s),
     }
@@ -343,7 +344,7 @@ def run_ours(a, rank, ws, local):
             "precision": "mixed: f32 vectors/matrices/exp, inner products and CG scalars to f64 accuracy",
             "cg_rtol": 1e-7,
             "energy_every_step": True,
-            "l2": "inputs larger than L2: 5 state vectors x 42 MB + 76 MB of CSR > 129 MB L2",
+            "l2": "inputs larger than L2: 6 state vectors x 42 MB + 84 MB of padded-ELL matrices > 129 MB L2",
             "grid_blocks": li["grid_blocks"],
             "autotune": tunes.get(seg.SEG_MIXED_FP32),
             "launch_mode": a.launch_mode,

@@ -10,16 +10,17 @@
 // Per step the kernels run in this order (one CUDA graph per step: the first
 // CG iterations as plain nodes, the rest in a device-controlled conditional
 // WHILE node):
-//   k_start         r0 = -tau K X (warm start x0 = X: M X - A X = -tau K X),
-//                   z0 = D^-1 r0, and the per-component sums ||X||_M^2,
-//                   X^T K X, r0.z0, ||M X||^2, ||r0||^2 -- the
+//   k_start         r0 = M X - A (X + y) = -tau K X - A y for the iterate
+//                   x = X + y (y: the correction the previous solve ended
+//                   with), z0 = D^-1 r0, and the per-component sums
+//                   ||X||_M^2, X^T K X, r0.z0, ||M X||^2, ||r0||^2 -- the
 //                   renormalisation of the previous step (step 3) is fused here
 //   k_energy_check  (every check_every steps) S_eps and the stop rule
 //   k_cg_a          p = z + beta p_old, q = A z + beta q_old, p.q; every second
-//                   iteration x += the two pending alpha p terms
+//                   iteration y += the two pending alpha p terms
 //   k_cg_b          z -= alpha D^-1 q, r.z and r.r (r = D z); convergence, beta
-//   k_finish        the solution updates still pending, then the exact nodal
-//                   ODE of step 2
+//   k_finish        x = X + y with the updates still pending, then the exact
+//                   nodal ODE of step 2
 // The two gather kernels stage each warp's next groups of rows (ELL indices,
 // values and own vector rows) in shared memory with TMA bulk copies while the
 // current group's neighbour rows are gathered.
@@ -595,15 +596,21 @@ __device__ __forceinline__ bool row_pipeline(unsigned char* smem_warp, unsigned 
 }
 
 template <typename T, int LPR, int W>
-using StartStage = RowStage<T, LPR, W, 2, 1>;
+using StartStage = RowStage<T, LPR, W, 3, 1>;
 template <typename T, int LPR, int W, bool XUP>
 using CgAStage = RowStage<T, LPR, W, 1, XUP ? 5 : 3>;
 
-// Start pass (warm start x0 = X of the CG solve of step 1, and the fused
-// renormalisation of the previous step):
-//   r0 = M X - (M + tau K) X = -tau K X,  z0 = D^-1 r0  -> Z,
-// per component  ||X||_M^2, X^T K X, r0.z0  (float-float) and
-// ||M X||_2^2, ||r0||_2^2 (float32 per thread; they only set the tolerance).
+// Start pass of the CG solve of step 1, (M + tau K) x = M X, fused with the
+// renormalisation of the previous step.  The iterate is x = X + y, with y
+// starting at w Y: Y holds the correction x - X the previous step's solve
+// ended with (a prediction of this step's correction; 0 after a state is
+// set) and w (per component, 0 or 1) says whether the last start pass found
+// that prediction better than none:
+//   r0 = M X - (M + tau K)(X + w Y) = -tau K X - w A Y,  z0 = D^-1 r0  -> Z,
+// per component  ||X||_M^2, X^T K X, r0.z0  (float-float) and, in float32 per
+// thread (they only set the tolerance and the choice of w), ||M X||_2^2 and
+// the squared norms of the residuals of both starts, -tau K X and
+// -tau K X - A Y.  The next step uses w = 1 where the second was smaller.
 template <typename T, int LPR, int W>
 __device__ __forceinline__ void body_start(const KArgs<T>& a, const int vb, const int vg) {
   typedef typename AccOf<T>::type Acc;
@@ -616,18 +623,23 @@ __device__ __forceinline__ void body_start(const KArgs<T>& a, const int vb, cons
   __shared__ __align__(8) unsigned long long bars[NW][kPipeStages];
   const T tau = (T)a.tau;
   const unsigned ms = a.ms;
-  Acc acc[5][VW];
+  Acc acc[6][VW];
 #pragma unroll
-  for (int d = 0; d < 5; ++d)
+  for (int d = 0; d < 6; ++d)
 #pragma unroll
     for (int v = 0; v < VW; ++v) acc[d][v].zero();
-  T bb[VW], rr[VW];
+  T bb[VW], rra[VW], rrb[VW];
+  unsigned om = 0;  // bit v: this lane's component c0 + v starts from the carried correction
 #pragma unroll
-  for (int v = 0; v < VW; ++v) bb[v] = rr[v] = T(0);
+  for (int v = 0; v < VW; ++v) {
+    bb[v] = rra[v] = rrb[v] = T(0);
+    if (ctl->carry[c0 + v]) om |= 1u << v;
+  }
   typename Stage::Src src;
   src.ell = a.ell_col;
   src.val[0] = a.valK;
   src.val[1] = a.valM;
+  src.val[2] = a.valA;
   src.vec[0] = a.X;
   const bool ok = row_pipeline<Stage>(
       dyn_smem + warp * Stage::kStages * Stage::kBytes, bars[warp], group_map(a.n, RPW, vb, vg), src, [&](const Stage& sg, int row0, int nr) {
@@ -656,10 +668,25 @@ __device__ __forceinline__ void body_start(const KArgs<T>& a, const int vb, cons
             mx[v] = fma(mm, xj[k][v], mx[v]);
           }
         }
+        T ay[VW], av[W];
+        lds_row<W>(av, sg.vals(2) + rs * W);
+#pragma unroll
+        for (int v = 0; v < VW; ++v) ay[v] = T(0);
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+          T yj[VW];
+          ld_ro(yj, a.Y + ((unsigned)cols[k] * ms + c0));
+          const T ak = av[k];
+#pragma unroll
+          for (int v = 0; v < VW; ++v) ay[v] = fma(ak, yj[v], ay[v]);
+        }
         T r[VW], z[VW];
 #pragma unroll
         for (int v = 0; v < VW; ++v) {
-          r[v] = -tau * kx[v];
+          const T ra = -tau * kx[v], rb = ra - ay[v];
+          rra[v] = fma(ra, ra, rra[v]);
+          rrb[v] = fma(rb, rb, rrb[v]);
+          r[v] = (om >> v) & 1u ? rb : ra;
           z[v] = di * r[v];
         }
         st(a.Z + (row * ms + c0), z);
@@ -669,22 +696,26 @@ __device__ __forceinline__ void body_start(const KArgs<T>& a, const int vb, cons
           acc[2][v].add_prod(x[v], kx[v]);
           acc[3][v].add_prod(r[v], z[v]);
           bb[v] = fma(mx[v], mx[v], bb[v]);
-          rr[v] = fma(r[v], r[v], rr[v]);
         }
       });
   if (__syncthreads_or(!ok) && threadIdx.x == 0) report_timeout(ctl);
 #pragma unroll
   for (int v = 0; v < VW; ++v) {
     acc[1][v].add_val(bb[v]);
-    acc[4][v].add_val(rr[v]);
+    acc[4][v].add_val(rra[v]);
+    acc[5][v].add_val(rrb[v]);
   }
-  __shared__ double tot[5][kMaxCols];
-  if (!grid_reduce<T, LPR, 5>(acc, a, kCtrStart, tot, vb, vg)) return;
+  __shared__ double tot[6][kMaxCols];
+  if (!grid_reduce<T, LPR, 6>(acc, a, kCtrStart, tot, vb, vg)) return;
   int act = 0, bad = 0;
   const int c = threadIdx.x;
   if (c < a.ms) {
-    const double n2 = tot[0][c], bbt = tot[1][c], ukt = tot[2][c], rz = tot[3][c], rrt = tot[4][c];
+    const bool used = ctl->carry[c] != 0;
+    const double n2 = tot[0][c], bbt = tot[1][c], ukt = tot[2][c], rz = tot[3][c];
+    const double rrt = used ? tot[5][c] : tot[4][c];
     const bool real = c < a.m;
+    ctl->ysc[c] = used ? 1.0 : 0.0;
+    ctl->carry[c] = (real && tot[5][c] < tot[4][c]) ? 1 : 0;
     if (real && !(n2 > 0.0 && isfinite(n2) && isfinite(rrt) && isfinite(ukt))) bad = 1;
     ctl->n2[c] = n2;
     ctl->inv_n[c] = (real && n2 > 0.0) ? 1.0 / sqrt(n2) : 0.0;
@@ -716,11 +747,12 @@ __device__ __forceinline__ void body_start(const KArgs<T>& a, const int vb, cons
 //   q_j = A p_j = A z_{j-1} + beta q_{j-1}           (q_{j-1} = A p_{j-1} from the
 //         previous pass A, own row; only z is gathered from the neighbours)
 //   p_j . q_j  (float-float).
-// The solution is updated every second iteration, two terms at a time (the
-// search directions of the last two iterations are both still in the
-// ping-pong buffers): for even j,  x += alpha_{j-2} p_{j-2} + alpha_{j-1} p_{j-1},
+// The solution (its correction y, buffer Y) is updated every second
+// iteration, two terms at a time (the search directions of the last two
+// iterations are both still in the ping-pong buffers): for even j,
+// y += alpha_{j-2} p_{j-2} + alpha_{j-1} p_{j-1},
 // the same sequence of operations as one lagged update per iteration, with
-// one read and write of x saved per two iterations; the finish pass applies
+// one read and write of y saved per two iterations; the finish pass applies
 // what is left.  In the first iteration of a step beta = 0 and alpha = 0
 // (any finite old values will do).
 // Padded ELL entries point at the row itself with value 0 (no branches).
@@ -743,12 +775,13 @@ __device__ __forceinline__ void body_cg_a_rows(const KArgs<T>& a, const int vb, 
   const T* Pold = (it & 1) ? a.P1 : a.P0;
   T* Pnew = (it & 1) ? a.P0 : a.P1;
   const unsigned ms = a.ms;
-  T beta[VW], al1[VW], al2[VW];
+  T beta[VW], al1[VW], al2[VW], ysc[VW];
 #pragma unroll
   for (int v = 0; v < VW; ++v) {
     beta[v] = (T)ctl->beta[c0 + v];
     al1[v] = (T)ctl->alpha[it & 1][c0 + v];        // alpha_{j-1}
     al2[v] = (T)ctl->alpha[(it + 1) & 1][c0 + v];  // alpha_{j-2} (this pass overwrites it with alpha_j)
+    ysc[v] = it == 1 ? (T)ctl->ysc[c0 + v] : T(1);  // the first update starts from w Y
   }
   Acc acc[1][VW];
 #pragma unroll
@@ -760,7 +793,7 @@ __device__ __forceinline__ void body_cg_a_rows(const KArgs<T>& a, const int vb, 
   src.vec[1] = Pold;
   src.vec[2] = a.Q;
   if (XUP) {
-    src.vec[3 % Stage::kNvec] = a.X;
+    src.vec[3 % Stage::kNvec] = a.Y;
     src.vec[4 % Stage::kNvec] = Pnew;  // still p_{j-2}
   }
   const bool ok = row_pipeline<Stage>(
@@ -784,8 +817,8 @@ __device__ __forceinline__ void body_cg_a_rows(const KArgs<T>& a, const int vb, 
           lds(x, sg.vec(3 % Stage::kNvec) + rs * ms + c0);
           lds(pp, sg.vec(4 % Stage::kNvec) + rs * ms + c0);
 #pragma unroll
-          for (int v = 0; v < VW; ++v) x[v] = fma(al1[v], po[v], fma(al2[v], pp[v], x[v]));
-          st(a.X + (row * ms + c0), x);
+          for (int v = 0; v < VW; ++v) x[v] = fma(al1[v], po[v], fma(al2[v], pp[v], ysc[v] * x[v]));
+          st(a.Y + (row * ms + c0), x);
         }
         T pn[VW], q[VW];
 #pragma unroll
@@ -1198,43 +1231,51 @@ __device__ __forceinline__ void body_cg_b(const KArgs<T>& a, const int vb, const
   }
 }
 
-// Last CG update x += alpha p (lagged from the final iteration), then the
-// exact solution of the nodal ODE of step 2 (Jacobi form):
-//   u~ = x * inv_n,  u^_i = u~_i exp(-(2 tau/eps^2) sum_{j != i} u~_j^2).
-template <typename T, int LPR>
-__device__ __forceinline__ void body_finish(const KArgs<T>& a, const int vb, const int vg) {
-  constexpr int RU = kStreamRows;
+// The solve's result x = X + y with the CG updates of y not yet applied
+// (lagged from the last iterations; apply_x, else x = X), then the exact
+// solution of the nodal ODE of step 2 (Jacobi form):
+//   u~ = x * inv_n,  u^_i = u~_i exp(-(2 tau/eps^2) sum_{j != i} u~_j^2)  -> X.
+// Y keeps the correction without those last updates (or an older one if the
+// solve ended before its second iteration): the next step may start its
+// solve from it (any initial guess gives the same solution to the solve's
+// tolerance; the last updates are the smallest).
+// The solution updates CG pass A has not applied yet: alpha_k p_k, and
+// alpha_{k-1} p_{k-1} before it (TWO) when the iteration count k is odd.
+template <typename T, int LPR, int RU, bool TWO>
+__device__ __forceinline__ void body_finish_rows(const KArgs<T>& a, const int vb, const int vg, const int it) {
   DevCtl* ctl = a.ctl;
-  count_launch(ctl, vb);
-  if (state_finished(a, ctl)) return;
   SEG_ROW_SETUP
   const int lbase = lane - cg;
-  const int it = ctl->it;
-  // the solution updates CG pass A has not applied yet: alpha_k p_k, and
-  // alpha_{k-1} p_{k-1} before it when the iteration count k is odd
   const T* P = (it & 1) ? a.P1 : a.P0;
   const T* P2 = (it & 1) ? a.P0 : a.P1;
-  const bool two = a.apply_x && (it & 1);
+  constexpr bool two = TWO;
   const unsigned ms = a.ms;
-  T al[VW], al2[VW], invn[VW];
+  T al[VW], al2[VW], invn[VW], ysc[VW];
 #pragma unroll
   for (int v = 0; v < VW; ++v) {
     al[v] = a.apply_x ? (T)ctl->alpha[it & 1][c0 + v] : T(0);
     al2[v] = two ? (T)ctl->alpha[(it + 1) & 1][c0 + v] : T(0);
     invn[v] = (T)ctl->inv_n[c0 + v];
+    ysc[v] = it < 2 ? (T)ctl->ysc[c0 + v] : T(1);  // no update of Y yet in this solve: y = w Y
   }
   const T mcoef = -(T)a.coef;
   for (int base = r0 + warp * RPW * RU; base < r1; base += NW * RPW * RU) {
-    T x[RU][VW], p[RU][VW], p2[RU][VW];
+    T x[RU][VW], y[RU][VW], p[RU][VW], p2[TWO ? RU : 1][VW];
 #pragma unroll
     for (int u = 0; u < RU; ++u) {
       const unsigned row = base + u * RPW + rs;
 #pragma unroll
-      for (int v = 0; v < VW; ++v) x[u][v] = p[u][v] = p2[u][v] = T(0);
+      for (int v = 0; v < VW; ++v) {
+        x[u][v] = y[u][v] = p[u][v] = T(0);
+        if (two) p2[u][v] = T(0);
+      }
       if ((int)row < r1) {
         ld(x[u], a.X + (row * ms + c0));
-        if (a.apply_x) ld_ro(p[u], P + (row * ms + c0));
-        if (two) ld_ro(p2[u], P2 + (row * ms + c0));
+        if (a.apply_x) {
+          ld_ro(y[u], a.Y + (row * ms + c0));
+          ld_ro(p[u], P + (row * ms + c0));
+        }
+        if (two) ld_ro(p2[TWO ? u : 0], P2 + (row * ms + c0));
       }
     }
 #pragma unroll
@@ -1242,8 +1283,9 @@ __device__ __forceinline__ void body_finish(const KArgs<T>& a, const int vb, con
       const unsigned row = base + u * RPW + rs;
 #pragma unroll
       for (int v = 0; v < VW; ++v) {
-        if (two) x[u][v] = fma(al2[v], p2[u][v], x[u][v]);
-        x[u][v] = fma(al[v], p[u][v], x[u][v]);
+        y[u][v] *= ysc[v];
+        if (two) y[u][v] = fma(al2[v], p2[TWO ? u : 0][v], y[u][v]);
+        x[u][v] += fma(al[v], p[u][v], y[u][v]);
       }
       if (a.apply_ode) {
         T sq[1][VW], ex[1][VW], ut[VW];
@@ -1259,6 +1301,21 @@ __device__ __forceinline__ void body_finish(const KArgs<T>& a, const int vb, con
       if ((int)row < r1) st(a.X + (row * ms + c0), x[u]);
     }
   }
+}
+
+template <typename T, int LPR>
+__device__ __forceinline__ void body_finish(const KArgs<T>& a, const int vb, const int vg) {
+  DevCtl* ctl = a.ctl;
+  count_launch(ctl, vb);
+  if (state_finished(a, ctl)) return;
+  const int it = ctl->it;
+  // rows in flight per lane group: fewer where more vectors are read per row
+  // (the registers of 2 resident blocks per SM)
+  constexpr int RU = sizeof(T) == 8 ? kStreamRows / 2 : kStreamRows;
+  if (a.apply_x && (it & 1))
+    body_finish_rows<T, LPR, RU - 1, true>(a, vb, vg, it);
+  else
+    body_finish_rows<T, LPR, RU, false>(a, vb, vg, it);
   if (a.count_step) {
     // the step is counted by the last block to finish, after every block has
     // passed its own state_finished() test (a block that started after an

@@ -13,7 +13,7 @@ namespace segimpl {
 
 constexpr int kMaxCols = 32;       // padded components per vertex row
 constexpr int kBlockThreads = 384;  // threads per block of every row kernel
-constexpr int kMaxDots = 5;         // inner products fused into one pass
+constexpr int kMaxDots = 6;         // inner products fused into one pass
 // Resident blocks per SM the row passes are compiled for (register bound)
 // and launched with; the triangle passes use kTriBlocksPerSM.
 constexpr int kRowBlocksPerSM = 2;
@@ -42,6 +42,8 @@ struct DevCtl {
   double beta[kMaxCols];      // CG direction update factor
   double coup[kMaxCols];      // int u_i^2 sum_{j != i} u_j^2 (normalised state)
   int active[kMaxCols];       // component still iterating in the current solve
+  int carry[kMaxCols];        // the next solve starts from the carried correction y (else from y = 0)
+  double ysc[kMaxCols];       // scale (1 or 0) of the carried correction in the current solve
   int it;                     // CG iterations completed in the current solve
   int cont;                   // loop-continue flag (mirrors the graph conditional)
   int halted;                 // 0 running, 1 stop rule met, 2 error
@@ -76,7 +78,8 @@ struct KArgs {
   const T* valK;
   const T* dinv;   // 1 / diag(A)
   const T* diagA;  // diag(A)
-  T* X;            // state / CG iterate
+  T* X;            // state (the step's right-hand side is M X)
+  T* Y;            // CG iterate x = X + y; kept as the next step's initial correction
   T* Z;            // preconditioned residual z = D^-1 r
   T* P0;           // search directions (ping-pong between CG iterations)
   T* P1;
@@ -97,7 +100,7 @@ struct KArgs {
   long long check_every;
   double energy_tol;
   int force;       // timing/forced launches: energy regardless of the cadence, CG passes regardless of the loop state
-  int apply_x;     // finish pass: apply the lagged CG update of X
+  int apply_x;     // finish pass: x = X + y with the lagged CG updates of y (else x = X)
   int apply_ode;   // finish pass: apply the nodal segregation ODE
   int count_step;  // finish pass: increment the step counter
   int ignore_halt; // run even if the control block is halted (direct calls)

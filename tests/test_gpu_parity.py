@@ -257,4 +257,6 @@ def test_set_get_roundtrip_and_device_pointers(seg):
     assert np.abs(seg.seg_get_u(st2) - U).max() < 1e-15
     seg.seg_step(st, 2)
     seg.seg_step(st2, 2)
-    assert np.abs(seg.seg_get_u(st2) - seg.seg_get_u(st)).max() < 1e-13
+    # st starts its next solve from the CG correction it carries, st2 (just
+    # set) from none: the two agree to the solve's tolerance (rtol 1e-12)
+    assert np.abs(seg.seg_get_u(st2) - seg.seg_get_u(st)).max() < 1e-10
