@@ -83,7 +83,8 @@ struct seg_state {
   int grid_cap = 0;    // the partial-sum buffer holds this many row blocks
   int grid_e_cap = 0;  // ... and this many triangle blocks
   void* X = nullptr;
-  void* Y = nullptr;        // correction of the CG iterate (x = X + y), carried to the next step
+  void* Y = nullptr;        // correction of the CG iterate (x = X + y), starts at a prediction
+  void* H = nullptr;        // the previous step's final correction
   void* Z = nullptr;        // preconditioned residual
   void* P0 = nullptr;       // search directions, ping-pong
   void* P1 = nullptr;
@@ -368,6 +369,7 @@ void fill_args(seg_state* s) {
   a.dinv = (const T*)p->dinv;
   a.X = (T*)s->X;
   a.Y = (T*)s->Y;
+  a.H = (T*)s->H;
   a.diagA = (const T*)p->diagA;
   a.Z = (T*)s->Z;
   a.P0 = (T*)s->P0;
@@ -417,7 +419,7 @@ void drop_graph(seg_state* s) {
 void free_state(seg_state* s) {
   if (!s) return;
   drop_graph(s);
-  void* bufs[] = {s->X, s->Y, s->Z, s->P0, s->P1, s->Q, s->ctl, s->part, s->io, s->ones, s->scale_backup, s->am, s->vp};
+  void* bufs[] = {s->X, s->Y, s->H, s->Z, s->P0, s->P1, s->Q, s->ctl, s->part, s->io, s->ones, s->scale_backup, s->am, s->vp};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (s->hctl) cudaFreeHost(s->hctl);
@@ -756,6 +758,7 @@ seg_status seg_state_create(const seg_problem* p, int32_t m, double eps, seg_ini
     size_t bytes;
   } allocs[] = {{&s->X, vbytes},
                 {&s->Y, vbytes},
+                {&s->H, vbytes},
                 {&s->Z, vbytes},
                 {&s->P0, vbytes},
                 {&s->P1, vbytes},
@@ -843,7 +846,7 @@ seg_status seg_state_bytes(const seg_problem* p, int32_t m, uint64_t* bytes) {
   const uint64_t grid_e = (uint64_t)std::min(kMaxGrid, kTuneWaves * kTriBlocksPerSM * nsm);
   const uint64_t vbytes = n * ms * vsize(p->prec);
   const uint64_t pbytes = partial_bytes((int)ms, (int)grid, (int)grid_e);
-  *bytes = 6 * vbytes + sizeof(DevCtl) + pbytes + std::max<uint64_t>(8, n * m * 8) + 2 * kMaxCols * 8 +
+  *bytes = 7 * vbytes + sizeof(DevCtl) + pbytes + std::max<uint64_t>(8, n * m * 8) + 2 * kMaxCols * 8 +
            std::max<uint64_t>(4, n * 4) + std::max<uint64_t>(4, n);
   return SEG_OK;
 }
@@ -868,7 +871,7 @@ seg_status seg_set_u(seg_state* s, const double* u, int32_t is_device) {
   // by beta = 0: clear them so that values left by a failed run cannot turn
   // into NaN; the solve of the first step starts from x = X (no correction)
   const size_t vbytes = (size_t)s->p->n * s->ms * vsize(s->prec);
-  for (void* b : {s->Y, s->P0, s->P1, s->Q}) SEG_CUDA(cudaMemsetAsync(b, 0, vbytes, s->stream));
+  for (void* b : {s->Y, s->H, s->P0, s->P1, s->Q}) SEG_CUDA(cudaMemsetAsync(b, 0, vbytes, s->stream));
   const int* perm = s->p->perm;
   st = launch_aux(s, s->ks.scatter_in, (long long)s->p->n * s->ms, src, perm);
   if (st != SEG_OK) return st;
@@ -1343,13 +1346,13 @@ seg_status seg_autotune(seg_state* s, int32_t reps, seg_tune_result* out) {
   if (st != SEG_OK) return st;
   // CG iterations per step so far (the weight of the two CG passes)
   const double k = s->hctl->step > 0 ? (double)s->hctl->cg_total / (double)s->hctl->step : 8.0;
-  // save the data the timing launches overwrite: X, Y and the control block;
+  // save the data the timing launches overwrite: X, Y, H and the control block;
   // Z, P and Q are rewritten by every step before they are read (the first
   // CG pass multiplies the old P by beta = 0, so any finite P will do)
   const size_t vbytes = (size_t)s->p->n * s->ms * vsize(s->prec);
-  void* saved_x = nullptr;  // X, then Y
+  void* saved_x = nullptr;  // X, Y, H
   DevCtl* saved_ctl = nullptr;
-  cudaError_t ce = cudaMalloc(&saved_x, 2 * vbytes);
+  cudaError_t ce = cudaMalloc(&saved_x, 3 * vbytes);
   if (ce == cudaSuccess) ce = cudaMalloc((void**)&saved_ctl, sizeof(DevCtl));
   if (ce != cudaSuccess) {
     cudaFree(saved_x);
@@ -1362,6 +1365,8 @@ seg_status seg_autotune(seg_state* s, int32_t reps, seg_tune_result* out) {
   ce = cudaMemcpyAsync(saved_x, s->X, vbytes, cudaMemcpyDeviceToDevice, s->stream);
   if (ce == cudaSuccess)
     ce = cudaMemcpyAsync((char*)saved_x + vbytes, s->Y, vbytes, cudaMemcpyDeviceToDevice, s->stream);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync((char*)saved_x + 2 * vbytes, s->H, vbytes, cudaMemcpyDeviceToDevice, s->stream);
   if (ce == cudaSuccess) ce = cudaMemcpyAsync(saved_ctl, s->ctl, sizeof(DevCtl), cudaMemcpyDeviceToDevice, s->stream);
   if (ce != cudaSuccess) st = fail(SEG_ERR_CUDA, std::string("save: ") + cudaGetErrorString(ce));
   // candidate row grids: 1 .. kRowBlocksPerSM blocks per SM (one wave), and
@@ -1429,6 +1434,8 @@ seg_status seg_autotune(seg_state* s, int32_t reps, seg_tune_result* out) {
   ce = cudaMemcpyAsync(s->X, saved_x, vbytes, cudaMemcpyDeviceToDevice, s->stream);
   if (ce == cudaSuccess)
     ce = cudaMemcpyAsync(s->Y, (char*)saved_x + vbytes, vbytes, cudaMemcpyDeviceToDevice, s->stream);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync(s->H, (char*)saved_x + 2 * vbytes, vbytes, cudaMemcpyDeviceToDevice, s->stream);
   if (ce == cudaSuccess) ce = cudaMemcpyAsync(s->ctl, saved_ctl, sizeof(DevCtl), cudaMemcpyDeviceToDevice, s->stream);
   for (void* b : {s->Z, s->P0, s->P1, s->Q})
     if (ce == cudaSuccess) ce = cudaMemsetAsync(b, 0, vbytes, s->stream);

@@ -132,6 +132,8 @@ struct AccOf<double> {
 
 __device__ __forceinline__ float2 to_part(const AccF& a) { return make_float2(a.hi, a.lo); }
 __device__ __forceinline__ double to_part(const AccD& a) { return a.v; }
+__device__ __forceinline__ float2 plain_part(float v) { return make_float2(v, 0.f); }
+__device__ __forceinline__ double plain_part(double v) { return v; }
 __device__ __forceinline__ void add_part(AccF& a, float2 p) { a.add_pair(p.x, p.y); }
 __device__ __forceinline__ void add_part(AccD& a, double p) { a.v += p; }
 __device__ __forceinline__ void shfl_add(AccF& a, int off) {
@@ -202,35 +204,50 @@ __device__ __forceinline__ bool reduce_blocks(const Part* part, unsigned int* co
   return true;
 }
 
-// Block + grid reduction of ND per-component sums.  Every block writes its
-// partial; the grid's partials are summed by reduce_blocks, which leaves the
-// totals in tot[ND][kMaxCols] of the last block.  Returns true in the last
+// Block + grid reduction of ND per-component sums, plus NP more sums kept in
+// plain T (sums that only set a tolerance or a choice; fewer registers are
+// live at the end of a pass than with float-float pairs): within the warp
+// they are added in T, from the block partials on like the others.  Every
+// block writes its partial; the grid's partials are summed by
+// reduce_blocks, which leaves the totals in tot[ND + NP][kMaxCols] of the
+// last block (the NP plain sums after the others).  Returns true in the last
 // block only.  Must be reached by every block of the grid.
-template <typename T, int LPR, int ND>
-__device__ __forceinline__ bool grid_reduce(typename AccOf<T>::type (&acc)[ND][VecW<T>::W],
-                                            const KArgs<T>& a, int slot, double (*tot)[kMaxCols], int vb, int vg) {
+template <typename T, int LPR, int ND, int NP>
+__device__ __forceinline__ bool grid_reduce_plain(typename AccOf<T>::type (&acc)[ND][VecW<T>::W],
+                                                  T (&pl)[NP > 0 ? NP : 1][VecW<T>::W], const KArgs<T>& a, int slot,
+                                                  double (*tot)[kMaxCols], int vb, int vg) {
   typedef typename AccOf<T>::type Acc;
   typedef typename AccOf<T>::part Part;
   constexpr int VW = VecW<T>::W;
   constexpr int NW = kBlockThreads / 32;
+  constexpr int NT = ND + NP;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, cg = lane % LPR;
 #pragma unroll
-  for (int off = LPR; off < 32; off <<= 1)
+  for (int off = LPR; off < 32; off <<= 1) {
 #pragma unroll
     for (int d = 0; d < ND; ++d)
 #pragma unroll
       for (int v = 0; v < VW; ++v) shfl_add(acc[d][v], off);
-  __shared__ Part red[ND][NW][kMaxCols];
+#pragma unroll
+    for (int d = 0; d < NP; ++d)
+#pragma unroll
+      for (int v = 0; v < VW; ++v) pl[d][v] += __shfl_xor_sync(0xffffffffu, pl[d][v], off);
+  }
+  __shared__ Part red[NT][NW][kMaxCols];
   if (lane < LPR) {
 #pragma unroll
     for (int d = 0; d < ND; ++d)
 #pragma unroll
       for (int v = 0; v < VW; ++v) red[d][warp][cg * VW + v] = to_part(acc[d][v]);
+#pragma unroll
+    for (int d = 0; d < NP; ++d)
+#pragma unroll
+      for (int v = 0; v < VW; ++v) red[ND + d][warp][cg * VW + v] = plain_part(pl[d][v]);
   }
   __syncthreads();
   const int G = vg;
   Part* part = reinterpret_cast<Part*>(a.part);
-  for (int t = threadIdx.x; t < ND * a.ms; t += kBlockThreads) {
+  for (int t = threadIdx.x; t < NT * a.ms; t += kBlockThreads) {
     const int d = t / a.ms, c = t % a.ms;
     Acc s;
     s.zero();
@@ -238,8 +255,16 @@ __device__ __forceinline__ bool grid_reduce(typename AccOf<T>::type (&acc)[ND][V
     part[(size_t)(d * a.ms + c) * G + vb] = to_part(s);
   }
   const int ms = a.ms;
-  return reduce_blocks<Acc>(part, &a.ctl->counters[slot], ND * ms, vb, G,
+  return reduce_blocks<Acc>(part, &a.ctl->counters[slot], NT * ms, vb, G,
                             [&](int p, double v) { tot[p / ms][p % ms] = v; });
+}
+
+// grid_reduce_plain without plain sums.
+template <typename T, int LPR, int ND>
+__device__ __forceinline__ bool grid_reduce(typename AccOf<T>::type (&acc)[ND][VecW<T>::W],
+                                            const KArgs<T>& a, int slot, double (*tot)[kMaxCols], int vb, int vg) {
+  T none[1][VecW<T>::W];
+  return grid_reduce_plain<T, LPR, ND, 0>(acc, none, a, slot, tot, vb, vg);
 }
 
 // Exclusive sums over the components of one vertex row held by the LPR lanes
@@ -623,16 +648,16 @@ __device__ __forceinline__ void body_start(const KArgs<T>& a, const int vb, cons
   __shared__ __align__(8) unsigned long long bars[NW][kPipeStages];
   const T tau = (T)a.tau;
   const unsigned ms = a.ms;
-  Acc acc[6][VW];
+  Acc acc[3][VW];  // ||X||_M^2, X^T K X, r0.z0
 #pragma unroll
-  for (int d = 0; d < 6; ++d)
+  for (int d = 0; d < 3; ++d)
 #pragma unroll
     for (int v = 0; v < VW; ++v) acc[d][v].zero();
-  T bb[VW], rra[VW], rrb[VW];
+  T pl[3][VW];  // ||M X||^2, ||-tau K X||^2, ||-tau K X - A Y||^2
   unsigned om = 0;  // bit v: this lane's component c0 + v starts from the carried correction
 #pragma unroll
   for (int v = 0; v < VW; ++v) {
-    bb[v] = rra[v] = rrb[v] = T(0);
+    pl[0][v] = pl[1][v] = pl[2][v] = T(0);
     if (ctl->carry[c0 + v]) om |= 1u << v;
   }
   typename Stage::Src src;
@@ -684,8 +709,8 @@ __device__ __forceinline__ void body_start(const KArgs<T>& a, const int vb, cons
 #pragma unroll
         for (int v = 0; v < VW; ++v) {
           const T ra = -tau * kx[v], rb = ra - ay[v];
-          rra[v] = fma(ra, ra, rra[v]);
-          rrb[v] = fma(rb, rb, rrb[v]);
+          pl[1][v] = fma(ra, ra, pl[1][v]);
+          pl[2][v] = fma(rb, rb, pl[2][v]);
           r[v] = (om >> v) & 1u ? rb : ra;
           z[v] = di * r[v];
         }
@@ -693,25 +718,19 @@ __device__ __forceinline__ void body_start(const KArgs<T>& a, const int vb, cons
 #pragma unroll
         for (int v = 0; v < VW; ++v) {
           acc[0][v].add_prod(x[v], mx[v]);
-          acc[2][v].add_prod(x[v], kx[v]);
-          acc[3][v].add_prod(r[v], z[v]);
-          bb[v] = fma(mx[v], mx[v], bb[v]);
+          acc[1][v].add_prod(x[v], kx[v]);
+          acc[2][v].add_prod(r[v], z[v]);
+          pl[0][v] = fma(mx[v], mx[v], pl[0][v]);
         }
       });
   if (__syncthreads_or(!ok) && threadIdx.x == 0) report_timeout(ctl);
-#pragma unroll
-  for (int v = 0; v < VW; ++v) {
-    acc[1][v].add_val(bb[v]);
-    acc[4][v].add_val(rra[v]);
-    acc[5][v].add_val(rrb[v]);
-  }
   __shared__ double tot[6][kMaxCols];
-  if (!grid_reduce<T, LPR, 6>(acc, a, kCtrStart, tot, vb, vg)) return;
+  if (!grid_reduce_plain<T, LPR, 3, 3>(acc, pl, a, kCtrStart, tot, vb, vg)) return;
   int act = 0, bad = 0;
   const int c = threadIdx.x;
   if (c < a.ms) {
     const bool used = ctl->carry[c] != 0;
-    const double n2 = tot[0][c], bbt = tot[1][c], ukt = tot[2][c], rz = tot[3][c];
+    const double n2 = tot[0][c], ukt = tot[1][c], rz = tot[2][c], bbt = tot[3][c];
     const double rrt = used ? tot[5][c] : tot[4][c];
     const bool real = c < a.m;
     ctl->ysc[c] = used ? 1.0 : 0.0;
@@ -1231,14 +1250,14 @@ __device__ __forceinline__ void body_cg_b(const KArgs<T>& a, const int vb, const
   }
 }
 
-// The solve's result x = X + y with the CG updates of y not yet applied
+// The solve's result x = X + y_k with the CG updates of y not yet applied
 // (lagged from the last iterations; apply_x, else x = X), then the exact
 // solution of the nodal ODE of step 2 (Jacobi form):
 //   u~ = x * inv_n,  u^_i = u~_i exp(-(2 tau/eps^2) sum_{j != i} u~_j^2)  -> X.
-// Y keeps the correction without those last updates (or an older one if the
-// solve ended before its second iteration): the next step may start its
-// solve from it (any initial guess gives the same solution to the solve's
-// tolerance; the last updates are the smallest).
+// With apply_x the next solve's initial correction is predicted by linear
+// extrapolation of the last two, Y = 2 y_k - y_{k-1} (H holds y_{k-1} and
+// then y_k); any initial guess gives the same solution to the solve's
+// tolerance.
 // The solution updates CG pass A has not applied yet: alpha_k p_k, and
 // alpha_{k-1} p_{k-1} before it (TWO) when the iteration count k is odd.
 template <typename T, int LPR, int RU, bool TWO>
@@ -1260,19 +1279,20 @@ __device__ __forceinline__ void body_finish_rows(const KArgs<T>& a, const int vb
   }
   const T mcoef = -(T)a.coef;
   for (int base = r0 + warp * RPW * RU; base < r1; base += NW * RPW * RU) {
-    T x[RU][VW], y[RU][VW], p[RU][VW], p2[TWO ? RU : 1][VW];
+    T x[RU][VW], y[RU][VW], h[RU][VW], p[RU][VW], p2[TWO ? RU : 1][VW];
 #pragma unroll
     for (int u = 0; u < RU; ++u) {
       const unsigned row = base + u * RPW + rs;
 #pragma unroll
       for (int v = 0; v < VW; ++v) {
-        x[u][v] = y[u][v] = p[u][v] = T(0);
+        x[u][v] = y[u][v] = h[u][v] = p[u][v] = T(0);
         if (two) p2[u][v] = T(0);
       }
       if ((int)row < r1) {
         ld(x[u], a.X + (row * ms + c0));
         if (a.apply_x) {
-          ld_ro(y[u], a.Y + (row * ms + c0));
+          ld(y[u], a.Y + (row * ms + c0));
+          ld(h[u], a.H + (row * ms + c0));
           ld_ro(p[u], P + (row * ms + c0));
         }
         if (two) ld_ro(p2[TWO ? u : 0], P2 + (row * ms + c0));
@@ -1285,7 +1305,16 @@ __device__ __forceinline__ void body_finish_rows(const KArgs<T>& a, const int vb
       for (int v = 0; v < VW; ++v) {
         y[u][v] *= ysc[v];
         if (two) y[u][v] = fma(al2[v], p2[TWO ? u : 0][v], y[u][v]);
-        x[u][v] += fma(al[v], p[u][v], y[u][v]);
+        y[u][v] = fma(al[v], p[u][v], y[u][v]);  // the solve's correction y_k
+        x[u][v] += y[u][v];
+      }
+      if (a.apply_x && (int)row < r1) {
+        // the next solve's predicted correction 2 y_k - y_{k-1}; y_k kept
+        T g[VW];
+#pragma unroll
+        for (int v = 0; v < VW; ++v) g[v] = fma(T(2), y[u][v], -h[u][v]);
+        st(a.Y + (row * ms + c0), g);
+        st(a.H + (row * ms + c0), y[u]);
       }
       if (a.apply_ode) {
         T sq[1][VW], ex[1][VW], ut[VW];
@@ -1311,7 +1340,7 @@ __device__ __forceinline__ void body_finish(const KArgs<T>& a, const int vb, con
   const int it = ctl->it;
   // rows in flight per lane group: fewer where more vectors are read per row
   // (the registers of 2 resident blocks per SM)
-  constexpr int RU = sizeof(T) == 8 ? kStreamRows / 2 : kStreamRows;
+  constexpr int RU = sizeof(T) == 8 ? kStreamRows / 2 : kStreamRows - 1;
   if (a.apply_x && (it & 1))
     body_finish_rows<T, LPR, RU - 1, true>(a, vb, vg, it);
   else

@@ -79,7 +79,8 @@ struct KArgs {
   const T* dinv;   // 1 / diag(A)
   const T* diagA;  // diag(A)
   T* X;            // state (the step's right-hand side is M X)
-  T* Y;            // CG iterate x = X + y; kept as the next step's initial correction
+  T* Y;            // CG iterate x = X + y; y starts at a prediction of the step's correction
+  T* H;            // the correction y of the previous step's solve
   T* Z;            // preconditioned residual z = D^-1 r
   T* P0;           // search directions (ping-pong between CG iterations)
   T* P1;
