@@ -103,6 +103,13 @@ typedef struct {
   int64_t kernel_launches;  /* hot-path kernel launches on this state (start, CG passes A and B
                                including those that returned at once after the loop ended,
                                finish, energy passes) */
+  int32_t graph_peel;       /* CG iterations the step graph (launch_mode 0) runs as plain nodes
+                               before its loop node: the autotuner sets it to the latest step's
+                               count; reviews after 3 or more steps (at seg_sync / seg_step, and
+                               every 16 steps inside a long seg_step) set it to their mean per
+                               step rounded up if that is larger, or smaller by 2 or more (the
+                               graph is then rebuilt for the next step) */
+  int32_t reserved;         /* 0 */
 } seg_stats;
 
 /* ------------------------------------------------------------------ meshes */
@@ -219,7 +226,10 @@ seg_status seg_get_u(seg_state* s, double* u, int32_t is_device);
 seg_status seg_step(seg_state* s, int64_t nsteps, int64_t* steps_done);
 
 /* As seg_step but only enqueues the work on the state's stream and returns;
- * seg_sync() waits and reports the same status and step count. */
+ * seg_sync() waits and reports the same status and step count.  (seg_step
+ * itself enqueues a run of 64 or more graph-mode steps in chunks of 16, at
+ * most two chunks ahead of the device, and adapts the step graph between
+ * chunks; seg_step_async enqueues everything at once.) */
 seg_status seg_step_async(seg_state* s, int64_t nsteps);
 seg_status seg_sync(seg_state* s, int64_t* steps_done);
 
@@ -412,7 +422,8 @@ typedef struct {
  * the CG iterations of the state's latest step (1 .. 16; unchanged before
  * the first step) as plain graph nodes ahead of the
  * conditional loop node (passes after convergence return at once; an
- * evaluation of the loop condition costs more).  Later steps give
+ * evaluation of the loop condition costs more); later syncs review the peel
+ * (seg_stats.graph_peel).  Later steps give
  * the same results as without tuning up to the summation order of the
  * per-block partial inner products.  A batch built from the state earlier
  * keeps the geometry it was built with.  Needs device memory for three

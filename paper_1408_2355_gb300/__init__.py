@@ -85,6 +85,8 @@ class seg_stats(C.Structure):
         ("last_check_total", C.c_double),
         ("checks", C.c_int64),
         ("kernel_launches", C.c_int64),
+        ("graph_peel", C.c_int32),
+        ("reserved", C.c_int32),
     ]
 
 

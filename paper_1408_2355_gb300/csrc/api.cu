@@ -105,6 +105,13 @@ struct seg_state {
   cudaGraphConditionalHandle cond = 0;
   bool pending = true;      // inv_n must be recomputed before use
   int cg_peel = kCgPeelDefault;  // CG iterations of the step graph before its WHILE node
+  long long peel_step = 0;       // step and CG iteration counters when the peel was last reviewed
+  long long peel_it = 0;
+  // step graphs replaced while launches of them may still be in flight
+  // (destroyed once the stream has drained)
+  std::vector<std::pair<cudaGraph_t, cudaGraphExec_t>> retired;
+  long long* hsnap = nullptr;   // pinned: counters after a chunk of seg_step, 2 slots x (step, cg_total)
+  cudaEvent_t snap_ev[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -409,6 +416,14 @@ seg_status upload_ints(const std::vector<I>& src, I** dst) {
   return SEG_OK;
 }
 
+void drop_retired(seg_state* s) {
+  for (auto& r : s->retired) {
+    if (r.second) cudaGraphExecDestroy(r.second);
+    if (r.first) cudaGraphDestroy(r.first);
+  }
+  s->retired.clear();
+}
+
 void drop_graph(seg_state* s) {
   if (s->exec) cudaGraphExecDestroy(s->exec);
   if (s->graph) cudaGraphDestroy(s->graph);
@@ -416,13 +431,25 @@ void drop_graph(seg_state* s) {
   s->graph = nullptr;
 }
 
+// Set the graph aside (launches of it may be in flight); the next graph-mode
+// step builds a new one.
+void retire_graph(seg_state* s) {
+  if (s->exec || s->graph) s->retired.emplace_back(s->graph, s->exec);
+  s->exec = nullptr;
+  s->graph = nullptr;
+}
+
 void free_state(seg_state* s) {
   if (!s) return;
+  drop_retired(s);
   drop_graph(s);
   void* bufs[] = {s->X, s->Y, s->H, s->Z, s->P0, s->P1, s->Q, s->ctl, s->part, s->io, s->ones, s->scale_backup, s->am, s->vp};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (s->hctl) cudaFreeHost(s->hctl);
+  if (s->hsnap) cudaFreeHost(s->hsnap);
+  for (cudaEvent_t e : s->snap_ev)
+    if (e) cudaEventDestroy(e);
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
   delete s;
 }
@@ -784,9 +811,17 @@ seg_status seg_state_create(const seg_problem* p, int32_t m, double eps, seg_ini
     }
   }
   ce = cudaMallocHost((void**)&s->hctl, sizeof(DevCtl));
+  if (ce == cudaSuccess) ce = cudaMallocHost((void**)&s->hsnap, 4 * sizeof(long long));
   if (ce != cudaSuccess) {
     free_state(s);
     return fail(SEG_ERR_NO_MEMORY, std::string("cudaMallocHost: ") + cudaGetErrorString(ce));
+  }
+  for (cudaEvent_t& e : s->snap_ev) {
+    ce = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+    if (ce != cudaSuccess) {
+      free_state(s);
+      return fail(SEG_ERR_CUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(ce));
+    }
   }
   std::memset(s->hctl, 0, sizeof(DevCtl));
   {
@@ -898,15 +933,21 @@ seg_status seg_get_u(seg_state* s, double* u, int32_t is_device) {
 
 // ------------------------------------------------------------------- steps
 
-seg_status seg_step_async(seg_state* s, int64_t nsteps) {
-  if (!s) return fail(SEG_ERR_ARG, "state is NULL");
-  if (nsteps < 0) return fail(SEG_ERR_ARG, "nsteps must be >= 0");
+}  // extern "C"
+
+namespace {
+
+// Start of a run of steps: remember the step count in stream order, and
+// clear the sticky status bits of earlier calls; halted states stay halted.
+seg_status begin_steps(seg_state* s) {
   SEG_CUDA(cudaSetDevice(s->p->device));
-  // remember the step count in stream order, and clear the sticky status
-  // bits of earlier calls; halted states stay halted
   SEG_CUDA(cudaMemcpyAsync(&s->ctl->step_mark, &s->ctl->step, sizeof(long long), cudaMemcpyDeviceToDevice,
                            s->stream));
   SEG_CUDA(cudaMemsetAsync(&s->ctl->status, 0, sizeof(int), s->stream));
+  return SEG_OK;
+}
+
+seg_status enqueue_steps(seg_state* s, int64_t nsteps) {
   if (s->launch_mode == 0) {
     if (!s->exec) {
       const seg_status gs = s->prec == SEG_MIXED_FP32 ? build_graph_t<float>(s) : build_graph_t<double>(s);
@@ -926,17 +967,89 @@ seg_status seg_step_async(seg_state* s, int64_t nsteps) {
   return SEG_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+seg_status seg_step_async(seg_state* s, int64_t nsteps) {
+  if (!s) return fail(SEG_ERR_ARG, "state is NULL");
+  if (nsteps < 0) return fail(SEG_ERR_ARG, "nsteps must be >= 0");
+  seg_status st = begin_steps(s);
+  if (st != SEG_OK) return st;
+  return enqueue_steps(s, nsteps);
+}
+
+// Review the step graph's peel (CG iterations placed before its WHILE node)
+// against the iterations per step since the last review: a pass after the
+// solve has converged returns at once, an evaluation of the loop condition
+// costs more, so the peel follows the mean rounded up.  It grows at once and
+// shrinks only by two or more (no rebuild for a mean that hovers at an
+// integer).  The graph is rebuilt at the next graph-mode step.  Called with
+// the stream idle.
+static void review_peel(seg_state* s, long long step, long long cg_total) {
+  const long long ds = step - s->peel_step, di = cg_total - s->peel_it;
+  if (ds < 0 || di < 0) {  // counters were reset (seg_set_u)
+    s->peel_step = step;
+    s->peel_it = cg_total;
+    return;
+  }
+  if (ds < 3 || s->launch_mode != 0) return;
+  const int target = std::min(kCgPeelMax, std::max(1, (int)std::ceil((double)di / (double)ds - 0.1)));
+  if (target > s->cg_peel || target <= s->cg_peel - 2) {
+    s->cg_peel = target;
+    retire_graph(s);
+  }
+  s->peel_step = step;
+  s->peel_it = cg_total;
+}
+
 seg_status seg_sync(seg_state* s, int64_t* steps_done) {
   if (!s) return fail(SEG_ERR_ARG, "state is NULL");
   seg_status st = sync_ctl(s);
   if (st != SEG_OK) return st;
+  drop_retired(s);
+  review_peel(s, s->hctl->step, s->hctl->cg_total);
   if (steps_done) *steps_done = s->hctl->step - s->hctl->step_mark;
   return status_from_ctl(*s->hctl);
 }
 
+// Steps per chunk of a long synchronous run in graph mode.  The run is
+// enqueued chunk by chunk, at most two chunks ahead of the device: after each
+// chunk the step and CG iteration counters are copied to pinned memory, and
+// once the chunk before has completed its counters review the graph's peel
+// (a new graph is built for the next chunk if it changes; the device keeps
+// working on the chunk in flight meanwhile).
+constexpr int64_t kReviewChunk = 16;
+
 seg_status seg_step(seg_state* s, int64_t nsteps, int64_t* steps_done) {
-  seg_status st = seg_step_async(s, nsteps);
+  if (!s) return fail(SEG_ERR_ARG, "state is NULL");
+  if (nsteps < 0) return fail(SEG_ERR_ARG, "nsteps must be >= 0");
+  seg_status st = begin_steps(s);
   if (st != SEG_OK) return st;
+  if (s->launch_mode != 0 || nsteps < 4 * kReviewChunk) {
+    st = enqueue_steps(s, nsteps);
+    if (st != SEG_OK) return st;
+    return seg_sync(s, steps_done);
+  }
+  int slot = 0;
+  bool have_prev = false;
+  for (int64_t left = nsteps; left > 0;) {
+    const int64_t n = std::min(left, kReviewChunk);
+    st = enqueue_steps(s, n);
+    if (st != SEG_OK) return st;
+    left -= n;
+    long long* snap = s->hsnap + 2 * slot;
+    SEG_CUDA(cudaMemcpyAsync(snap, &s->ctl->step, sizeof(long long), cudaMemcpyDeviceToHost, s->stream));
+    SEG_CUDA(cudaMemcpyAsync(snap + 1, &s->ctl->cg_total, sizeof(long long), cudaMemcpyDeviceToHost, s->stream));
+    SEG_CUDA(cudaEventRecord(s->snap_ev[slot], s->stream));
+    if (have_prev && left > 0) {
+      const int prev = slot ^ 1;
+      SEG_CUDA(cudaEventSynchronize(s->snap_ev[prev]));
+      review_peel(s, s->hsnap[2 * prev], s->hsnap[2 * prev + 1]);
+    }
+    have_prev = true;
+    slot ^= 1;
+  }
   return seg_sync(s, steps_done);
 }
 
@@ -1321,6 +1434,8 @@ seg_status seg_get_stats(seg_state* s, seg_stats* out) {
   out->last_check_total = c.e_prev;
   out->checks = c.checks;
   out->kernel_launches = (int64_t)c.launches;
+  out->graph_peel = s->cg_peel;
+  out->reserved = 0;
   return SEG_OK;
 }
 
@@ -1458,6 +1573,8 @@ seg_status seg_autotune(seg_state* s, int32_t reps, seg_tune_result* out) {
   // count of the latest step (early steps from random data need more)
   if (st == SEG_OK && s->hctl->step > 0) s->cg_peel = std::min(kCgPeelMax, std::max(1, s->hctl->cg_last));
   out->cg_peel = s->cg_peel;
+  s->peel_step = s->hctl->step;
+  s->peel_it = s->hctl->cg_total;
   // the step graph has the geometry baked in: drop it, the next graph-mode
   // step builds it again
   drop_graph(s);

@@ -52,7 +52,7 @@ def test_struct_layouts_match_header(seg):
     assert C.sizeof(seg.seg_params) == 48
     assert C.sizeof(seg.seg_server_params) == 16
     assert C.sizeof(seg.seg_request_info) == 64
-    assert C.sizeof(seg.seg_stats) == 56
+    assert C.sizeof(seg.seg_stats) == 64
     assert C.sizeof(seg.seg_tune_result) == 152
     assert C.sizeof(seg.seg_surface) == 32
 

@@ -27,7 +27,10 @@ def test_autotune_restores_and_agrees(seg, prec, tol):
     stats0 = seg.seg_get_stats(tuned)
     r = seg.seg_autotune(tuned, 5)
     assert np.array_equal(seg.seg_get_u(tuned), before)
-    assert seg.seg_get_stats(tuned) == stats0
+    stats1 = seg.seg_get_stats(tuned)
+    assert stats1.pop("graph_peel") == r["cg_peel"]
+    stats0.pop("graph_peel")
+    assert stats1 == stats0
     grids = [g for g, _ in r["candidates"]]
     assert r["grid_blocks"] in grids and len(grids) >= 2
     assert r["ms_model"] <= min(ms for _, ms in r["candidates"]) * (1 + 1e-12)

@@ -28,9 +28,10 @@ def test_kernel_launch_counter(seg, mode):
         s1 = seg.seg_get_stats(st)
         k = s1["cg_last"]
         assert k == s1["cg_iterations"] - s0["cg_iterations"] and k >= 1
-        # graph: 4 iterations as plain nodes (the untuned default), then the
-        # loop node with two iterations per evaluation
-        pairs = k if mode == 1 else 4 + (0 if k <= 4 else 2 * ((k - 4 + 1) // 2))
+        # graph: the peel's iterations as plain nodes, then the loop node
+        # with two iterations per evaluation
+        pl = s0["graph_peel"]
+        pairs = k if mode == 1 else pl + (0 if k <= pl else 2 * ((k - pl + 1) // 2))
         assert s1["kernel_launches"] - s0["kernel_launches"] == 3 + 2 * pairs
 
 
@@ -47,3 +48,21 @@ def test_step_limit_with_more_blocks_than_resident(seg):
     assert seg.seg_step(b, 3) == 3
     ua, ub = seg.seg_get_u(a), seg.seg_get_u(b)
     assert np.abs(ua - ub).max() <= 1e-12 * np.abs(ub).max()
+
+
+def test_long_step_reviews_the_graph_without_changing_results(seg):
+    """A long seg_step adapts the step graph's peel between chunks of steps;
+    the arithmetic is the same as one graph for the whole run (bitwise)."""
+    import numpy as np
+
+    xyz, tri = w.icosphere(5)
+    a = make_state(seg, xyz, tri, 2e-5, 6, 2e-3, 1, 7, check_every=-1)
+    b = make_state(seg, xyz, tri, 2e-5, 6, 2e-3, 1, 7, check_every=-1)
+    assert seg.seg_get_stats(a)["graph_peel"] == 4  # the untuned default
+    assert seg.seg_step(a, 160) == 160
+    seg.seg_step_async(b, 160)
+    assert seg.seg_sync(b) == 160
+    assert np.array_equal(seg.seg_get_u(a), seg.seg_get_u(b))
+    sa, sb = seg.seg_get_stats(a), seg.seg_get_stats(b)
+    assert sa["cg_iterations"] == sb["cg_iterations"]
+    assert 1 <= sa["graph_peel"] <= max(4, sa["cg_max"])
