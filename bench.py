@@ -229,8 +229,9 @@ def kernel_bytes(n, ntri, m_pad, s, W=8):
       k_cg_a   even iterations: read Z, p_old, q_old; write p_new, q; columns + A values;
                odd iterations also read Y and p_{j-2} and write Y (two solution updates)
       k_cg_b   read Z, q; write Z; diagonal of A and its inverse
-      k_finish read X, Y, H, p (and p of the iteration before after an odd count);
-               write X, the next step's predicted correction Y and this step's correction H
+      k_finish read X, Y, the last two corrections, p (and p of the iteration before after
+               an odd count); write X, the next step's predicted correction Y and this
+               step's correction (over the older of the two)
       k_energy_check / k_energy  read X, triangle corners (3 int32) and areas
     """
     V = n * m_pad * s
@@ -240,8 +241,8 @@ def kernel_bytes(n, ntri, m_pad, s, W=8):
         "k_cg_a_even": 5 * V + ell + n * W * s,
         "k_cg_a_odd": 8 * V + ell + n * W * s,
         "k_cg_b": 3 * V + 2 * n * s,
-        "k_finish_even": 7 * V,
-        "k_finish_odd": 8 * V,
+        "k_finish_even": 8 * V,
+        "k_finish_odd": 9 * V,
         "k_energy_check": V + ntri * (12 + s),
         "k_energy": V + ntri * (12 + s),
     }
@@ -344,7 +345,7 @@ def run_ours(a, rank, ws, local):
             "precision": "mixed: f32 vectors/matrices/exp, inner products and CG scalars to f64 accuracy",
             "cg_rtol": 1e-7,
             "energy_every_step": True,
-            "l2": "inputs larger than L2: 7 state vectors x 42 MB + 84 MB of padded-ELL matrices > 129 MB L2",
+            "l2": "inputs larger than L2: 8 state vectors x 42 MB + 84 MB of padded-ELL matrices > 129 MB L2",
             "grid_blocks": li["grid_blocks"],
             "autotune": tunes.get(seg.SEG_MIXED_FP32),
             "launch_mode": a.launch_mode,

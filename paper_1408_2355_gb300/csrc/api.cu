@@ -84,7 +84,8 @@ struct seg_state {
   int grid_e_cap = 0;  // ... and this many triangle blocks
   void* X = nullptr;
   void* Y = nullptr;        // correction of the CG iterate (x = X + y), starts at a prediction
-  void* H = nullptr;        // the previous step's final correction
+  void* H0 = nullptr;       // the last two steps' final corrections (step k's in H[k % 2])
+  void* H1 = nullptr;
   void* Z = nullptr;        // preconditioned residual
   void* P0 = nullptr;       // search directions, ping-pong
   void* P1 = nullptr;
@@ -376,7 +377,8 @@ void fill_args(seg_state* s) {
   a.dinv = (const T*)p->dinv;
   a.X = (T*)s->X;
   a.Y = (T*)s->Y;
-  a.H = (T*)s->H;
+  a.H0 = (T*)s->H0;
+  a.H1 = (T*)s->H1;
   a.diagA = (const T*)p->diagA;
   a.Z = (T*)s->Z;
   a.P0 = (T*)s->P0;
@@ -443,7 +445,7 @@ void free_state(seg_state* s) {
   if (!s) return;
   drop_retired(s);
   drop_graph(s);
-  void* bufs[] = {s->X, s->Y, s->H, s->Z, s->P0, s->P1, s->Q, s->ctl, s->part, s->io, s->ones, s->scale_backup, s->am, s->vp};
+  void* bufs[] = {s->X, s->Y, s->H0, s->H1, s->Z, s->P0, s->P1, s->Q, s->ctl, s->part, s->io, s->ones, s->scale_backup, s->am, s->vp};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (s->hctl) cudaFreeHost(s->hctl);
@@ -785,7 +787,8 @@ seg_status seg_state_create(const seg_problem* p, int32_t m, double eps, seg_ini
     size_t bytes;
   } allocs[] = {{&s->X, vbytes},
                 {&s->Y, vbytes},
-                {&s->H, vbytes},
+                {&s->H0, vbytes},
+                {&s->H1, vbytes},
                 {&s->Z, vbytes},
                 {&s->P0, vbytes},
                 {&s->P1, vbytes},
@@ -881,7 +884,7 @@ seg_status seg_state_bytes(const seg_problem* p, int32_t m, uint64_t* bytes) {
   const uint64_t grid_e = (uint64_t)std::min(kMaxGrid, kTuneWaves * kTriBlocksPerSM * nsm);
   const uint64_t vbytes = n * ms * vsize(p->prec);
   const uint64_t pbytes = partial_bytes((int)ms, (int)grid, (int)grid_e);
-  *bytes = 7 * vbytes + sizeof(DevCtl) + pbytes + std::max<uint64_t>(8, n * m * 8) + 2 * kMaxCols * 8 +
+  *bytes = 8 * vbytes + sizeof(DevCtl) + pbytes + std::max<uint64_t>(8, n * m * 8) + 2 * kMaxCols * 8 +
            std::max<uint64_t>(4, n * 4) + std::max<uint64_t>(4, n);
   return SEG_OK;
 }
@@ -906,7 +909,7 @@ seg_status seg_set_u(seg_state* s, const double* u, int32_t is_device) {
   // by beta = 0: clear them so that values left by a failed run cannot turn
   // into NaN; the solve of the first step starts from x = X (no correction)
   const size_t vbytes = (size_t)s->p->n * s->ms * vsize(s->prec);
-  for (void* b : {s->Y, s->H, s->P0, s->P1, s->Q}) SEG_CUDA(cudaMemsetAsync(b, 0, vbytes, s->stream));
+  for (void* b : {s->Y, s->H0, s->H1, s->P0, s->P1, s->Q}) SEG_CUDA(cudaMemsetAsync(b, 0, vbytes, s->stream));
   const int* perm = s->p->perm;
   st = launch_aux(s, s->ks.scatter_in, (long long)s->p->n * s->ms, src, perm);
   if (st != SEG_OK) return st;
@@ -1461,13 +1464,13 @@ seg_status seg_autotune(seg_state* s, int32_t reps, seg_tune_result* out) {
   if (st != SEG_OK) return st;
   // CG iterations per step so far (the weight of the two CG passes)
   const double k = s->hctl->step > 0 ? (double)s->hctl->cg_total / (double)s->hctl->step : 8.0;
-  // save the data the timing launches overwrite: X, Y, H and the control block;
+  // save the data the timing launches overwrite: X, Y, H0, H1 and the control block;
   // Z, P and Q are rewritten by every step before they are read (the first
   // CG pass multiplies the old P by beta = 0, so any finite P will do)
   const size_t vbytes = (size_t)s->p->n * s->ms * vsize(s->prec);
-  void* saved_x = nullptr;  // X, Y, H
+  void* saved_x = nullptr;  // X, Y, H0, H1
   DevCtl* saved_ctl = nullptr;
-  cudaError_t ce = cudaMalloc(&saved_x, 3 * vbytes);
+  cudaError_t ce = cudaMalloc(&saved_x, 4 * vbytes);
   if (ce == cudaSuccess) ce = cudaMalloc((void**)&saved_ctl, sizeof(DevCtl));
   if (ce != cudaSuccess) {
     cudaFree(saved_x);
@@ -1481,7 +1484,9 @@ seg_status seg_autotune(seg_state* s, int32_t reps, seg_tune_result* out) {
   if (ce == cudaSuccess)
     ce = cudaMemcpyAsync((char*)saved_x + vbytes, s->Y, vbytes, cudaMemcpyDeviceToDevice, s->stream);
   if (ce == cudaSuccess)
-    ce = cudaMemcpyAsync((char*)saved_x + 2 * vbytes, s->H, vbytes, cudaMemcpyDeviceToDevice, s->stream);
+    ce = cudaMemcpyAsync((char*)saved_x + 2 * vbytes, s->H0, vbytes, cudaMemcpyDeviceToDevice, s->stream);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync((char*)saved_x + 3 * vbytes, s->H1, vbytes, cudaMemcpyDeviceToDevice, s->stream);
   if (ce == cudaSuccess) ce = cudaMemcpyAsync(saved_ctl, s->ctl, sizeof(DevCtl), cudaMemcpyDeviceToDevice, s->stream);
   if (ce != cudaSuccess) st = fail(SEG_ERR_CUDA, std::string("save: ") + cudaGetErrorString(ce));
   // candidate row grids: 1 .. kRowBlocksPerSM blocks per SM (one wave), and
@@ -1550,7 +1555,9 @@ seg_status seg_autotune(seg_state* s, int32_t reps, seg_tune_result* out) {
   if (ce == cudaSuccess)
     ce = cudaMemcpyAsync(s->Y, (char*)saved_x + vbytes, vbytes, cudaMemcpyDeviceToDevice, s->stream);
   if (ce == cudaSuccess)
-    ce = cudaMemcpyAsync(s->H, (char*)saved_x + 2 * vbytes, vbytes, cudaMemcpyDeviceToDevice, s->stream);
+    ce = cudaMemcpyAsync(s->H0, (char*)saved_x + 2 * vbytes, vbytes, cudaMemcpyDeviceToDevice, s->stream);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync(s->H1, (char*)saved_x + 3 * vbytes, vbytes, cudaMemcpyDeviceToDevice, s->stream);
   if (ce == cudaSuccess) ce = cudaMemcpyAsync(s->ctl, saved_ctl, sizeof(DevCtl), cudaMemcpyDeviceToDevice, s->stream);
   for (void* b : {s->Z, s->P0, s->P1, s->Q})
     if (ce == cudaSuccess) ce = cudaMemsetAsync(b, 0, vbytes, s->stream);

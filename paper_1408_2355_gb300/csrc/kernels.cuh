@@ -1254,10 +1254,11 @@ __device__ __forceinline__ void body_cg_b(const KArgs<T>& a, const int vb, const
 // (lagged from the last iterations; apply_x, else x = X), then the exact
 // solution of the nodal ODE of step 2 (Jacobi form):
 //   u~ = x * inv_n,  u^_i = u~_i exp(-(2 tau/eps^2) sum_{j != i} u~_j^2)  -> X.
-// With apply_x the next solve's initial correction is predicted by linear
-// extrapolation of the last two, Y = 2 y_k - y_{k-1} (H holds y_{k-1} and
-// then y_k); any initial guess gives the same solution to the solve's
-// tolerance.
+// With apply_x the next solve's initial correction is predicted by quadratic
+// extrapolation of the last three, Y = 3 y_k - 3 y_{k-1} + y_{k-2}; H0 and H1
+// keep the corrections of the last two solves (step k reads y_{k-1} from
+// H[(k+1) % 2] and y_{k-2} from H[k % 2], then writes y_k over the latter).
+// Any initial guess gives the same solution to the solve's tolerance.
 // The solution updates CG pass A has not applied yet: alpha_k p_k, and
 // alpha_{k-1} p_{k-1} before it (TWO) when the iteration count k is odd.
 template <typename T, int LPR, int RU, bool TWO>
@@ -1267,6 +1268,9 @@ __device__ __forceinline__ void body_finish_rows(const KArgs<T>& a, const int vb
   const int lbase = lane - cg;
   const T* P = (it & 1) ? a.P1 : a.P0;
   const T* P2 = (it & 1) ? a.P0 : a.P1;
+  const bool odd_step = (ctl->step & 1) != 0;
+  const T* Hm1 = odd_step ? a.H0 : a.H1;  // y_{k-1}
+  T* Hm2 = odd_step ? a.H1 : a.H0;        // y_{k-2}, replaced by y_k
   constexpr bool two = TWO;
   const unsigned ms = a.ms;
   T al[VW], al2[VW], invn[VW], ysc[VW];
@@ -1279,20 +1283,21 @@ __device__ __forceinline__ void body_finish_rows(const KArgs<T>& a, const int vb
   }
   const T mcoef = -(T)a.coef;
   for (int base = r0 + warp * RPW * RU; base < r1; base += NW * RPW * RU) {
-    T x[RU][VW], y[RU][VW], h[RU][VW], p[RU][VW], p2[TWO ? RU : 1][VW];
+    T x[RU][VW], y[RU][VW], h1[RU][VW], h2[RU][VW], p[RU][VW], p2[TWO ? RU : 1][VW];
 #pragma unroll
     for (int u = 0; u < RU; ++u) {
       const unsigned row = base + u * RPW + rs;
 #pragma unroll
       for (int v = 0; v < VW; ++v) {
-        x[u][v] = y[u][v] = h[u][v] = p[u][v] = T(0);
+        x[u][v] = y[u][v] = h1[u][v] = h2[u][v] = p[u][v] = T(0);
         if (two) p2[u][v] = T(0);
       }
       if ((int)row < r1) {
         ld(x[u], a.X + (row * ms + c0));
         if (a.apply_x) {
           ld(y[u], a.Y + (row * ms + c0));
-          ld(h[u], a.H + (row * ms + c0));
+          ld(h1[u], Hm1 + (row * ms + c0));
+          ld(h2[u], Hm2 + (row * ms + c0));
           ld_ro(p[u], P + (row * ms + c0));
         }
         if (two) ld_ro(p2[TWO ? u : 0], P2 + (row * ms + c0));
@@ -1309,12 +1314,12 @@ __device__ __forceinline__ void body_finish_rows(const KArgs<T>& a, const int vb
         x[u][v] += y[u][v];
       }
       if (a.apply_x && (int)row < r1) {
-        // the next solve's predicted correction 2 y_k - y_{k-1}; y_k kept
+        // the next solve's predicted correction 3 (y_k - y_{k-1}) + y_{k-2}; y_k kept
         T g[VW];
 #pragma unroll
-        for (int v = 0; v < VW; ++v) g[v] = fma(T(2), y[u][v], -h[u][v]);
+        for (int v = 0; v < VW; ++v) g[v] = fma(T(3), y[u][v] - h1[u][v], h2[u][v]);
         st(a.Y + (row * ms + c0), g);
-        st(a.H + (row * ms + c0), y[u]);
+        st(Hm2 + (row * ms + c0), y[u]);
       }
       if (a.apply_ode) {
         T sq[1][VW], ex[1][VW], ut[VW];
