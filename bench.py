@@ -35,7 +35,7 @@ HBM_FALLBACK_GBS = 6800.0
 # even and one of its odd form, from the ncu capture summarised in
 # profiles/k_cg_a_sphere_L8_m16_mixed.md (level-8 sphere, m = 16, mixed);
 # valid for that workload and that version of the kernel only.
-TRAFFIC_CG_A = 270.3e6
+TRAFFIC_CG_A = 270.6e6
 METRIC = "DoF-steps/s (N*m*steps) sphere 655k m=16 FP32-mix vs FP64; p50/p99 latency"
 
 
@@ -357,7 +357,7 @@ def run_ours(a, rank, ws, local):
         "clocks": clk,
         "roofline": {
             "bound": "hbm",
-            "kernel": "k_cg_a (CG pass A: p = z + beta p, q = A z + beta q, p.q; x updated every second iteration), mean of its even and odd forms",
+            "kernel": "k_cg_a (CG pass A: p = z + beta p, q = A z + beta q, p.q; the solve's correction y updated every second iteration), mean of its even and odd forms",
             "achieved": achieved,
             "peak": peak,
             "peak_kind": peak_kind,

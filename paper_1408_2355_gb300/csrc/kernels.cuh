@@ -1394,7 +1394,9 @@ __device__ __forceinline__ int batch_slot(const BatchArgs<T>& b) {
 
 #define SEG_TPL_W template <typename T, int LPR, int W>
 #define SEG_TPL template <typename T, int LPR>
-SEG_DEFINE_PASS(start, kRowBlocksPerSM, SEG_TPL_W, T, LPR, W)
+// The start pass (three sparse products and two float-float sums per row)
+// is compiled for one resident block per SM, so that it does not spill.
+SEG_DEFINE_PASS(start, 1, SEG_TPL_W, T, LPR, W)
 SEG_DEFINE_PASS(cg_a, kRowBlocksPerSM, SEG_TPL_W, T, LPR, W)
 SEG_DEFINE_PASS(cg_b, kRowBlocksPerSM, SEG_TPL, T, LPR)
 SEG_DEFINE_PASS(finish, kRowBlocksPerSM, SEG_TPL, T, LPR)
