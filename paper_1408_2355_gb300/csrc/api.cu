@@ -1113,6 +1113,12 @@ struct seg_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaGraphConditionalHandle cond = 0;
+  int peel = 0;  // CG iterations of the graph ahead of its loop node (0: the members' largest)
+  // graphs replaced while launches of them may still be in flight
+  std::vector<std::pair<cudaGraph_t, cudaGraphExec_t>> retired;
+  long long* hsnap = nullptr;  // pinned: 2 slots x members x (step, cg_total)
+  cudaEvent_t snap_ev[2] = {nullptr, nullptr};
+  std::vector<long long> mark_step, mark_it;  // members' counters at the last peel review
 };
 
 namespace {
@@ -1160,10 +1166,12 @@ seg_status build_batch_t(seg_batch* b) {
   SEG_CUDA(add_batch_node<T>(&n_start, b->graph, nullptr, 0, b->ks.b_start, rows[kPassStart], kBlockThreads,
                              b->ks.smem_start));
   SEG_CUDA(add_batch_node<T>(&n_energy, b->graph, &n_start, 1, b->ks.b_energy_check, tris, kBlockThreads, 0));
-  // as in the single-state graph: the first CG iterations (the largest
-  // peel count of the members) as plain nodes, then the vote and the loop
-  int peel = 0;
-  for (seg_state* m : b->members) peel = std::max(peel, m->cg_peel);
+  // as in the single-state graph: the first CG iterations (at first the
+  // largest peel count of the members, then reviewed while stepping) as
+  // plain nodes, then the vote and the loop
+  if (b->peel <= 0)
+    for (seg_state* m : b->members) b->peel = std::max(b->peel, m->cg_peel);
+  const int peel = b->peel;
   cudaGraphNode_t last = n_energy;
   for (int u = 0; u < peel; ++u) {
     SEG_CUDA(add_batch_node<T>(&n_a, b->graph, &last, 1, b->ks.b_cg_a, rows[kPassCgA], kBlockThreads,
@@ -1230,6 +1238,23 @@ seg_status seg_batch_create(seg_state* const* states, int32_t n, void* cuda_stre
     e = cudaStreamSynchronize(states[i]->stream);
     if (e != cudaSuccess) st = fail(SEG_ERR_CUDA, cudaGetErrorString(e));
   }
+  if (st == SEG_OK) {
+    e = cudaMallocHost((void**)&b->hsnap, 4 * (size_t)n * sizeof(long long));
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&b->snap_ev[k], cudaEventDisableTiming);
+    if (e != cudaSuccess) st = fail(SEG_ERR_CUDA, cudaGetErrorString(e));
+  }
+  if (st == SEG_OK) {
+    // members' counters as of now (their streams are idle) start the first review
+    b->mark_step.assign(n, 0);
+    b->mark_it.assign(n, 0);
+    for (int i = 0; i < n && st == SEG_OK; ++i) {
+      st = sync_ctl(states[i]);
+      if (st == SEG_OK) {
+        b->mark_step[i] = states[i]->hctl->step;
+        b->mark_it[i] = states[i]->hctl->cg_total;
+      }
+    }
+  }
   if (st == SEG_OK) st = b->prec == SEG_MIXED_FP32 ? build_batch_t<float>(b) : build_batch_t<double>(b);
   if (st != SEG_OK) {
     seg_batch_destroy(b);
@@ -1239,14 +1264,30 @@ seg_status seg_batch_create(seg_state* const* states, int32_t n, void* cuda_stre
   return SEG_OK;
 }
 
-seg_status seg_batch_step_async(seg_batch* b, int64_t nsteps) {
-  if (!b) return fail(SEG_ERR_ARG, "batch is NULL");
-  if (nsteps < 0) return fail(SEG_ERR_ARG, "nsteps must be >= 0");
+}  // extern "C"
+
+namespace {
+
+seg_status begin_batch_steps(seg_batch* b) {
   SEG_CUDA(cudaSetDevice(b->members[0]->p->device));
   for (seg_state* s : b->members) {
     SEG_CUDA(cudaMemcpyAsync(&s->ctl->step_mark, &s->ctl->step, sizeof(long long), cudaMemcpyDeviceToDevice,
                              b->stream));
     SEG_CUDA(cudaMemsetAsync(&s->ctl->status, 0, sizeof(int), b->stream));
+  }
+  return SEG_OK;
+}
+
+seg_status enqueue_batch_steps(seg_batch* b, int64_t nsteps) {
+  if (!b->exec) {
+    const seg_status gs = b->prec == SEG_MIXED_FP32 ? build_batch_t<float>(b) : build_batch_t<double>(b);
+    if (gs != SEG_OK) {
+      if (b->exec) cudaGraphExecDestroy(b->exec);
+      if (b->graph) cudaGraphDestroy(b->graph);
+      b->exec = nullptr;
+      b->graph = nullptr;
+      return gs;
+    }
   }
   for (int64_t k = 0; k < nsteps; ++k) SEG_CUDA(cudaGraphLaunch(b->exec, b->stream));
   if (nsteps > 0)
@@ -1254,11 +1295,60 @@ seg_status seg_batch_step_async(seg_batch* b, int64_t nsteps) {
   return SEG_OK;
 }
 
+void drop_batch_retired(seg_batch* b) {
+  for (auto& r : b->retired) {
+    if (r.second) cudaGraphExecDestroy(r.second);
+    if (r.first) cudaGraphDestroy(r.first);
+  }
+  b->retired.clear();
+}
+
+// The batch's graph runs as many CG iterations per step as its slowest
+// member: review its peel against the largest mean iterations per step of
+// the members since the last review (the same rule as review_peel; members
+// that took no step, e.g. stopped ones, are left out).  snap holds the
+// members' (step, cg_total) pairs.
+void review_batch_peel(seg_batch* b, const long long* snap) {
+  const size_t n = b->members.size();
+  double worst = 0.0;
+  long long most = 0;
+  for (size_t i = 0; i < n; ++i) {
+    const long long ds = snap[2 * i] - b->mark_step[i], di = snap[2 * i + 1] - b->mark_it[i];
+    if (ds > 0 && di >= 0) worst = std::max(worst, (double)di / (double)ds);
+    most = std::max(most, ds);
+  }
+  if (most < 3) return;
+  const int target = std::min(kCgPeelMax, std::max(1, (int)std::ceil(worst - 0.1)));
+  if (target > b->peel || target <= b->peel - 2) {
+    b->peel = target;
+    if (b->exec || b->graph) b->retired.emplace_back(b->graph, b->exec);
+    b->exec = nullptr;
+    b->graph = nullptr;
+  }
+  for (size_t i = 0; i < n; ++i) {
+    b->mark_step[i] = snap[2 * i];
+    b->mark_it[i] = snap[2 * i + 1];
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+seg_status seg_batch_step_async(seg_batch* b, int64_t nsteps) {
+  if (!b) return fail(SEG_ERR_ARG, "batch is NULL");
+  if (nsteps < 0) return fail(SEG_ERR_ARG, "nsteps must be >= 0");
+  seg_status st = begin_batch_steps(b);
+  if (st != SEG_OK) return st;
+  return enqueue_batch_steps(b, nsteps);
+}
+
 seg_status seg_batch_sync(seg_batch* b) {
   if (!b) return fail(SEG_ERR_ARG, "batch is NULL");
   for (seg_state* s : b->members)
     SEG_CUDA(cudaMemcpyAsync(s->hctl, s->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, b->stream));
   SEG_CUDA(cudaStreamSynchronize(b->stream));
+  drop_batch_retired(b);
   for (seg_state* s : b->members) {
     seg_status st = status_from_ctl(*s->hctl);
     if (st != SEG_OK) return st;
@@ -1266,18 +1356,56 @@ seg_status seg_batch_sync(seg_batch* b) {
   return SEG_OK;
 }
 
+// As seg_step: a run of 64 or more steps is enqueued in chunks of 16, at
+// most two ahead of the device, and the graph's peel is reviewed between
+// chunks from the members' counters.
 seg_status seg_batch_step(seg_batch* b, int64_t nsteps) {
-  seg_status st = seg_batch_step_async(b, nsteps);
+  if (!b) return fail(SEG_ERR_ARG, "batch is NULL");
+  if (nsteps < 0) return fail(SEG_ERR_ARG, "nsteps must be >= 0");
+  seg_status st = begin_batch_steps(b);
   if (st != SEG_OK) return st;
+  if (nsteps < 4 * kReviewChunk) {
+    st = enqueue_batch_steps(b, nsteps);
+    if (st != SEG_OK) return st;
+    return seg_batch_sync(b);
+  }
+  const size_t n = b->members.size();
+  int slot = 0;
+  bool have_prev = false;
+  for (int64_t left = nsteps; left > 0;) {
+    const int64_t c = std::min(left, kReviewChunk);
+    st = enqueue_batch_steps(b, c);
+    if (st != SEG_OK) return st;
+    left -= c;
+    long long* snap = b->hsnap + 2 * n * slot;
+    for (size_t i = 0; i < n; ++i) {
+      seg_state* s = b->members[i];
+      SEG_CUDA(cudaMemcpyAsync(snap + 2 * i, &s->ctl->step, sizeof(long long), cudaMemcpyDeviceToHost, b->stream));
+      SEG_CUDA(cudaMemcpyAsync(snap + 2 * i + 1, &s->ctl->cg_total, sizeof(long long), cudaMemcpyDeviceToHost,
+                               b->stream));
+    }
+    SEG_CUDA(cudaEventRecord(b->snap_ev[slot], b->stream));
+    if (have_prev && left > 0) {
+      const int prev = slot ^ 1;
+      SEG_CUDA(cudaEventSynchronize(b->snap_ev[prev]));
+      review_batch_peel(b, b->hsnap + 2 * n * prev);
+    }
+    have_prev = true;
+    slot ^= 1;
+  }
   return seg_batch_sync(b);
 }
 
 void seg_batch_destroy(seg_batch* b) {
   if (!b) return;
   if (b->stream) cudaStreamSynchronize(b->stream);
+  drop_batch_retired(b);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->tab) cudaFree(b->tab);
+  if (b->hsnap) cudaFreeHost(b->hsnap);
+  for (cudaEvent_t e : b->snap_ev)
+    if (e) cudaEventDestroy(e);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
 }
