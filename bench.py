@@ -31,11 +31,22 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 HBM_FALLBACK_GBS = 6800.0
-# DRAM bytes (read + write) per k_cg_a launch, the mean of one launch of its
-# even and one of its odd form, from the ncu capture summarised in
-# profiles/k_cg_a_sphere_L8_m16_mixed.md (level-8 sphere, m = 16, mixed);
-# valid for that workload and that version of the kernel only.
-TRAFFIC_CG_A = 270.6e6
+# DRAM bytes (read + write) per launch from the ncu captures summarised in
+# profiles/k_cg_a_sphere_L8_m16_mixed.md (k_cg_a: the mean of one launch of its
+# even and one of its odd form) and profiles/other_passes_sphere_L8_m16_mixed.md
+# (level-8 sphere, m = 16, mixed); valid for that workload and those versions
+# of the kernels only.  k_finish was captured in its even form only.
+TRAFFIC = {"k_cg_a": 270.6e6, "k_start": 200.2e6, "k_cg_b": 93.3e6, "k_energy_check": 63.3e6, "k_finish": None}
+KERNEL_ROLE = {
+    "k_start": "start pass: r0 = -tau K X - A y for the predicted correction y, z0 = D^-1 r0, norms "
+               "(issue and latency bound: three sparse products and two float-float sums per row)",
+    "k_cg_a": "CG pass A: p = z + beta p, q = A z + beta q, p.q; the solve's correction updated every "
+              "second iteration (mean of its even and odd forms)",
+    "k_cg_b": "CG pass B: z -= alpha D^-1 q, r.z, |r|^2, convergence and beta",
+    "k_finish": "finish pass: x = X + y, nodal segregation ODE, next predicted correction (mean of its "
+                "forms after an even and an odd iteration count)",
+    "k_energy_check": "S_eps by the degree-4 rule and the stop rule",
+}
 METRIC = "DoF-steps/s (N*m*steps) sphere 655k m=16 FP32-mix vs FP64; p50/p99 latency"
 
 
@@ -317,10 +328,31 @@ def run_ours(a, rank, ws, local):
         t = seg.seg_time_kernel(st, which, 20)
         kern[name] = {"ms": t, "bytes": kb[name], "GBps": kb[name] / (t / 1e3) / 1e9,
                       "frac": kb[name] / (t / 1e3) / 1e9 / peak}
-    # CG pass A alternates between its two forms: one launch of each, averaged
-    t_a = 0.5 * (kern["k_cg_a_even"]["ms"] + kern["k_cg_a_odd"]["ms"])
-    bytes_a = 0.5 * (kb["k_cg_a_even"] + kb["k_cg_a_odd"])
-    achieved = bytes_a / (t_a / 1e3) / 1e9
+    # per-step kernel time: CG pass A alternates between its two forms and the
+    # finish pass has one form per parity of the iteration count (taken as
+    # equally likely); the energy check runs every step here
+    kcg = dcg / a.steps
+    per = {
+        "k_start": (kern["k_start"]["ms"], kb["k_start"], 1.0),
+        "k_energy_check": (kern["k_energy_check"]["ms"], kb["k_energy_check"], 1.0),
+        "k_cg_a": (0.5 * (kern["k_cg_a_even"]["ms"] + kern["k_cg_a_odd"]["ms"]),
+                   0.5 * (kb["k_cg_a_even"] + kb["k_cg_a_odd"]), kcg),
+        "k_cg_b": (kern["k_cg_b"]["ms"], kb["k_cg_b"], kcg),
+        "k_finish": (0.5 * (kern["k_finish_even"]["ms"] + kern["k_finish_odd"]["ms"]),
+                     0.5 * (kb["k_finish_even"] + kb["k_finish_odd"]), 1.0),
+    }
+    share = {k: t * c for k, (t, _, c) in per.items()}
+    tot_share = sum(share.values())
+
+    def roofline_of(name):
+        t, b, c = per[name]
+        got = b / (t / 1e3) / 1e9
+        return {"bound": "hbm", "kernel": f"{name} ({KERNEL_ROLE[name]})", "achieved": got, "peak": peak,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": got / peak, "traffic": TRAFFIC[name],
+                "bytes_per_launch": b, "launch_ms": t, "launches_per_step": c,
+                "share_of_kernel_time": share[name] / tot_share}
+
+    dominant = max(share, key=share.get)
 
     out = {
         "metric": METRIC,
@@ -355,18 +387,14 @@ def run_ours(a, rank, ws, local):
         "final_total_energy": e_final["total"],
         "gpu_launches": launches,
         "clocks": clk,
-        "roofline": {
-            "bound": "hbm",
-            "kernel": "k_cg_a (CG pass A: p = z + beta p, q = A z + beta q, p.q; the solve's correction y updated every second iteration), mean of its even and odd forms",
-            "achieved": achieved,
-            "peak": peak,
-            "peak_kind": peak_kind,
-            "unit": "GB/s",
-            "frac": achieved / peak,
-            "traffic": TRAFFIC_CG_A,
-            "bytes_per_launch": bytes_a,
-            "launch_ms": t_a,
-        },
+        # the kernel with the largest share of the kernel time per step, and
+        # CG pass A, the bandwidth-bound pass of the solve
+        "roofline": roofline_of(dominant),
+        "roofline_cg_a": roofline_of("k_cg_a"),
+        "step_roofline": {"bytes_per_step": sum(b * c for _, b, c in per.values()),
+                          "achieved": sum(b * c for _, b, c in per.values()) / (ms / a.steps / 1e3) / 1e9,
+                          "peak": peak, "unit": "GB/s",
+                          "frac": sum(b * c for _, b, c in per.values()) / (ms / a.steps / 1e3) / 1e9 / peak},
         "kernels": kern,
     }
 
