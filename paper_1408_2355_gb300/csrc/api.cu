@@ -1137,11 +1137,50 @@ cudaError_t add_batch_node(cudaGraphNode_t* node, cudaGraph_t g, const cudaGraph
   return cudaGraphAddKernelNode(node, g, deps, ndeps, &kp);
 }
 
+// Blocks of each member in a batched pass.  A member keeps its own grid
+// while the members' grids together take no more waves of resident blocks
+// than the member that needs the most (then results are bitwise those of the
+// member alone); otherwise that many waves are shared out in proportion to
+// the members' work (rows, or triangles for the energy check), at least one
+// block each: two members that each fill the GPU run side by side on half of
+// it instead of in twice the waves.
+void batch_grids(const std::vector<int>& own, const std::vector<int64_t>& work, int per_wave, std::vector<int>* out) {
+  const size_t n = own.size();
+  int64_t sum = 0, waves = 1, wsum = 0;
+  for (size_t i = 0; i < n; ++i) {
+    sum += own[i];
+    waves = std::max<int64_t>(waves, (own[i] + per_wave - 1) / per_wave);
+    wsum += work[i];
+  }
+  out->assign(own.begin(), own.end());
+  const int64_t cap = waves * per_wave;
+  if (sum <= cap || wsum <= 0) return;
+  for (size_t i = 0; i < n; ++i)
+    (*out)[i] = (int)std::max<int64_t>(1, std::min<int64_t>(own[i], cap * work[i] / wsum));
+}
+
 template <typename T>
 seg_status build_batch_t(seg_batch* b) {
   const int n = (int)b->members.size();
   std::vector<KArgs<T>> tab(n);
   BatchArgs<T> rows[4] = {}, tris{}, vote{};
+  int nsm = 0;
+  SEG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->members[0]->p->device));
+  std::vector<int> grids[5];
+  {
+    std::vector<int64_t> nrow(n), ntri(n);
+    std::vector<int> own(n);
+    for (int i = 0; i < n; ++i) {
+      nrow[i] = b->members[i]->p->n;
+      ntri[i] = b->members[i]->p->f;
+    }
+    for (int k = 0; k < 4; ++k) {
+      for (int i = 0; i < n; ++i) own[i] = b->members[i]->grid[k];
+      batch_grids(own, nrow, nsm * (k == kPassStart ? kStartBlocksPerSM : kRowBlocksPerSM), &grids[k]);
+    }
+    for (int i = 0; i < n; ++i) own[i] = b->members[i]->grid_e;
+    batch_grids(own, ntri, nsm * kTriBlocksPerSM, &grids[4]);
+  }
   for (int i = 0; i < n; ++i) {
     seg_state* s = b->members[i];
     Launch l;
@@ -1150,8 +1189,8 @@ seg_status build_batch_t(seg_batch* b) {
     l.apply_ode = 1;
     l.count_step = 1;
     tab[i] = make_args<T>(s, l);
-    for (int k = 0; k < 4; ++k) rows[k].off[i + 1] = rows[k].off[i] + s->grid[k];
-    tris.off[i + 1] = tris.off[i] + s->grid_e;
+    for (int k = 0; k < 4; ++k) rows[k].off[i + 1] = rows[k].off[i] + grids[k][i];
+    tris.off[i + 1] = tris.off[i] + grids[4][i];
   }
 
   SEG_CUDA(cudaGraphCreate(&b->graph, 0));

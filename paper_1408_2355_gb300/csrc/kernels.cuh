@@ -678,9 +678,15 @@ __device__ __forceinline__ void body_start(const KArgs<T>& a, const int vb, cons
         T x[VW];
         lds(x, sg.vec(0) + rs * ms + c0);
         const T di = __ldg(a.dinv + row);
-        T xj[W][VW];  // padding entries point at the row itself with value 0
+        // the neighbours' rows of X and Y all in flight at once (padding
+        // entries point at the row itself with value 0)
+        T xj[W][VW], yj[W][VW];
 #pragma unroll
-        for (int k = 0; k < W; ++k) ld_ro(xj[k], a.X + ((unsigned)cols[k] * ms + c0));
+        for (int k = 0; k < W; ++k) {
+          const unsigned o = (unsigned)cols[k] * ms + c0;
+          ld_ro(xj[k], a.X + o);
+          ld_ro(yj[k], a.Y + o);
+        }
         T kx[VW], mx[VW];
 #pragma unroll
         for (int v = 0; v < VW; ++v) kx[v] = mx[v] = T(0);
@@ -699,11 +705,9 @@ __device__ __forceinline__ void body_start(const KArgs<T>& a, const int vb, cons
         for (int v = 0; v < VW; ++v) ay[v] = T(0);
 #pragma unroll
         for (int k = 0; k < W; ++k) {
-          T yj[VW];
-          ld_ro(yj, a.Y + ((unsigned)cols[k] * ms + c0));
           const T ak = av[k];
 #pragma unroll
-          for (int v = 0; v < VW; ++v) ay[v] = fma(ak, yj[v], ay[v]);
+          for (int v = 0; v < VW; ++v) ay[v] = fma(ak, yj[k][v], ay[v]);
         }
         T r[VW], z[VW];
 #pragma unroll
@@ -1396,7 +1400,7 @@ __device__ __forceinline__ int batch_slot(const BatchArgs<T>& b) {
 #define SEG_TPL template <typename T, int LPR>
 // The start pass (three sparse products and two float-float sums per row)
 // is compiled for one resident block per SM, so that it does not spill.
-SEG_DEFINE_PASS(start, 1, SEG_TPL_W, T, LPR, W)
+SEG_DEFINE_PASS(start, kStartBlocksPerSM, SEG_TPL_W, T, LPR, W)
 SEG_DEFINE_PASS(cg_a, kRowBlocksPerSM, SEG_TPL_W, T, LPR, W)
 SEG_DEFINE_PASS(cg_b, kRowBlocksPerSM, SEG_TPL, T, LPR)
 SEG_DEFINE_PASS(finish, kRowBlocksPerSM, SEG_TPL, T, LPR)

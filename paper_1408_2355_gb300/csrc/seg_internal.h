@@ -18,6 +18,7 @@ constexpr int kMaxDots = 6;         // inner products fused into one pass
 // and launched with; the triangle passes use kTriBlocksPerSM.
 constexpr int kRowBlocksPerSM = 2;
 constexpr int kTriBlocksPerSM = 2;
+constexpr int kStartBlocksPerSM = 1;  // the start pass (more registers per thread)
 constexpr int kMaxGrid = 2048;  // blocks of one kernel of a state
 constexpr int kTuneWaves = 4;   // the autotuner tries up to this many waves of blocks
 constexpr int kCgUnroll = 2;    // CG iterations per evaluation of the step graph's loop condition
