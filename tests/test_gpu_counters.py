@@ -66,3 +66,29 @@ def test_long_step_reviews_the_graph_without_changing_results(seg):
     sa, sb = seg.seg_get_stats(a), seg.seg_get_stats(b)
     assert sa["cg_iterations"] == sb["cg_iterations"]
     assert 1 <= sa["graph_peel"] <= max(4, sa["cg_max"])
+
+
+def test_predicted_start_cuts_the_iterations(seg):
+    """The step-1 solve starts from the extrapolated correction once that
+    beats a plain warm start: after the first steps from random data the CG
+    iterations per step drop well below those of the first steps, and a state
+    set to the same data again (no history) starts over."""
+    import numpy as np
+
+    xyz, tri = w.icosphere(5)  # tau / h^2 and 2 tau / eps^2 as in the level-8 workload
+    st = make_state(seg, xyz, tri, 3e-4, 8, 8e-3, 1, 3, check_every=-1)
+
+    def its(k):
+        c0 = seg.seg_get_stats(st)["cg_iterations"]
+        seg.seg_step(st, k)
+        return (seg.seg_get_stats(st)["cg_iterations"] - c0) / k
+
+    first = its(5)
+    its(45)
+    late = its(20)
+    assert late < 0.75 * first, (first, late)
+    U = seg.seg_get_u(st)
+    seg.seg_set_u(st, U)  # same state, no history: plain warm start again
+    again = its(1)
+    assert again > late
+    assert np.all(np.isfinite(seg.seg_get_u(st)))
