@@ -39,7 +39,7 @@ HBM_FALLBACK_GBS = 6800.0
 TRAFFIC = {"k_cg_a": 270.6e6, "k_start": 200.2e6, "k_cg_b": 93.3e6, "k_energy_check": 63.3e6, "k_finish": None}
 KERNEL_ROLE = {
     "k_start": "start pass: r0 = -tau K X - A y for the predicted correction y, z0 = D^-1 r0, norms "
-               "(issue and latency bound: three sparse products and two float-float sums per row)",
+               "(issue and latency bound: three sparse products and three float-float sums per row)",
     "k_cg_a": "CG pass A: p = z + beta p, q = A z + beta q, p.q; the solve's correction updated every "
               "second iteration (mean of its even and odd forms)",
     "k_cg_b": "CG pass B: z -= alpha D^-1 q, r.z, |r|^2, convergence and beta",

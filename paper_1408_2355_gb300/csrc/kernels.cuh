@@ -1398,7 +1398,7 @@ __device__ __forceinline__ int batch_slot(const BatchArgs<T>& b) {
 
 #define SEG_TPL_W template <typename T, int LPR, int W>
 #define SEG_TPL template <typename T, int LPR>
-// The start pass (three sparse products and two float-float sums per row)
+// The start pass (three sparse products and three float-float sums per row)
 // is compiled for one resident block per SM, so that it does not spill.
 SEG_DEFINE_PASS(start, kStartBlocksPerSM, SEG_TPL_W, T, LPR, W)
 SEG_DEFINE_PASS(cg_a, kRowBlocksPerSM, SEG_TPL_W, T, LPR, W)
