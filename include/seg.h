@@ -71,10 +71,11 @@ typedef struct {
   double cg_rtol;        /* step-1 CG stops at ||r||_2 <= cg_rtol ||M u||_2 per component;
                             default 1e-12 (SEG_FP64), 1e-7 (SEG_MIXED_FP32).  The solve of
                             step k starts from u^k plus the correction extrapolated from the
-                            last three solves, 3 y_{k-1} - 3 y_{k-2} + y_{k-3} (y = u~ - u),
-                            for the components where that prediction beat none in the
-                            previous step (none after seg_set_u or creation); its result is
-                            the same to this tolerance */
+                            last solves (y = u~ - u): 3 y_{k-1} - 3 y_{k-2} + y_{k-3} in
+                            SEG_MIXED_FP32, 4 y_{k-1} - 6 y_{k-2} + 4 y_{k-3} - y_{k-4} in
+                            SEG_FP64, for the components where that prediction beat none in
+                            the previous step (none after seg_set_u or creation); its result
+                            is the same to this tolerance */
   int32_t cg_maxit;      /* default 1000 */
   int32_t grid_blocks;   /* CUDA blocks of the row kernels (<= 2048); default 2 per SM */
   int64_t check_every;   /* Sec. 2.2 stop rule cadence M_tau; default round(0.1 / tau);
@@ -431,9 +432,10 @@ typedef struct {
  * (seg_stats.graph_peel).  Later steps give
  * the same results as without tuning up to the summation order of the
  * per-block partial inner products.  A batch built from the state earlier
- * keeps the geometry it was built with.  Needs device memory for four
- * state-sized vectors (the state and the three corrections its solves carry;
- * SEG_ERR_NO_MEMORY otherwise).  Synchronises. */
+ * keeps the geometry it was built with.  Needs device memory for four (five
+ * in SEG_FP64) state-sized vectors (the state, the predicted correction and
+ * the corrections of the last solves; SEG_ERR_NO_MEMORY otherwise).
+ * Synchronises. */
 seg_status seg_autotune(seg_state* s, int32_t reps, seg_tune_result* out);
 
 /* ------------------------------------------------------- allocation-free call */

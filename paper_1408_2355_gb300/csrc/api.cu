@@ -84,8 +84,9 @@ struct seg_state {
   int grid_e_cap = 0;  // ... and this many triangle blocks
   void* X = nullptr;
   void* Y = nullptr;        // correction of the CG iterate (x = X + y), starts at a prediction
-  void* H0 = nullptr;       // the last two steps' final corrections (step k's in H[k % 2])
+  void* H0 = nullptr;       // the last two (float) or three (double) steps' final corrections
   void* H1 = nullptr;
+  void* H2 = nullptr;       // double states only
   void* Z = nullptr;        // preconditioned residual
   void* P0 = nullptr;       // search directions, ping-pong
   void* P1 = nullptr;
@@ -379,6 +380,7 @@ void fill_args(seg_state* s) {
   a.Y = (T*)s->Y;
   a.H0 = (T*)s->H0;
   a.H1 = (T*)s->H1;
+  a.H2 = (T*)s->H2;
   a.diagA = (const T*)p->diagA;
   a.Z = (T*)s->Z;
   a.P0 = (T*)s->P0;
@@ -445,7 +447,7 @@ void free_state(seg_state* s) {
   if (!s) return;
   drop_retired(s);
   drop_graph(s);
-  void* bufs[] = {s->X, s->Y, s->H0, s->H1, s->Z, s->P0, s->P1, s->Q, s->ctl, s->part, s->io, s->ones, s->scale_backup, s->am, s->vp};
+  void* bufs[] = {s->X, s->Y, s->H0, s->H1, s->H2, s->Z, s->P0, s->P1, s->Q, s->ctl, s->part, s->io, s->ones, s->scale_backup, s->am, s->vp};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (s->hctl) cudaFreeHost(s->hctl);
@@ -789,6 +791,7 @@ seg_status seg_state_create(const seg_problem* p, int32_t m, double eps, seg_ini
                 {&s->Y, vbytes},
                 {&s->H0, vbytes},
                 {&s->H1, vbytes},
+                {&s->H2, s->prec == SEG_FP64 ? vbytes : 0},
                 {&s->Z, vbytes},
                 {&s->P0, vbytes},
                 {&s->P1, vbytes},
@@ -801,6 +804,7 @@ seg_status seg_state_create(const seg_problem* p, int32_t m, double eps, seg_ini
                 {(void**)&s->am, std::max<size_t>(4, (size_t)p->n * sizeof(int))},
                 {(void**)&s->vp, std::max<size_t>(4, (size_t)p->n)}};
   for (auto& al : allocs) {
+    if (al.bytes == 0) continue;  // (a buffer only some precisions use)
     ce = cudaMalloc(al.ptr, al.bytes);
     if (ce != cudaSuccess) {
       free_state(s);
@@ -884,7 +888,7 @@ seg_status seg_state_bytes(const seg_problem* p, int32_t m, uint64_t* bytes) {
   const uint64_t grid_e = (uint64_t)std::min(kMaxGrid, kTuneWaves * kTriBlocksPerSM * nsm);
   const uint64_t vbytes = n * ms * vsize(p->prec);
   const uint64_t pbytes = partial_bytes((int)ms, (int)grid, (int)grid_e);
-  *bytes = 8 * vbytes + sizeof(DevCtl) + pbytes + std::max<uint64_t>(8, n * m * 8) + 2 * kMaxCols * 8 +
+  *bytes = (p->prec == SEG_FP64 ? 9 : 8) * vbytes + sizeof(DevCtl) + pbytes + std::max<uint64_t>(8, n * m * 8) + 2 * kMaxCols * 8 +
            std::max<uint64_t>(4, n * 4) + std::max<uint64_t>(4, n);
   return SEG_OK;
 }
@@ -909,7 +913,8 @@ seg_status seg_set_u(seg_state* s, const double* u, int32_t is_device) {
   // by beta = 0: clear them so that values left by a failed run cannot turn
   // into NaN; the solve of the first step starts from x = X (no correction)
   const size_t vbytes = (size_t)s->p->n * s->ms * vsize(s->prec);
-  for (void* b : {s->Y, s->H0, s->H1, s->P0, s->P1, s->Q}) SEG_CUDA(cudaMemsetAsync(b, 0, vbytes, s->stream));
+  for (void* b : {s->Y, s->H0, s->H1, s->H2, s->P0, s->P1, s->Q})
+    if (b) SEG_CUDA(cudaMemsetAsync(b, 0, vbytes, s->stream));
   const int* perm = s->p->perm;
   st = launch_aux(s, s->ks.scatter_in, (long long)s->p->n * s->ms, src, perm);
   if (st != SEG_OK) return st;
@@ -1635,9 +1640,12 @@ seg_status seg_autotune(seg_state* s, int32_t reps, seg_tune_result* out) {
   // Z, P and Q are rewritten by every step before they are read (the first
   // CG pass multiplies the old P by beta = 0, so any finite P will do)
   const size_t vbytes = (size_t)s->p->n * s->ms * vsize(s->prec);
-  void* saved_x = nullptr;  // X, Y, H0, H1
+  void* saved_x = nullptr;  // X, Y and the history slots
   DevCtl* saved_ctl = nullptr;
-  cudaError_t ce = cudaMalloc(&saved_x, 4 * vbytes);
+  std::vector<void*> keep = {s->X, s->Y, s->H0, s->H1};
+  if (s->H2) keep.push_back(s->H2);
+  const size_t nkeep = keep.size();
+  cudaError_t ce = cudaMalloc(&saved_x, nkeep * vbytes);
   if (ce == cudaSuccess) ce = cudaMalloc((void**)&saved_ctl, sizeof(DevCtl));
   if (ce != cudaSuccess) {
     cudaFree(saved_x);
@@ -1647,13 +1655,9 @@ seg_status seg_autotune(seg_state* s, int32_t reps, seg_tune_result* out) {
   int grid0[4];
   for (int w = 0; w < 4; ++w) grid0[w] = s->grid[w];
   const int grid_e0 = s->grid_e;
-  ce = cudaMemcpyAsync(saved_x, s->X, vbytes, cudaMemcpyDeviceToDevice, s->stream);
-  if (ce == cudaSuccess)
-    ce = cudaMemcpyAsync((char*)saved_x + vbytes, s->Y, vbytes, cudaMemcpyDeviceToDevice, s->stream);
-  if (ce == cudaSuccess)
-    ce = cudaMemcpyAsync((char*)saved_x + 2 * vbytes, s->H0, vbytes, cudaMemcpyDeviceToDevice, s->stream);
-  if (ce == cudaSuccess)
-    ce = cudaMemcpyAsync((char*)saved_x + 3 * vbytes, s->H1, vbytes, cudaMemcpyDeviceToDevice, s->stream);
+  ce = cudaSuccess;
+  for (size_t b = 0; b < nkeep && ce == cudaSuccess; ++b)
+    ce = cudaMemcpyAsync((char*)saved_x + b * vbytes, keep[b], vbytes, cudaMemcpyDeviceToDevice, s->stream);
   if (ce == cudaSuccess) ce = cudaMemcpyAsync(saved_ctl, s->ctl, sizeof(DevCtl), cudaMemcpyDeviceToDevice, s->stream);
   if (ce != cudaSuccess) st = fail(SEG_ERR_CUDA, std::string("save: ") + cudaGetErrorString(ce));
   // candidate row grids: 1 .. kRowBlocksPerSM blocks per SM (one wave), and
@@ -1718,13 +1722,9 @@ seg_status seg_autotune(seg_state* s, int32_t reps, seg_tune_result* out) {
     }
   }
   // restore the state's data bitwise
-  ce = cudaMemcpyAsync(s->X, saved_x, vbytes, cudaMemcpyDeviceToDevice, s->stream);
-  if (ce == cudaSuccess)
-    ce = cudaMemcpyAsync(s->Y, (char*)saved_x + vbytes, vbytes, cudaMemcpyDeviceToDevice, s->stream);
-  if (ce == cudaSuccess)
-    ce = cudaMemcpyAsync(s->H0, (char*)saved_x + 2 * vbytes, vbytes, cudaMemcpyDeviceToDevice, s->stream);
-  if (ce == cudaSuccess)
-    ce = cudaMemcpyAsync(s->H1, (char*)saved_x + 3 * vbytes, vbytes, cudaMemcpyDeviceToDevice, s->stream);
+  ce = cudaSuccess;
+  for (size_t b = 0; b < nkeep && ce == cudaSuccess; ++b)
+    ce = cudaMemcpyAsync(keep[b], (char*)saved_x + b * vbytes, vbytes, cudaMemcpyDeviceToDevice, s->stream);
   if (ce == cudaSuccess) ce = cudaMemcpyAsync(s->ctl, saved_ctl, sizeof(DevCtl), cudaMemcpyDeviceToDevice, s->stream);
   for (void* b : {s->Z, s->P0, s->P1, s->Q})
     if (ce == cudaSuccess) ce = cudaMemsetAsync(b, 0, vbytes, s->stream);

@@ -1258,11 +1258,15 @@ __device__ __forceinline__ void body_cg_b(const KArgs<T>& a, const int vb, const
 // (lagged from the last iterations; apply_x, else x = X), then the exact
 // solution of the nodal ODE of step 2 (Jacobi form):
 //   u~ = x * inv_n,  u^_i = u~_i exp(-(2 tau/eps^2) sum_{j != i} u~_j^2)  -> X.
-// With apply_x the next solve's initial correction is predicted by quadratic
-// extrapolation of the last three, Y = 3 y_k - 3 y_{k-1} + y_{k-2}; H0 and H1
-// keep the corrections of the last two solves (step k reads y_{k-1} from
-// H[(k+1) % 2] and y_{k-2} from H[k % 2], then writes y_k over the latter).
-// Any initial guess gives the same solution to the solve's tolerance.
+// With apply_x the next solve's initial correction is predicted by
+// extrapolation of the last corrections: quadratic for float data,
+// Y = 3 y_k - 3 y_{k-1} + y_{k-2}, with H0, H1 keeping the last two (step k
+// reads y_{k-1} from H[(k+1) % 2] and y_{k-2} from H[k % 2], then writes y_k
+// over the latter); cubic for double data, Y = 4 y_k - 6 y_{k-1} + 4 y_{k-2}
+// - y_{k-3}, with H0, H1, H2 keeping the last three (step j's in H[j % 3]).
+// (In float32 the cubic rule's amplification of rounding outweighs its
+// better prediction.)  Any initial guess gives the same solution to the
+// solve's tolerance.
 // The solution updates CG pass A has not applied yet: alpha_k p_k, and
 // alpha_{k-1} p_{k-1} before it (TWO) when the iteration count k is odd.
 template <typename T, int LPR, int RU, bool TWO>
@@ -1272,9 +1276,14 @@ __device__ __forceinline__ void body_finish_rows(const KArgs<T>& a, const int vb
   const int lbase = lane - cg;
   const T* P = (it & 1) ? a.P1 : a.P0;
   const T* P2 = (it & 1) ? a.P0 : a.P1;
-  const bool odd_step = (ctl->step & 1) != 0;
-  const T* Hm1 = odd_step ? a.H0 : a.H1;  // y_{k-1}
-  T* Hm2 = odd_step ? a.H1 : a.H0;        // y_{k-2}, replaced by y_k
+  // history slots of the corrections: two (quadratic prediction) for
+  // float, three (cubic) for double; step j's correction is in H[j % NH]
+  constexpr int NH = sizeof(T) == 8 ? 3 : 2;
+  const int kh = (int)(ctl->step % NH);
+  const T* Hm1 = kh == 0 ? (NH == 3 ? a.H2 : a.H1) : (kh == 1 ? a.H0 : a.H1);  // y_{k-1}
+  const T* Hm2 = NH == 3 ? (kh == 0 ? a.H1 : (kh == 1 ? a.H2 : a.H0)) : (kh == 0 ? a.H0 : a.H1);  // y_{k-2}
+  const T* Hm3 = NH == 3 ? (kh == 0 ? a.H0 : (kh == 1 ? a.H1 : a.H2)) : Hm2;  // y_{k-3} (cubic only)
+  T* Hnew = const_cast<T*>(NH == 3 ? Hm3 : Hm2);  // the oldest, replaced by y_k
   constexpr bool two = TWO;
   const unsigned ms = a.ms;
   T al[VW], al2[VW], invn[VW], ysc[VW];
@@ -1287,13 +1296,15 @@ __device__ __forceinline__ void body_finish_rows(const KArgs<T>& a, const int vb
   }
   const T mcoef = -(T)a.coef;
   for (int base = r0 + warp * RPW * RU; base < r1; base += NW * RPW * RU) {
-    T x[RU][VW], y[RU][VW], h1[RU][VW], h2[RU][VW], p[RU][VW], p2[TWO ? RU : 1][VW];
+    T x[RU][VW], y[RU][VW], h1[RU][VW], h2[RU][VW], h3[NH == 3 ? RU : 1][VW], p[RU][VW],
+        p2[TWO ? RU : 1][VW];
 #pragma unroll
     for (int u = 0; u < RU; ++u) {
       const unsigned row = base + u * RPW + rs;
 #pragma unroll
       for (int v = 0; v < VW; ++v) {
         x[u][v] = y[u][v] = h1[u][v] = h2[u][v] = p[u][v] = T(0);
+        h3[NH == 3 ? u : 0][v] = T(0);
         if (two) p2[u][v] = T(0);
       }
       if ((int)row < r1) {
@@ -1302,6 +1313,7 @@ __device__ __forceinline__ void body_finish_rows(const KArgs<T>& a, const int vb
           ld(y[u], a.Y + (row * ms + c0));
           ld(h1[u], Hm1 + (row * ms + c0));
           ld(h2[u], Hm2 + (row * ms + c0));
+          if (NH == 3) ld(h3[NH == 3 ? u : 0], Hm3 + (row * ms + c0));
           ld_ro(p[u], P + (row * ms + c0));
         }
         if (two) ld_ro(p2[TWO ? u : 0], P2 + (row * ms + c0));
@@ -1318,12 +1330,15 @@ __device__ __forceinline__ void body_finish_rows(const KArgs<T>& a, const int vb
         x[u][v] += y[u][v];
       }
       if (a.apply_x && (int)row < r1) {
-        // the next solve's predicted correction 3 (y_k - y_{k-1}) + y_{k-2}; y_k kept
+        // the next solve's predicted correction, quadratic 3 (y_k - y_{k-1}) + y_{k-2}
+        // or cubic 4 (y_k + y_{k-2}) - 6 y_{k-1} - y_{k-3}; y_k kept
         T g[VW];
 #pragma unroll
-        for (int v = 0; v < VW; ++v) g[v] = fma(T(3), y[u][v] - h1[u][v], h2[u][v]);
+        for (int v = 0; v < VW; ++v)
+          g[v] = NH == 3 ? fma(T(4), y[u][v] + h2[u][v], fma(T(-6), h1[u][v], -h3[NH == 3 ? u : 0][v]))
+                         : fma(T(3), y[u][v] - h1[u][v], h2[u][v]);
         st(a.Y + (row * ms + c0), g);
-        st(Hm2 + (row * ms + c0), y[u]);
+        st(Hnew + (row * ms + c0), y[u]);
       }
       if (a.apply_ode) {
         T sq[1][VW], ex[1][VW], ut[VW];

@@ -81,8 +81,9 @@ struct KArgs {
   const T* diagA;  // diag(A)
   T* X;            // state (the step's right-hand side is M X)
   T* Y;            // CG iterate x = X + y; y starts at a prediction of the step's correction
-  T* H0;           // the corrections y of the last two solves (step k's in H[k % 2])
-  T* H1;
+  T* H0;           // the corrections y of the last two (float) or three (double)
+  T* H1;           // solves, step k's in H[k % 2] or H[k % 3]
+  T* H2;           // (double only)
   T* Z;            // preconditioned residual z = D^-1 r
   T* P0;           // search directions (ping-pong between CG iterations)
   T* P1;
