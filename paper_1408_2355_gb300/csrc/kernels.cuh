@@ -1280,10 +1280,10 @@ __device__ __forceinline__ void body_finish_rows(const KArgs<T>& a, const int vb
   // float, three (cubic) for double; step j's correction is in H[j % NH]
   constexpr int NH = sizeof(T) == 8 ? 3 : 2;
   const int kh = (int)(ctl->step % NH);
-  const T* Hm1 = kh == 0 ? (NH == 3 ? a.H2 : a.H1) : (kh == 1 ? a.H0 : a.H1);  // y_{k-1}
-  const T* Hm2 = NH == 3 ? (kh == 0 ? a.H1 : (kh == 1 ? a.H2 : a.H0)) : (kh == 0 ? a.H0 : a.H1);  // y_{k-2}
-  const T* Hm3 = NH == 3 ? (kh == 0 ? a.H0 : (kh == 1 ? a.H1 : a.H2)) : Hm2;  // y_{k-3} (cubic only)
-  T* Hnew = const_cast<T*>(NH == 3 ? Hm3 : Hm2);  // the oldest, replaced by y_k
+  T* const Hm1 = kh == 0 ? (NH == 3 ? a.H2 : a.H1) : (kh == 1 ? a.H0 : a.H1);  // y_{k-1}
+  T* const Hm2 = NH == 3 ? (kh == 0 ? a.H1 : (kh == 1 ? a.H2 : a.H0)) : (kh == 0 ? a.H0 : a.H1);  // y_{k-2}
+  T* const Hm3 = NH == 3 ? (kh == 0 ? a.H0 : (kh == 1 ? a.H1 : a.H2)) : Hm2;  // y_{k-3} (cubic only)
+  T* const Hnew = NH == 3 ? Hm3 : Hm2;  // the oldest, replaced by y_k
   constexpr bool two = TWO;
   const unsigned ms = a.ms;
   T al[VW], al2[VW], invn[VW], ysc[VW];
