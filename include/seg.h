@@ -368,7 +368,23 @@ seg_status seg_continue(seg_state* coarse, const seg_mesh* coarse_mesh, const se
  * v_i(z) = u_i(z) - sum_{j!=i} u_j(z) > 0 for that i (eq. (vi)), else 0. */
 seg_status seg_labels(seg_state* s, int32_t* argmax, uint8_t* v_positive);
 
+/* Statistics of the state (synchronises its stream). */
 seg_status seg_get_stats(seg_state* s, seg_stats* out);
+
+/* Statistics without waiting for later work: seg_stats_enqueue enqueues on
+ * the state's stream a copy of the statistics as they will be once the work
+ * enqueued so far is done (into one of SEG_STATS_RING pinned slots) and
+ * returns a ticket (>= 0); seg_stats_wait waits for that copy only -- not
+ * for steps enqueued after it -- and fills *out as seg_get_stats would then
+ * have.  A loop that enqueues step k + 1 before it waits for step k's
+ * statistics reads every step's result while the device keeps stepping.  A
+ * ticket stays valid until SEG_STATS_RING more copies have been enqueued
+ * (SEG_ERR_ARG after that, or for a ticket never issued).  Each copy moves
+ * SEG_STATS_COPY_BYTES bytes from the device. */
+#define SEG_STATS_COPY_BYTES 56
+#define SEG_STATS_RING 8
+seg_status seg_stats_enqueue(seg_state* s, int32_t* ticket);
+seg_status seg_stats_wait(seg_state* s, int32_t ticket, seg_stats* out);
 
 /* Thread-local description of the last error of this thread ("" if none). */
 const char* seg_last_error(void);

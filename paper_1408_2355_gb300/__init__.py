@@ -47,7 +47,8 @@ EXPORTED = [
     "seg_mesh_dziuk", "seg_mesh_refine", "seg_mesh_info", "seg_mesh_get", "seg_mesh_destroy", "seg_assemble", "seg_assemble_ex", "seg_problem_info",
     "seg_problem_destroy", "seg_state_create", "seg_state_destroy", "seg_set_u", "seg_get_u",
     "seg_step", "seg_step_async", "seg_sync", "seg_substep", "seg_energy",
-    "seg_eigenvalue_estimates", "seg_energy_p", "seg_prolong", "seg_continue", "seg_labels", "seg_get_stats", "seg_last_error",
+    "seg_eigenvalue_estimates", "seg_energy_p", "seg_prolong", "seg_continue", "seg_labels", "seg_get_stats",
+    "seg_stats_enqueue", "seg_stats_wait", "seg_last_error",
     "seg_time_kernel", "seg_launch_info", "seg_autotune", "seg_s_eps_noalloc",
     "seg_batch_create", "seg_batch_step", "seg_batch_step_async", "seg_batch_sync", "seg_batch_destroy",
     "seg_server_create", "seg_server_submit", "seg_server_tick", "seg_server_info", "seg_server_result",
@@ -163,6 +164,8 @@ _SIG = {
     "seg_continue": [_vp, _vp, _vp, _d, _d, _vp, _pp, _pp, _pp],
     "seg_labels": [_vp, _vp, _vp],
     "seg_get_stats": [_vp, _vp],
+    "seg_stats_enqueue": [_vp, _vp],
+    "seg_stats_wait": [_vp, _i32, _vp],
     "seg_time_kernel": [_vp, _i32, _i32, _vp],
     "seg_launch_info": [_vp, _vp, _vp, _vp, _vp],
     "seg_autotune": [_vp, _i32, _vp],
@@ -543,6 +546,24 @@ def seg_labels(state: State):
 def seg_get_stats(state: State) -> dict:
     st = seg_stats()
     _check(lib.seg_get_stats(state.ptr, C.byref(st)))
+    return {k: getattr(st, k) for k, _ in seg_stats._fields_}
+
+
+SEG_STATS_RING = 8
+SEG_STATS_COPY_BYTES = 56
+
+
+def seg_stats_enqueue(state: State) -> int:
+    """Ticket for the statistics as of the work enqueued so far (no wait)."""
+    t = C.c_int32()
+    _check(lib.seg_stats_enqueue(state.ptr, C.byref(t)))
+    return t.value
+
+
+def seg_stats_wait(state: State, ticket: int) -> dict:
+    """Wait for the copy behind a ticket only; the statistics it holds."""
+    st = seg_stats()
+    _check(lib.seg_stats_wait(state.ptr, ticket, C.byref(st)))
     return {k: getattr(st, k) for k, _ in seg_stats._fields_}
 
 

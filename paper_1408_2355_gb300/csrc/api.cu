@@ -114,6 +114,10 @@ struct seg_state {
   std::vector<std::pair<cudaGraph_t, cudaGraphExec_t>> retired;
   long long* hsnap = nullptr;   // pinned: counters after a chunk of seg_step, 2 slots x (step, cg_total)
   cudaEvent_t snap_ev[2] = {nullptr, nullptr};
+  DevCtl* hring = nullptr;      // pinned: SEG_STATS_RING control-block copies of seg_stats_enqueue
+  cudaEvent_t ring_ev[SEG_STATS_RING] = {};
+  int ring_ticket[SEG_STATS_RING] = {};  // ticket whose copy a slot holds (-1: none)
+  int ring_next = 0;
 };
 
 namespace {
@@ -453,6 +457,9 @@ void free_state(seg_state* s) {
   if (s->hctl) cudaFreeHost(s->hctl);
   if (s->hsnap) cudaFreeHost(s->hsnap);
   for (cudaEvent_t e : s->snap_ev)
+    if (e) cudaEventDestroy(e);
+  if (s->hring) cudaFreeHost(s->hring);
+  for (cudaEvent_t e : s->ring_ev)
     if (e) cudaEventDestroy(e);
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
   delete s;
@@ -819,9 +826,18 @@ seg_status seg_state_create(const seg_problem* p, int32_t m, double eps, seg_ini
   }
   ce = cudaMallocHost((void**)&s->hctl, sizeof(DevCtl));
   if (ce == cudaSuccess) ce = cudaMallocHost((void**)&s->hsnap, 4 * sizeof(long long));
+  if (ce == cudaSuccess) ce = cudaMallocHost((void**)&s->hring, SEG_STATS_RING * sizeof(DevCtl));
   if (ce != cudaSuccess) {
     free_state(s);
     return fail(SEG_ERR_NO_MEMORY, std::string("cudaMallocHost: ") + cudaGetErrorString(ce));
+  }
+  for (int& t : s->ring_ticket) t = -1;
+  for (cudaEvent_t& e : s->ring_ev) {
+    ce = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+    if (ce != cudaSuccess) {
+      free_state(s);
+      return fail(SEG_ERR_CUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(ce));
+    }
   }
   for (cudaEvent_t& e : s->snap_ev) {
     ce = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
@@ -1594,12 +1610,11 @@ seg_status seg_labels(seg_state* s, int32_t* argmax, uint8_t* v_positive) {
   return sync_ctl(s);
 }
 
-seg_status seg_get_stats(seg_state* s, seg_stats* out) {
-  if (!s || !out) return fail(SEG_ERR_ARG, "state or out is NULL");
-  SEG_CUDA(cudaSetDevice(s->p->device));
-  seg_status st = sync_ctl(s);
-  if (st != SEG_OK) return st;
-  const DevCtl& c = *s->hctl;
+}  // extern "C"
+
+namespace {
+
+void stats_of(const seg_state* s, const DevCtl& c, seg_stats* out) {
   out->steps = c.step;
   out->cg_iterations = c.cg_total;
   out->cg_last = c.cg_last;
@@ -1611,6 +1626,41 @@ seg_status seg_get_stats(seg_state* s, seg_stats* out) {
   out->kernel_launches = (int64_t)c.launches;
   out->graph_peel = s->cg_peel;
   out->reserved = 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+seg_status seg_get_stats(seg_state* s, seg_stats* out) {
+  if (!s || !out) return fail(SEG_ERR_ARG, "state or out is NULL");
+  SEG_CUDA(cudaSetDevice(s->p->device));
+  seg_status st = sync_ctl(s);
+  if (st != SEG_OK) return st;
+  stats_of(s, *s->hctl, out);
+  return SEG_OK;
+}
+
+seg_status seg_stats_enqueue(seg_state* s, int32_t* ticket) {
+  if (!s || !ticket) return fail(SEG_ERR_ARG, "state or ticket is NULL");
+  SEG_CUDA(cudaSetDevice(s->p->device));
+  const int t = s->ring_next;
+  const int slot = t % SEG_STATS_RING;
+  SEG_CUDA(cudaMemcpyAsync(s->hring + slot, s->ctl, kCtlStatsBytes, cudaMemcpyDeviceToHost, s->stream));
+  SEG_CUDA(cudaEventRecord(s->ring_ev[slot], s->stream));
+  s->ring_ticket[slot] = t;
+  s->ring_next = t == 0x7fffffff ? 0 : t + 1;
+  *ticket = t;
+  return SEG_OK;
+}
+
+seg_status seg_stats_wait(seg_state* s, int32_t ticket, seg_stats* out) {
+  if (!s || !out) return fail(SEG_ERR_ARG, "state or out is NULL");
+  if (ticket < 0 || s->ring_ticket[ticket % SEG_STATS_RING] != ticket)
+    return fail(SEG_ERR_ARG, "unknown or overwritten statistics ticket");
+  const int slot = ticket % SEG_STATS_RING;
+  SEG_CUDA(cudaEventSynchronize(s->ring_ev[slot]));
+  stats_of(s, s->hring[slot], out);
   return SEG_OK;
 }
 

@@ -92,3 +92,30 @@ def test_predicted_start_cuts_the_iterations(seg):
     again = its(1)
     assert again > late
     assert np.all(np.isfinite(seg.seg_get_u(st)))
+
+
+def test_pipelined_statistics_read_every_step(seg):
+    """seg_stats_enqueue / seg_stats_wait: the statistics of step k read while
+    step k + 1 is queued equal those a synchronous twin reports after step k."""
+    xyz, tri = w.icosphere(4)
+    a = make_state(seg, xyz, tri, 1e-4, 5, 2e-2, 1, 21, check_every=1, energy_tol=-1.0)
+    b = make_state(seg, xyz, tri, 1e-4, 5, 2e-2, 1, 21, check_every=1, energy_tol=-1.0)
+    got, want, tickets = [], [], []
+    for k in range(12):
+        seg.seg_step_async(a, 1)
+        tickets.append(seg.seg_stats_enqueue(a))
+        if k >= 1:
+            got.append(seg.seg_stats_wait(a, tickets[k - 1]))
+        seg.seg_step(b, 1)
+        want.append(seg.seg_get_stats(b))
+    got.append(seg.seg_stats_wait(a, tickets[-1]))
+    assert seg.seg_sync(a) == 12
+    for g, w_ in zip(got, want):
+        for key in ("steps", "cg_iterations", "cg_last", "checks", "last_check_total", "status_bits"):
+            assert g[key] == w_[key], key
+    # a ticket overwritten by SEG_STATS_RING newer copies is refused
+    for _ in range(seg.SEG_STATS_RING):
+        seg.seg_stats_enqueue(a)
+    with pytest.raises(seg.SegError) as e:
+        seg.seg_stats_wait(a, tickets[-1])
+    assert e.value.status == seg.SEG_ERR_ARG
