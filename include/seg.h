@@ -380,8 +380,8 @@ seg_status seg_get_stats(seg_state* s, seg_stats* out);
  * statistics reads every step's result while the device keeps stepping.  A
  * ticket stays valid until SEG_STATS_RING more copies have been enqueued
  * (SEG_ERR_ARG after that, or for a ticket never issued).  Each copy moves
- * SEG_STATS_COPY_BYTES bytes from the device. */
-#define SEG_STATS_COPY_BYTES 56
+ * SEG_STATS_COPY_BYTES bytes (the state's control block) from the device. */
+#define SEG_STATS_COPY_BYTES 2952
 #define SEG_STATS_RING 8
 seg_status seg_stats_enqueue(seg_state* s, int32_t* ticket);
 seg_status seg_stats_wait(seg_state* s, int32_t ticket, seg_stats* out);

@@ -550,7 +550,7 @@ def seg_get_stats(state: State) -> dict:
 
 
 SEG_STATS_RING = 8
-SEG_STATS_COPY_BYTES = 56
+SEG_STATS_COPY_BYTES = 2952
 
 
 def seg_stats_enqueue(state: State) -> int:

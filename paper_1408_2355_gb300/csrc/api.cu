@@ -1646,7 +1646,7 @@ seg_status seg_stats_enqueue(seg_state* s, int32_t* ticket) {
   SEG_CUDA(cudaSetDevice(s->p->device));
   const int t = s->ring_next;
   const int slot = t % SEG_STATS_RING;
-  SEG_CUDA(cudaMemcpyAsync(s->hring + slot, s->ctl, kCtlStatsBytes, cudaMemcpyDeviceToHost, s->stream));
+  SEG_CUDA(cudaMemcpyAsync(s->hring + slot, s->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, s->stream));
   SEG_CUDA(cudaEventRecord(s->ring_ev[slot], s->stream));
   s->ring_ticket[slot] = t;
   s->ring_next = t == 0x7fffffff ? 0 : t + 1;

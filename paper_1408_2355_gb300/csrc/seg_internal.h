@@ -2,7 +2,6 @@
 #pragma once
 
 #include <cuda_runtime.h>
-#include <stddef.h>
 #include <stdint.h>
 
 #include <string>
@@ -35,16 +34,6 @@ enum CounterSlot { kCtrStart = 0, kCtrCgA = 1, kCtrCgB = 2, kCtrEnergy = 3, kCtr
 // thread), read by the following kernels; the host copies it back at sync
 // points.
 struct DevCtl {
-  // what seg_get_stats reports comes first: a copy of this prefix suffices
-  long long step;             // steps completed
-  long long cg_total;         // total CG iterations
-  long long checks;           // stop-rule checks evaluated
-  unsigned long long launches;  // hot-path kernel launches (block 0 counts each)
-  double e_prev;              // total of the previous stop-rule check
-  int cg_last;
-  int cg_max;
-  int halted;                 // 0 running, 1 stop rule met, 2 error
-  int status;                 // bit0: solve hit maxit, bit1: non-finite value, bit2: timeout
   double n2[kMaxCols];        // ||X_i||_M^2 of the stored (un-normalised) components
   double inv_n[kMaxCols];     // scale of the represented state u_i = X_i * inv_n[i]
   double lam[kMaxCols];       // D_i = u_i^T K u_i of the normalised state
@@ -58,17 +47,25 @@ struct DevCtl {
   double ysc[kMaxCols];       // scale (1 or 0) of the carried correction in the current solve
   int it;                     // CG iterations completed in the current solve
   int cont;                   // loop-continue flag (mirrors the graph conditional)
+  int halted;                 // 0 running, 1 stop rule met, 2 error
+  int status;                 // bit0: solve hit maxit, bit1: non-finite value, bit2: timeout
+  long long step;             // steps completed
+  long long cg_total;         // total CG iterations
+  int cg_last;
+  int cg_max;
+  long long checks;           // stop-rule checks evaluated
   double e_total;             // last energy evaluation: sum D + S_eps
   double e_dir;
   double e_s;
+  double e_prev;              // total of the previous stop-rule check
   int have_prev;
   int pad0;
   long long step_mark;        // ctl->step when the last batch of steps was enqueued
+  unsigned long long launches;  // hot-path kernel launches (block 0 counts each)
   unsigned int counters[kNumCounters];
 };
-// Bytes of the DevCtl prefix that seg_get_stats reads.
-constexpr size_t kCtlStatsBytes = offsetof(DevCtl, n2);
-static_assert(kCtlStatsBytes == SEG_STATS_COPY_BYTES, "statistics prefix of the control block");
+// seg_stats_enqueue copies the whole control block.
+static_assert(sizeof(DevCtl) == SEG_STATS_COPY_BYTES, "size of the control block");
 
 // Arguments of every hot-path kernel (passed by value; identical struct for
 // all kernels of a state so that one graph node layout fits all).
