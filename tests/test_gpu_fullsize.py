@@ -76,3 +76,34 @@ def test_level8_m16_mixed_bench_configuration(seg):
     check_labels(seg, st, tri, U, Ug)
     stats = seg.seg_get_stats(st)
     assert stats["status_bits"] == 0 and stats["checks"] == steps
+
+
+def test_level7_m16_bench_regime_with_predicted_start(seg):
+    """The bench's regime one level coarser (tau / h^2 and 2 tau / eps^2 as at
+    level 8: tau = 2e-5, eps = 2e-3), m = 16, float64 and mixed precision, 40
+    steps: long enough for the solves to start from the predicted
+    correction, which the oracle (exact solves from u^k) does not use -- the
+    results agree to the parity tolerances all the same."""
+    xyz, tri = w.icosphere(7)
+    M, K = o.assemble(xyz, tri)
+    m, tau, eps, seed, steps = 16, 2e-5, 2e-3, 1237, 40
+    U = o.initial_state(M, w.uniform01(seed, xyz.shape[0], m))
+    for _ in range(steps):
+        U = o.step(M, K, tau, eps, U)
+    eo = o.energy(xyz, tri, K, U, eps)
+    for prec, utol, etol in ((0, 1e-9, 1e-10), (1, 1e-4, 1e-5)):
+        st = make_state(seg, xyz, tri, tau, m, eps, prec, seed=seed, check_every=1, energy_tol=-1.0)
+        its = []
+        for _ in range(steps):
+            c0 = seg.seg_get_stats(st)["cg_iterations"]
+            assert seg.seg_step(st, 1) == 1
+            its.append(seg.seg_get_stats(st)["cg_iterations"] - c0)
+        # the predicted start is in use by now: fewer iterations than at first
+        assert np.mean(its[-10:]) < 0.75 * np.mean(its[:5]), (prec, its)
+        Ug = seg.seg_get_u(st)
+        assert np.abs(Ug - U).max() <= utol * np.abs(U).max(), prec
+        e = seg.seg_energy(st)
+        assert rel(e["total"], eo["total"]) <= etol, (prec, e["total"], eo["total"])
+        lam, _ = seg.seg_eigenvalue_estimates(st)
+        assert np.abs(lam - eo["D"]).max() <= etol * np.abs(eo["D"]).max(), prec
+        check_labels(seg, st, tri, U, Ug)
