@@ -146,17 +146,51 @@ __device__ __forceinline__ void shfl_add(AccD& a, int off) { a.v += __shfl_xor_s
 __device__ __forceinline__ void zero_part(float2& p) { p = make_float2(0.f, 0.f); }
 __device__ __forceinline__ void zero_part(double& p) { p = 0.0; }
 
+// The grid sums of reduce_blocks: warp w takes sums w, w + NW, ... S at a
+// time; lane l adds blocks l, l + 32, ... in order (S x UL loads in flight),
+// then a fixed shuffle tree; out(p, total) is called from lane 0.
+template <int S, int UL, typename Acc, typename Part, typename Out>
+__device__ __forceinline__ void sum_partials(const Part* part, int P, int G, int lane, int warp, Out& out) {
+  constexpr int NW = kBlockThreads / 32;
+  for (int p0 = warp; p0 < P; p0 += S * NW) {
+    Acc s[S];
+#pragma unroll
+    for (int j = 0; j < S; ++j) s[j].zero();
+    for (int b0 = 0; b0 < G; b0 += 32 * UL) {
+      Part v[S][UL];
+#pragma unroll
+      for (int j = 0; j < S; ++j)
+#pragma unroll
+        for (int u = 0; u < UL; ++u) {
+          const int b = b0 + u * 32 + lane, p = p0 + j * NW;
+          zero_part(v[j][u]);
+          if (b < G && p < P) v[j][u] = __ldcg(&part[(size_t)p * G + b]);
+        }
+#pragma unroll
+      for (int j = 0; j < S; ++j)
+#pragma unroll
+        for (int u = 0; u < UL; ++u) add_part(s[j], v[j][u]);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+      for (int j = 0; j < S; ++j) shfl_add(s[j], off);
+    if (lane == 0)
+#pragma unroll
+      for (int j = 0; j < S; ++j)
+        if (p0 + j * NW < P) out(p0 + j * NW, s[j].value());
+  }
+}
+
 // Deterministic sum over the G blocks of a grid of P partial sums:
 // part[p * G + b] holds block b's partial of sum p (every block has written
-// its own before the call).  The last block to arrive (ticket) sums them:
-// warp w takes sums w, w + NW, ... two at a time; lane l adds blocks l,
-// l + 32, ... in order (up to 2 x 10 loads in flight), then a fixed shuffle
-// tree; out(p, total) is called from lane 0.  Returns true in that block
-// only.  Must be reached by every block of the grid.
+// its own before the call).  The last block to arrive (ticket) sums them
+// (sum_partials: two sums per warp at a time with 10 loads per lane each, or
+// four with 5 when the grid has at most 160 blocks -- the same additions in
+// the same order, the absent blocks' loads being zeros either way).  Returns
+// true in that block only.  Must be reached by every block of the grid.
 template <typename Acc, typename Part, typename Out>
 __device__ __forceinline__ bool reduce_blocks(const Part* part, unsigned int* count, int P, int vb, int G, Out out) {
-  constexpr int NW = kBlockThreads / 32;
-  constexpr int U = 10;  // loads per lane and sum in flight (one pass covers 320 blocks)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   __shared__ unsigned int ticket;
   (void)vb;
@@ -166,39 +200,10 @@ __device__ __forceinline__ bool reduce_blocks(const Part* part, unsigned int* co
   __syncthreads();
   if (ticket != (unsigned int)(G - 1)) return false;
   __threadfence();
-  for (int p = warp; p < P; p += 2 * NW) {
-    const int q = p + NW;  // second sum of this pass (if any)
-    Acc s0, s1;
-    s0.zero();
-    s1.zero();
-    for (int b0 = 0; b0 < G; b0 += 32 * U) {
-      Part v0[U], v1[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int b = b0 + u * 32 + lane;
-        zero_part(v0[u]);
-        zero_part(v1[u]);
-        if (b < G) {
-          v0[u] = __ldcg(&part[(size_t)p * G + b]);
-          if (q < P) v1[u] = __ldcg(&part[(size_t)q * G + b]);
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        add_part(s0, v0[u]);
-        add_part(s1, v1[u]);
-      }
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      shfl_add(s0, off);
-      shfl_add(s1, off);
-    }
-    if (lane == 0) {
-      out(p, s0.value());
-      if (q < P) out(q, s1.value());
-    }
-  }
+  if (G <= 32 * 5)
+    sum_partials<4, 5, Acc>(part, P, G, lane, warp, out);
+  else
+    sum_partials<2, 10, Acc>(part, P, G, lane, warp, out);
   __syncthreads();
   if (threadIdx.x == 0) *count = 0u;
   return true;
