@@ -632,10 +632,10 @@ using CgAStage = RowStage<T, LPR, W, 1, XUP ? 5 : 3>;
 
 // Start pass of the CG solve of step 1, (M + tau K) x = M X, fused with the
 // renormalisation of the previous step.  The iterate is x = X + y, with y
-// starting at w Y: Y holds the correction x - X the previous step's solve
-// ended with (a prediction of this step's correction; 0 after a state is
-// set) and w (per component, 0 or 1) says whether the last start pass found
-// that prediction better than none:
+// starting at w Y: Y holds this step's correction as the finish pass of the
+// previous step predicted it from the last solves' corrections (0 after a
+// state is set) and w (per component, 0 or 1) says whether the last start
+// pass found the prediction better than none:
 //   r0 = M X - (M + tau K)(X + w Y) = -tau K X - w A Y,  z0 = D^-1 r0  -> Z,
 // per component  ||X||_M^2, X^T K X, r0.z0  (float-float) and, in float32 per
 // thread (they only set the tolerance and the choice of w), ||M X||_2^2 and
@@ -659,7 +659,7 @@ __device__ __forceinline__ void body_start(const KArgs<T>& a, const int vb, cons
 #pragma unroll
     for (int v = 0; v < VW; ++v) acc[d][v].zero();
   T pl[3][VW];  // ||M X||^2, ||-tau K X||^2, ||-tau K X - A Y||^2
-  unsigned om = 0;  // bit v: this lane's component c0 + v starts from the carried correction
+  unsigned om = 0;  // bit v: this lane's component c0 + v starts from the predicted correction
 #pragma unroll
   for (int v = 0; v < VW; ++v) {
     pl[0][v] = pl[1][v] = pl[2][v] = T(0);

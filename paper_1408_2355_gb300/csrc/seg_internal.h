@@ -43,8 +43,8 @@ struct DevCtl {
   double beta[kMaxCols];      // CG direction update factor
   double coup[kMaxCols];      // int u_i^2 sum_{j != i} u_j^2 (normalised state)
   int active[kMaxCols];       // component still iterating in the current solve
-  int carry[kMaxCols];        // the next solve starts from the carried correction y (else from y = 0)
-  double ysc[kMaxCols];       // scale (1 or 0) of the carried correction in the current solve
+  int carry[kMaxCols];        // the next solve starts from the predicted correction in Y (else from y = 0)
+  double ysc[kMaxCols];       // scale (1 or 0) of the predicted correction in the current solve
   int it;                     // CG iterations completed in the current solve
   int cont;                   // loop-continue flag (mirrors the graph conditional)
   int halted;                 // 0 running, 1 stop rule met, 2 error
