@@ -32,12 +32,12 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 HBM_FALLBACK_GBS = 6800.0
-# DRAM bytes (read + write) per launch from the ncu captures summarised in
-# profiles/k_cg_a_sphere_L8_m16_mixed.md (k_cg_a: the mean of one launch of its
-# even and one of its odd form) and profiles/other_passes_sphere_L8_m16_mixed.md
-# (level-8 sphere, m = 16, mixed); valid for that workload and those versions
-# of the kernels only.  k_finish was captured in its even form only.
-TRAFFIC = {"k_cg_a": 270.6e6, "k_start": 200.2e6, "k_cg_b": 93.3e6, "k_energy_check": 63.3e6, "k_finish": None}
+# DRAM bytes (read + write) per launch from the ncu capture summarised in
+# profiles/traffic_sphere_L8_m16_mixed.md (level-8 sphere, m = 16, mixed; k_cg_a:
+# the mean of its even and odd forms, k_cg_b: the mean of five launches); valid
+# for that workload and those versions of the kernels only.  k_finish was
+# captured in its even form only.
+TRAFFIC = {"k_cg_a": 272.7e6, "k_start": 194.7e6, "k_cg_b": 91.6e6, "k_energy_check": 63.0e6, "k_finish": None}
 KERNEL_ROLE = {
     "k_start": "start pass: r0 = -tau K X - A y for the predicted correction y, z0 = D^-1 r0, norms "
                "(issue and latency bound: three sparse products and three float-float sums per row)",
