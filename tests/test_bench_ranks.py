@@ -79,3 +79,26 @@ def test_reference_arm_under_two_ranks_prints_once():
     lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
     assert len(lines) == 1
     _check_reference_line(lines[0])
+
+
+def test_kernel_byte_model_matches_the_design_table():
+    """The algorithmic bytes per launch that bench.py divides by the measured
+    times (level-8 sphere, m = 16, float32, ELL width 8): V = N * 16 * 4."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    n, ntri = 655362, 1310720
+    kb = bench.kernel_bytes(n, ntri, 16, 4)
+    V = n * 16 * 4
+    ell = n * 8 * 4
+    assert kb["k_start"] == 3 * V + ell + 3 * n * 8 * 4 + n * 4
+    assert kb["k_cg_a_even"] == 5 * V + ell + n * 8 * 4
+    assert kb["k_cg_a_odd"] == 8 * V + ell + n * 8 * 4
+    assert kb["k_cg_b"] == 3 * V + 2 * n * 4
+    assert (kb["k_finish_even"], kb["k_finish_odd"]) == (8 * V, 9 * V)
+    assert kb["k_energy_check"] == V + ntri * 16
+    # the figures quoted in the design notes, MB
+    quoted = {"k_start": 212.3, "k_cg_a_even": 251.7, "k_cg_a_odd": 377.5, "k_cg_b": 131.1,
+              "k_finish_even": 335.5, "k_energy_check": 62.9}
+    for k, mb in quoted.items():
+        assert abs(kb[k] / 1e6 - mb) < 0.06, (k, kb[k] / 1e6)
