@@ -136,3 +136,21 @@ def test_planted_mistakes_in_the_variants_fail_their_pins(monkeypatch):
     wrong = float(np.sum(lam ** 2) ** 0.5)
     assert abs(o.energy_p(lam, 2) - math.sqrt((lam ** 2).mean())) < 1e-14
     assert abs(wrong - math.sqrt((lam ** 2).mean())) > 1.0
+
+
+def test_functional_without_the_half_is_caught():
+    """A functional with the 1/2 of Problem 2.1 dropped fails its pins."""
+    from tests.test_oracle_pins import functional_pin_errors
+
+    xyz, tri = w.icosphere(3)
+    M, K = o.assemble(xyz, tri)
+
+    def no_half(xyz, tri, K, U, eps):
+        e = o.energy(xyz, tri, K, U, eps)
+        e["functional"] = e["dirichlet"] + e["s_eps"]
+        return e
+
+    good_a, good_b = functional_pin_errors(o.energy, xyz, tri, M, K)
+    bad_a, bad_b = functional_pin_errors(no_half, xyz, tri, M, K)
+    assert good_a < 1e-13 and good_b < 1e-12
+    assert bad_a > 0.1 and bad_b > 0.4

@@ -266,6 +266,34 @@ def test_lambda_formula_sums_to_dirichlet_plus_twice_s_eps(sph3):
     assert e["functional"] <= lam.sum()
 
 
+def functional_pin_errors(energy_fn, xyz, tri, M, K):
+    """Relative errors of the functional of Problem 2.1 against two things
+    that fix it: (a) half the sum of the eigenvalue estimates of Sec. 1.1
+    (summing lambda_i over i gives sum D_i + 2 S_eps, which is twice
+    E^{eps,h} = 0.5 sum D_i + S_eps exactly); (b) for m = 1 (no coupling,
+    S_eps = 0) and u an M-normalised generalised eigenvector K v = lambda M v
+    from LAPACK, E^{eps,h} = lambda / 2 and the total energy = lambda."""
+    U = o.initial_state(M, w.uniform01(8, xyz.shape[0], 4))
+    eps = 0.3
+    e = energy_fn(xyz, tri, K, U, eps)
+    lam = o.lambda_cl(xyz, tri, K, U, eps)
+    err_a = abs(e["functional"] - 0.5 * lam.sum()) / (0.5 * lam.sum())
+    ev, V = sla.eigh(K.toarray(), M.toarray())
+    err_b = 0.0
+    for k in (1, 4, 9):  # eigenvalues near l(l+1) = 2, 6, 12
+        v = V[:, k:k + 1]
+        e1 = energy_fn(xyz, tri, K, v, eps)
+        err_b = max(err_b, abs(e1["functional"] - 0.5 * ev[k]) / ev[k], abs(e1["total"] - ev[k]) / ev[k])
+    return err_a, err_b
+
+
+def test_functional_is_half_the_eigenvalue_sum_and_half_an_eigenvalue(sph3):
+    xyz, tri, M, K = sph3
+    err_a, err_b = functional_pin_errors(o.energy, xyz, tri, M, K)
+    assert err_a < 1e-13
+    assert err_b < 1e-12
+
+
 def test_table_u_eps_first_row():
     """Flow at eps = 0.5 from random one-hot data reaches the printed energy and S_eps."""
     g = _golden("table_u_eps_row1.txt")
