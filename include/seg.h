@@ -90,6 +90,10 @@ typedef struct {
   int32_t reserved;      /* must be 0 */
   int64_t max_steps;     /* the state stops for good after this many steps (0: no limit); unlike
                             seg_step's nsteps this also holds inside batches and the server */
+  int64_t wait_limit_ns; /* limit of each bounded device wait for data staged by the bulk-copy
+                            engine (0: 1 s).  A wait that runs out records SEG_ERR_TIMEOUT and
+                            halts the run; the copies still in flight are then waited for with
+                            the 1 s limit before the kernel returns */
 } seg_params;
 
 typedef struct {
@@ -213,8 +217,35 @@ void seg_state_destroy(seg_state* s);
 seg_status seg_set_u(seg_state* s, const double* u, int32_t is_device);
 
 /* Write the current normalised state u[n_vert*m] (float64, caller's vertex
- * order) to host memory, or device memory if is_device != 0. */
+ * order) to host memory, or device memory if is_device != 0.  Reading the
+ * state (this call, seg_energy, seg_eigenvalue_estimates, seg_labels) does not
+ * change the steps that follow. */
 seg_status seg_get_u(seg_state* s, double* u, int32_t is_device);
+
+/* Checkpoint and resume (no counterpart in the paper).  A checkpoint holds
+ * everything the next step of Algorithm 2.2 reads: the stored state X and its
+ * normalisation, the predicted correction of the next solve and the
+ * corrections of the last solves it is extrapolated from, the choice of start
+ * per component, the stop rule's previous energy and every counter -- in the
+ * state's internal vertex order and precision.  seg_set_checkpoint restores it
+ * into a state created on the same mesh (the same problem or one assembled
+ * from the same mesh, tau and precision) with the same m and eps; the steps
+ * that follow are then bitwise those of the run the checkpoint was taken
+ * from, provided the restoring state has the same launch geometry
+ * (seg_launch_info; the per-block partial sums are added in that order).
+ * buf is host memory of seg_checkpoint_size bytes, owned by the caller.
+ * seg_get_checkpoint synchronises the state's stream; SEG_ERR_ARG for a
+ * buffer too small, a checkpoint of another size, precision, m or eps, or
+ * one that is damaged (magic and version are checked). */
+seg_status seg_checkpoint_size(seg_state* s, uint64_t* bytes);
+seg_status seg_get_checkpoint(seg_state* s, void* buf, uint64_t bytes);
+seg_status seg_set_checkpoint(seg_state* s, const void* buf, uint64_t bytes);
+
+/* Change the limit of the bounded device waits of a state (see
+ * seg_params.wait_limit_ns; ns <= 0 restores the 1 s default).  Takes effect
+ * at the next step; a batch built from the state earlier keeps the limit it
+ * was built with. */
+seg_status seg_set_wait_limit(seg_state* s, int64_t ns);
 
 /* ------------------------------------------------------------------- steps */
 

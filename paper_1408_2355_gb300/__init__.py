@@ -53,6 +53,7 @@ EXPORTED = [
     "seg_batch_create", "seg_batch_step", "seg_batch_step_async", "seg_batch_sync", "seg_batch_destroy",
     "seg_server_create", "seg_server_submit", "seg_server_tick", "seg_server_info", "seg_server_result",
     "seg_server_clock", "seg_server_destroy", "seg_state_bytes",
+    "seg_checkpoint_size", "seg_get_checkpoint", "seg_set_checkpoint", "seg_set_wait_limit",
 ]
 
 
@@ -72,6 +73,7 @@ class seg_params(C.Structure):
         ("launch_mode", C.c_int32),
         ("reserved", C.c_int32),
         ("max_steps", C.c_int64),
+        ("wait_limit_ns", C.c_int64),
     ]
 
 
@@ -180,6 +182,10 @@ _SIG = {
     "seg_server_info": [_vp, _i64, _vp],
     "seg_server_result": [_vp, _i64, _vp],
     "seg_state_bytes": [_vp, _i32, _vp],
+    "seg_checkpoint_size": [_vp, _vp],
+    "seg_get_checkpoint": [_vp, _vp, C.c_uint64],
+    "seg_set_checkpoint": [_vp, _vp, C.c_uint64],
+    "seg_set_wait_limit": [_vp, _i64],
 }
 for _name, _args in _SIG.items():
     _f = getattr(lib, _name)
@@ -389,6 +395,28 @@ def seg_get_u(state: State, out=None, is_device: bool = False):
     return out
 
 
+def seg_checkpoint_size(state: State) -> int:
+    b = C.c_uint64()
+    _check(lib.seg_checkpoint_size(state.ptr, C.byref(b)))
+    return b.value
+
+
+def seg_get_checkpoint(state: State) -> np.ndarray:
+    """The state's checkpoint as a host byte array (see include/seg.h)."""
+    buf = np.empty(seg_checkpoint_size(state), dtype=np.uint8)
+    _check(lib.seg_get_checkpoint(state.ptr, _ptr(buf), buf.nbytes))
+    return buf
+
+
+def seg_set_checkpoint(state: State, buf):
+    buf = np.ascontiguousarray(buf, dtype=np.uint8)
+    _check(lib.seg_set_checkpoint(state.ptr, _ptr(buf), buf.nbytes))
+
+
+def seg_set_wait_limit(state: State, ns: int):
+    _check(lib.seg_set_wait_limit(state.ptr, int(ns)))
+
+
 def seg_step(state: State, nsteps: int, ok_not_converged: bool = False) -> int:
     done = C.c_int64()
     ok = (SEG_OK, SEG_ERR_NOT_CONVERGED) if ok_not_converged else (SEG_OK,)
@@ -590,13 +618,52 @@ def seg_autotune(state: State, reps: int = 10) -> dict:
                           "finish": r.grid_pass[3]}}
 
 
+def _noalloc_args(u, xyz, tri, out):
+    """Checks of seg_s_eps_noalloc's arguments, before anything reaches the
+    library (which sees only raw device addresses): every array a contiguous
+    torch CUDA tensor on the current device with the dtype and shape the C
+    entry point reads.  Raises SegError(SEG_ERR_ARG) otherwise."""
+    import torch
+
+    def bad(msg):
+        raise SegError(SEG_ERR_ARG, "seg_s_eps_noalloc: " + msg)
+
+    named = (("u", u, torch.float64), ("xyz", xyz, torch.float64), ("tri", tri, torch.int32),
+             ("out", out, torch.float64))
+    for name, t, dt in named:
+        if not isinstance(t, torch.Tensor):
+            bad(f"{name} must be a torch tensor (device memory), not {type(t).__name__}")
+        if t.dtype != dt:
+            bad(f"{name} must be {dt}, not {t.dtype}")
+        if not t.is_contiguous():
+            bad(f"{name} must be contiguous")
+    if u.ndim != 2:
+        bad("u must be (n_vert, m)")
+    n_vert, m = int(u.shape[0]), int(u.shape[1])
+    if tuple(xyz.shape) != (n_vert, 3):
+        bad(f"xyz must be ({n_vert}, 3)")
+    if tri.ndim != 2 or tri.shape[1] != 3:
+        bad("tri must be (n_tri, 3)")
+    if out.numel() < m + 1:
+        bad(f"out must hold m + 1 = {m + 1} values")
+    for name, t, _ in named:
+        if not t.is_cuda:
+            bad(f"{name} must be a CUDA tensor")
+    dev = torch.cuda.current_device()
+    for name, t, _ in named:
+        if t.device.index != dev:
+            bad(f"{name} is on cuda:{t.device.index}, the current device is cuda:{dev}")
+    return n_vert, m, int(tri.shape[0])
+
+
 def seg_s_eps_noalloc(u, xyz, tri, eps: float, out, cuda_stream: int | None = None):
     """Allocation-free S_eps and coupling integrals (see include/seg.h).
 
     u (n_vert x m float64), xyz (n_vert x 3 float64), tri (n_tri x 3 int32)
-    and out (m + 1 float64) are caller-owned CUDA tensors on the current
-    device; the call only enqueues work on cuda_stream and returns.
+    and out (m + 1 float64) are caller-owned contiguous CUDA tensors on the
+    current device (checked); the call only enqueues work on cuda_stream and
+    returns.
     """
-    n_vert, m = int(u.shape[0]), int(u.shape[1])
-    _check(lib.seg_s_eps_noalloc(_ptr(u), n_vert, m, _ptr(xyz), _ptr(tri), int(tri.shape[0]), eps, _ptr(out),
+    n_vert, m, n_tri = _noalloc_args(u, xyz, tri, out)
+    _check(lib.seg_s_eps_noalloc(_ptr(u), n_vert, m, _ptr(xyz), _ptr(tri), n_tri, eps, _ptr(out),
                                  C.c_void_p(cuda_stream) if cuda_stream else None))

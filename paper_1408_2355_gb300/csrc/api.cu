@@ -75,6 +75,7 @@ struct seg_state {
   long long check_every = 0;
   double energy_tol = 0;
   long long max_steps = 0;
+  unsigned long long wait_ns = kDefaultWaitNs;  // limit of one bounded device wait
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int launch_mode = 0;
@@ -149,7 +150,7 @@ template <>
 KArgs<double>& args_of<double>(seg_state* s) { return s->ad; }
 
 struct Launch {
-  int set_cond = 0, force = 0, apply_x = 0, apply_ode = 0, count_step = 0, ignore_halt = 1;
+  int set_cond = 0, force = 0, apply_x = 0, apply_ode = 0, count_step = 0, ignore_halt = 1, norm_only = 0;
 };
 
 template <typename T>
@@ -162,6 +163,7 @@ KArgs<T> make_args(seg_state* s, const Launch& l) {
   a.apply_ode = l.apply_ode;
   a.count_step = l.count_step;
   a.ignore_halt = l.ignore_halt;
+  a.norm_only = l.norm_only;
   return a;
 }
 
@@ -225,10 +227,14 @@ seg_status sync_ctl(seg_state* s) {
 }
 
 // Recompute the normalisation factors of the stored state if needed (fused
-// Algorithm 2.2 step 3 of the previous step / of freshly set data).
+// Algorithm 2.2 step 3 of the previous step / of freshly set data).  The
+// start pass runs in its norm-only form: the solver's state for the next
+// step is left as it is, so reading the state does not change the run.
 seg_status ensure_norm(seg_state* s) {
   if (!s->pending) return SEG_OK;
-  seg_status st = launch_row(s, s->ks.start, Launch());
+  Launch l;
+  l.norm_only = 1;
+  seg_status st = launch_row(s, s->ks.start, l);
   if (st != SEG_OK) return st;
   s->pending = false;
   return SEG_OK;
@@ -403,6 +409,7 @@ void fill_args(seg_state* s) {
   a.check_every = s->check_every;
   a.energy_tol = s->energy_tol;
   a.max_steps = s->max_steps;
+  a.wait_ns = s->wait_ns;
 }
 
 template <typename T>
@@ -732,6 +739,7 @@ seg_status seg_state_create(const seg_problem* p, int32_t m, double eps, seg_ini
                                        : (prm.check_every < 0 ? 0 : std::max<long long>(1, std::llround(0.1 / p->tau)));
   s->energy_tol = prm.energy_tol > 0 ? prm.energy_tol : (prm.energy_tol < 0 ? -1.0 : 1e-6);
   s->max_steps = prm.max_steps > 0 ? prm.max_steps : 0;
+  s->wait_ns = prm.wait_limit_ns > 0 ? (unsigned long long)prm.wait_limit_ns : kDefaultWaitNs;
   if (prm.launch_mode != 0 && prm.launch_mode != 1) {
     delete s;
     return fail(SEG_ERR_ARG, "launch_mode must be 0 (graph) or 1 (direct)");
@@ -953,6 +961,136 @@ seg_status seg_get_u(seg_state* s, double* u, int32_t is_device) {
   st = sync_ctl(s);
   if (st != SEG_OK) return st;
   return (s->hctl->status & 2) ? status_from_ctl(*s->hctl) : SEG_OK;
+}
+
+// ------------------------------------------------------- checkpoint / resume
+
+}  // extern "C"
+
+namespace {
+
+// Layout of a checkpoint: this header, the control block, then the state's
+// vectors X, Y, H0, H1 (and H2 for float64 states) in internal row order.
+struct CkptHeader {
+  char magic[8];       // "SEGCKPT"
+  int32_t version;     // kCkptVersion
+  int32_t prec;        // seg_precision
+  int64_t n;           // vertex rows
+  int32_t m, ms;       // components, padded components
+  double eps, tau;
+  int32_t nvec;        // state-sized vectors after the control block
+  int32_t pending;     // the normalisation of X is to be recomputed before it is read
+  uint64_t vec_bytes;  // bytes of one vector
+  uint64_t ctl_bytes;  // bytes of the control block
+};
+constexpr int32_t kCkptVersion = 1;
+const char kCkptMagic[8] = {'S', 'E', 'G', 'C', 'K', 'P', 'T', 0};
+
+int ckpt_vectors(const seg_state* s, void* const** out) {
+  static thread_local void* v[5];
+  v[0] = s->X;
+  v[1] = s->Y;
+  v[2] = s->H0;
+  v[3] = s->H1;
+  v[4] = s->H2;
+  *out = v;
+  return s->prec == SEG_FP64 ? 5 : 4;
+}
+
+uint64_t ckpt_bytes(const seg_state* s) {
+  void* const* v;
+  const int nv = ckpt_vectors(s, &v);
+  return sizeof(CkptHeader) + sizeof(DevCtl) + (uint64_t)nv * (uint64_t)s->p->n * s->ms * vsize(s->prec);
+}
+
+}  // namespace
+
+extern "C" {
+
+seg_status seg_checkpoint_size(seg_state* s, uint64_t* bytes) {
+  if (!s || !bytes) return fail(SEG_ERR_ARG, "state or bytes is NULL");
+  *bytes = ckpt_bytes(s);
+  return SEG_OK;
+}
+
+seg_status seg_get_checkpoint(seg_state* s, void* buf, uint64_t bytes) {
+  if (!s || !buf) return fail(SEG_ERR_ARG, "state or buffer is NULL");
+  if (bytes < ckpt_bytes(s)) return fail(SEG_ERR_ARG, "checkpoint buffer smaller than seg_checkpoint_size");
+  SEG_CUDA(cudaSetDevice(s->p->device));
+  SEG_CUDA(cudaStreamSynchronize(s->stream));
+  void* const* v;
+  const int nv = ckpt_vectors(s, &v);
+  CkptHeader h{};
+  std::memcpy(h.magic, kCkptMagic, sizeof(h.magic));
+  h.version = kCkptVersion;
+  h.prec = (int32_t)s->prec;
+  h.n = s->p->n;
+  h.m = s->m;
+  h.ms = s->ms;
+  h.eps = s->eps;
+  h.tau = s->p->tau;
+  h.nvec = nv;
+  h.pending = s->pending ? 1 : 0;
+  h.vec_bytes = (uint64_t)s->p->n * s->ms * vsize(s->prec);
+  h.ctl_bytes = sizeof(DevCtl);
+  unsigned char* out = static_cast<unsigned char*>(buf);
+  std::memcpy(out, &h, sizeof(h));
+  out += sizeof(h);
+  SEG_CUDA(cudaMemcpyAsync(out, s->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, s->stream));
+  out += sizeof(DevCtl);
+  for (int k = 0; k < nv; ++k) {
+    SEG_CUDA(cudaMemcpyAsync(out, v[k], h.vec_bytes, cudaMemcpyDeviceToHost, s->stream));
+    out += h.vec_bytes;
+  }
+  SEG_CUDA(cudaStreamSynchronize(s->stream));
+  return SEG_OK;
+}
+
+seg_status seg_set_checkpoint(seg_state* s, const void* buf, uint64_t bytes) {
+  if (!s || !buf) return fail(SEG_ERR_ARG, "state or buffer is NULL");
+  if (bytes < sizeof(CkptHeader)) return fail(SEG_ERR_ARG, "checkpoint shorter than its header");
+  CkptHeader h;
+  const unsigned char* in = static_cast<const unsigned char*>(buf);
+  std::memcpy(&h, in, sizeof(h));
+  void* const* v;
+  const int nv = ckpt_vectors(s, &v);
+  const uint64_t vb = (uint64_t)s->p->n * s->ms * vsize(s->prec);
+  if (std::memcmp(h.magic, kCkptMagic, sizeof(h.magic)) != 0 || h.version != kCkptVersion)
+    return fail(SEG_ERR_ARG, "not a checkpoint of this library version");
+  if (h.prec != (int32_t)s->prec || h.n != s->p->n || h.m != s->m || h.ms != s->ms || h.nvec != nv ||
+      h.vec_bytes != vb || h.ctl_bytes != sizeof(DevCtl))
+    return fail(SEG_ERR_ARG, "checkpoint of another mesh size, m or precision");
+  if (h.eps != s->eps || h.tau != s->p->tau) return fail(SEG_ERR_ARG, "checkpoint of another eps or tau");
+  if (bytes < ckpt_bytes(s)) return fail(SEG_ERR_ARG, "checkpoint buffer shorter than its contents");
+  SEG_CUDA(cudaSetDevice(s->p->device));
+  SEG_CUDA(cudaStreamSynchronize(s->stream));
+  in += sizeof(h);
+  DevCtl c;
+  std::memcpy(&c, in, sizeof(DevCtl));
+  in += sizeof(DevCtl);
+  for (unsigned int& t : c.counters) t = 0u;  // tickets are zero between launches
+  std::memcpy(s->hctl, &c, sizeof(DevCtl));
+  SEG_CUDA(cudaMemcpyAsync(s->ctl, s->hctl, sizeof(DevCtl), cudaMemcpyHostToDevice, s->stream));
+  for (int k = 0; k < nv; ++k) {
+    SEG_CUDA(cudaMemcpyAsync(v[k], in, vb, cudaMemcpyHostToDevice, s->stream));
+    in += vb;
+  }
+  SEG_CUDA(cudaStreamSynchronize(s->stream));
+  s->pending = h.pending != 0;
+  s->peel_step = c.step;
+  s->peel_it = c.cg_total;
+  return SEG_OK;
+}
+
+seg_status seg_set_wait_limit(seg_state* s, int64_t ns) {
+  if (!s) return fail(SEG_ERR_ARG, "state is NULL");
+  s->wait_ns = ns > 0 ? (unsigned long long)ns : kDefaultWaitNs;
+  if (s->prec == SEG_MIXED_FP32)
+    args_of<float>(s).wait_ns = s->wait_ns;
+  else
+    args_of<double>(s).wait_ns = s->wait_ns;
+  retire_graph(s);  // the step graph holds the arguments it was built with
+  return SEG_OK;
 }
 
 // ------------------------------------------------------------------- steps

@@ -385,33 +385,55 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
-// Bounded wait for the phase `parity` of `bar`: false once kWaitNs have
-// passed (globaltimer).  Each try may suspend the warp for up to kSuspendNs
-// until the phase completes, so a waiting warp does not spin on the issue
-// slots that the other warps of the SM need.
+// Bounded wait for the phase `parity` of `bar`: false once limit_ns have
+// passed (globaltimer; the state's wait limit, 1 s by default).  Each try may
+// suspend the warp for up to kSuspendNs until the phase completes, so a
+// waiting warp does not spin on the issue slots that the other warps of the
+// SM need.
 constexpr unsigned kSuspendNs = 2000;
-constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s
+constexpr unsigned long long kWaitNs = kDefaultWaitNs;  // 1 s
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity, unsigned hint_ns) {
   unsigned ok;
   asm volatile(
       "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3; selp.u32 %0, 1, 0, p; }"
       : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendNs)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
       : "memory");
   return ok != 0;
 }
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
-  if (mbar_try_wait(bar, parity)) return true;
+// Non-blocking probe of the phase `parity` of `bar`.
+__device__ __forceinline__ bool mbar_test_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{ .reg .pred p; mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, unsigned long long limit_ns) {
+  if (limit_ns < kSuspendNs) {
+    // a limit shorter than one suspension: non-blocking probes only (a
+    // suspended try may outlast the limit by the time the data needs)
+    if (mbar_test_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (unsigned n = 0; n < (1u << 26); ++n) {
+      if (mbar_test_wait(bar, parity)) return true;
+      if (global_ns() - t0 > limit_ns) return false;
+    }
+    return false;
+  }
+  if (mbar_try_wait(bar, parity, kSuspendNs)) return true;
   const unsigned long long t0 = global_ns();
   // bounded by time and, as a backstop, by the number of tries
   for (unsigned n = 0; n < (1u << 26); ++n) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if (global_ns() - t0 > kWaitNs) return false;
+    if (mbar_try_wait(bar, parity, kSuspendNs)) return true;
+    if (global_ns() - t0 > limit_ns) return false;
   }
   return false;
 }
@@ -555,10 +577,12 @@ __device__ __forceinline__ GroupMap group_map(int n, int rpw, int vb, int vg) {
 // Stage::RPW rows); warp w takes local groups w, w+NW, ...  The copies of the
 // warp's next Stage::kStages - 1 groups are in flight while one group is
 // processed.  `body(stage, row0, nr)` consumes a landed stage.  Returns false
-// if a wait timed out (the copies still in flight are waited for, bounded).
+// if a wait gave up after wait_ns; the copies still in flight are then waited
+// for with the default limit kWaitNs, so that none is outstanding when the
+// block exits.
 template <typename Stage, typename Body>
 __device__ __forceinline__ bool row_pipeline(unsigned char* smem_warp, unsigned long long* bars, const GroupMap& gm,
-                                             const typename Stage::Src& src, Body body) {
+                                             const typename Stage::Src& src, unsigned long long wait_ns, Body body) {
   constexpr int NW = kBlockThreads / 32;
   constexpr int RPW = Stage::RPW;
   constexpr int NS = Stage::kStages;
@@ -605,7 +629,7 @@ __device__ __forceinline__ bool row_pipeline(unsigned char* smem_warp, unsigned 
       }
       pending |= 1u << sn;
     }
-    const bool landed = mbar_wait(&bars[s], (phase >> s) & 1u);
+    const bool landed = mbar_wait(&bars[s], (phase >> s) & 1u, wait_ns);
     if (!__all_sync(0xffffffffu, landed)) {
       ok = false;
       break;
@@ -620,7 +644,7 @@ __device__ __forceinline__ bool row_pipeline(unsigned char* smem_warp, unsigned 
   if (!ok) {
     // drain: wait (bounded) for every stage that still has copies in flight
     for (int k = 0; k < NS; ++k)
-      if (pending & (1u << k)) mbar_wait(&bars[k], (phase >> k) & 1u);
+      if (pending & (1u << k)) mbar_wait(&bars[k], (phase >> k) & 1u, kWaitNs);
   }
   return ok;
 }
@@ -672,7 +696,8 @@ __device__ __forceinline__ void body_start(const KArgs<T>& a, const int vb, cons
   src.val[2] = a.valA;
   src.vec[0] = a.X;
   const bool ok = row_pipeline<Stage>(
-      dyn_smem + warp * Stage::kStages * Stage::kBytes, bars[warp], group_map(a.n, RPW, vb, vg), src, [&](const Stage& sg, int row0, int nr) {
+      dyn_smem + warp * Stage::kStages * Stage::kBytes, bars[warp], group_map(a.n, RPW, vb, vg), src, a.wait_ns,
+      [&](const Stage& sg, int row0, int nr) {
         if (rs >= nr) return;
         const unsigned row = row0 + rs;
         int cols[W];
@@ -737,6 +762,21 @@ __device__ __forceinline__ void body_start(const KArgs<T>& a, const int vb, cons
   if (!grid_reduce_plain<T, LPR, 3, 3>(acc, pl, a, kCtrStart, tot, vb, vg)) return;
   int act = 0, bad = 0;
   const int c = threadIdx.x;
+  if (a.norm_only) {
+    // the normalisation only (reading the state between steps): the solver's
+    // scalars, the choice of start and the loop flag keep the values the
+    // step before left, so that reading the state does not change the run
+    if (c < a.ms) {
+      const double n2 = tot[0][c], ukt = tot[1][c];
+      const bool real = c < a.m;
+      if (real && !(n2 > 0.0 && isfinite(n2) && isfinite(ukt))) bad = 1;
+      ctl->n2[c] = n2;
+      ctl->inv_n[c] = (real && n2 > 0.0) ? 1.0 / sqrt(n2) : 0.0;
+      ctl->lam[c] = (real && n2 > 0.0) ? ukt / n2 : 0.0;
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) ctl->status |= 2;
+    return;
+  }
   if (c < a.ms) {
     const bool used = ctl->carry[c] != 0;
     const double n2 = tot[0][c], ukt = tot[1][c], rz = tot[2][c], bbt = tot[3][c];
@@ -811,6 +851,10 @@ __device__ __forceinline__ void body_cg_a_rows(const KArgs<T>& a, const int vb, 
     al2[v] = (T)ctl->alpha[(it + 1) & 1][c0 + v];  // alpha_{j-2} (this pass overwrites it with alpha_j)
     ysc[v] = it == 1 ? (T)ctl->ysc[c0 + v] : T(1);  // the first update starts from w Y
   }
+  // the first iteration of a solve has no previous direction (p_1 = z_0,
+  // q_1 = A z_0): the direction buffers then hold values of the previous
+  // solve, which are not read at all (not even times beta = 0)
+  const bool first = it == 0;
   Acc acc[1][VW];
 #pragma unroll
   for (int v = 0; v < VW; ++v) acc[0][v].zero();
@@ -822,10 +866,14 @@ __device__ __forceinline__ void body_cg_a_rows(const KArgs<T>& a, const int vb, 
   src.vec[2] = a.Q;
   if (XUP) {
     src.vec[3 % Stage::kNvec] = a.Y;
-    src.vec[4 % Stage::kNvec] = Pnew;  // still p_{j-2}
+    // still p_{j-2}; in the second iteration (alpha_0 = 0) there is no p_0
+    // and the buffer holds the previous solve's last direction: read the
+    // fresh p_1 in its place, so that no value of the previous solve enters
+    src.vec[4 % Stage::kNvec] = it == 1 ? Pold : Pnew;
   }
   const bool ok = row_pipeline<Stage>(
-      dyn_smem + warp * Stage::kStages * Stage::kBytes, bars[warp], group_map(a.n, RPW, vb, vg), src, [&](const Stage& sg, int row0, int nr) {
+      dyn_smem + warp * Stage::kStages * Stage::kBytes, bars[warp], group_map(a.n, RPW, vb, vg), src, a.wait_ns,
+      [&](const Stage& sg, int row0, int nr) {
         if (rs >= nr) return;
         const unsigned row = row0 + rs;
         int cols[W];
@@ -851,7 +899,7 @@ __device__ __forceinline__ void body_cg_a_rows(const KArgs<T>& a, const int vb, 
         T pn[VW], q[VW];
 #pragma unroll
         for (int v = 0; v < VW; ++v) {
-          pn[v] = fma(beta[v], po[v], zi[v]);
+          pn[v] = first ? zi[v] : fma(beta[v], po[v], zi[v]);
           q[v] = T(0);
         }
 #pragma unroll
@@ -860,8 +908,9 @@ __device__ __forceinline__ void body_cg_a_rows(const KArgs<T>& a, const int vb, 
 #pragma unroll
           for (int v = 0; v < VW; ++v) q[v] = fma(ak, zj[k][v], q[v]);
         }
+        if (!first)
 #pragma unroll
-        for (int v = 0; v < VW; ++v) q[v] = fma(beta[v], qo[v], q[v]);
+          for (int v = 0; v < VW; ++v) q[v] = fma(beta[v], qo[v], q[v]);
         st(Pnew + (row * ms + c0), pn);
         st(a.Q + (row * ms + c0), q);
 #pragma unroll
@@ -1329,9 +1378,11 @@ __device__ __forceinline__ void body_finish_rows(const KArgs<T>& a, const int vb
       const unsigned row = base + u * RPW + rs;
 #pragma unroll
       for (int v = 0; v < VW; ++v) {
+        // (after one iteration there is no alpha_0 term, after none no
+        // update: the direction buffers then hold the previous solve's)
         y[u][v] *= ysc[v];
-        if (two) y[u][v] = fma(al2[v], p2[TWO ? u : 0][v], y[u][v]);
-        y[u][v] = fma(al[v], p[u][v], y[u][v]);  // the solve's correction y_k
+        if (two && it > 1) y[u][v] = fma(al2[v], p2[TWO ? u : 0][v], y[u][v]);
+        if (it > 0) y[u][v] = fma(al[v], p[u][v], y[u][v]);  // the solve's correction y_k
         x[u][v] += y[u][v];
       }
       if (a.apply_x && (int)row < r1) {

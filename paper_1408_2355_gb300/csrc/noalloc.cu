@@ -212,15 +212,16 @@ extern "C" seg_status seg_s_eps_noalloc(const double* u, int64_t n_vert, int32_t
   const double inv_eps2 = 1.0 / (eps * eps);
   const int n = (int)n_tri;
   const int nv = (int)n_vert;
-  dim3 grid(kNaBlocks), block(kBlockThreads);
-  switch (pw) {
-    case 1: k_s_eps_noalloc<1><<<grid, block, 0, stream>>>(u, nv, m, xyz, tri, n, inv_eps2, scratch, out); break;
-    case 2: k_s_eps_noalloc<2><<<grid, block, 0, stream>>>(u, nv, m, xyz, tri, n, inv_eps2, scratch, out); break;
-    case 4: k_s_eps_noalloc<4><<<grid, block, 0, stream>>>(u, nv, m, xyz, tri, n, inv_eps2, scratch, out); break;
-    case 8: k_s_eps_noalloc<8><<<grid, block, 0, stream>>>(u, nv, m, xyz, tri, n, inv_eps2, scratch, out); break;
-    default: k_s_eps_noalloc<16><<<grid, block, 0, stream>>>(u, nv, m, xyz, tri, n, inv_eps2, scratch, out); break;
-  }
-  e = cudaGetLastError();
+  void* fn = pw == 1   ? (void*)k_s_eps_noalloc<1>
+             : pw == 2 ? (void*)k_s_eps_noalloc<2>
+             : pw == 4 ? (void*)k_s_eps_noalloc<4>
+             : pw == 8 ? (void*)k_s_eps_noalloc<8>
+                       : (void*)k_s_eps_noalloc<16>;
+  void* args[] = {(void*)&u, (void*)&nv, (void*)&m, (void*)&xyz, (void*)&tri, (void*)&n, (void*)&inv_eps2,
+                  (void*)&scratch, (void*)&out};
+  // the launch's own status: an error left pending on this thread by earlier,
+  // unrelated work is neither reported as ours nor cleared
+  e = cudaLaunchKernel(fn, dim3(kNaBlocks), dim3(kBlockThreads), args, 0, stream);
   if (e != cudaSuccess) return fail(SEG_ERR_CUDA, cudaGetErrorString(e));
   return SEG_OK;
 }

@@ -25,6 +25,7 @@ constexpr int kCgUnroll = 2;    // CG iterations per evaluation of the step grap
 constexpr int kCgPeelDefault = 4;  // CG iterations placed before the loop (the autotuner adjusts it)
 constexpr int kCgPeelMax = 16;
 constexpr int kNumCounters = 8;    // last-block tickets, one per kernel kind
+constexpr unsigned long long kDefaultWaitNs = 1000000000ull;  // bounded waits for staged data: 1 s
 
 enum RowPass { kPassStart = 0, kPassCgA = 1, kPassCgB = 2, kPassFinish = 3 };
 enum CounterSlot { kCtrStart = 0, kCtrCgA = 1, kCtrCgB = 2, kCtrEnergy = 3, kCtrFinish = 4 };
@@ -111,6 +112,8 @@ struct KArgs {
   int count_step;  // finish pass: increment the step counter
   int ignore_halt; // run even if the control block is halted (direct calls)
   long long max_steps;  // > 0: the state is finished once step >= max_steps
+  unsigned long long wait_ns;  // limit of one bounded wait for staged data (default 1 s)
+  int norm_only;   // start pass: the normalisation and D_i only (reading the state between steps)
 };
 
 // True if a step pass must not touch this state: it halted (stop rule or

@@ -49,7 +49,7 @@ def test_no_oracle_in_the_library_path():
 
 
 def test_struct_layouts_match_header(seg):
-    assert C.sizeof(seg.seg_params) == 48
+    assert C.sizeof(seg.seg_params) == 56
     assert C.sizeof(seg.seg_server_params) == 16
     assert C.sizeof(seg.seg_request_info) == 64
     assert C.sizeof(seg.seg_stats) == 64
@@ -150,3 +150,33 @@ def test_mesh_validation_errors(seg):
     with pytest.raises(seg.SegError):
         seg.seg_mesh_torus(8, 8, 0.3, 0.4)
     assert "R > r" in seg.seg_last_error()
+
+
+def test_noalloc_wrapper_rejects_bad_arguments_before_any_call(seg):
+    """seg_s_eps_noalloc's binding checks every argument (kind, dtype,
+    contiguity, shape, output length, device) before the library sees a raw
+    address; each bad argument below is refused with SEG_ERR_ARG on the host
+    (no GPU here: the valid tensors are CPU tensors, refused last for not
+    being on a CUDA device)."""
+    torch = pytest.importorskip("torch")
+    n, m, f = 12, 3, 20
+    good = dict(u=torch.zeros((n, m), dtype=torch.float64), xyz=torch.zeros((n, 3), dtype=torch.float64),
+                tri=torch.zeros((f, 3), dtype=torch.int32), out=torch.zeros(m + 1, dtype=torch.float64))
+    bad_cases = [
+        ("u", np.zeros((n, m)), "torch tensor"),
+        ("tri", torch.zeros((f, 3), dtype=torch.int64), "torch.int32"),
+        ("u", torch.zeros((m, n), dtype=torch.float64).t(), "contiguous"),
+        ("u", torch.zeros(n * m, dtype=torch.float64), "(n_vert, m)"),
+        ("xyz", torch.zeros((n + 1, 3), dtype=torch.float64), "xyz must be"),
+        ("tri", torch.zeros((f, 4), dtype=torch.int32), "tri must be"),
+        ("out", torch.zeros(m, dtype=torch.float64), "m + 1"),
+        (None, None, "CUDA tensor"),
+    ]
+    for key, value, words in bad_cases:
+        args = dict(good)
+        if key is not None:
+            args[key] = value
+        with pytest.raises(seg.SegError) as err:
+            seg.seg_s_eps_noalloc(args["u"], args["xyz"], args["tri"], 0.1, args["out"])
+        assert err.value.status == seg.SEG_ERR_ARG
+        assert words in str(err.value), (key, str(err.value))

@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 
 import workload as w
+from oracle import seg_oracle as o
 from tests.gpu_helpers import lib, make_state, rel
 
 pytestmark = pytest.mark.gpu
@@ -41,9 +42,16 @@ def test_noalloc_matches_energy_entry_points_on_consecutive_calls():
         seg.seg_s_eps_noalloc(u_d, x_d, t_d, eps, out, stream)
         torch.cuda.synchronize()
         outs.append(out.cpu().numpy())
+    # the FP64 oracle on the same u: S_eps by its own quadrature, and the
+    # coupling integrals from its lambda formula (Sec. 1.1)
+    M, K = o.assemble(xyz, tri)
+    s_or = o.s_eps(xyz, tri, U, eps)
+    coup_or = (o.lambda_cl(xyz, tri, K, U, eps) - o.dirichlet(K, U)) * eps * eps / 2.0
     for out in outs:
         assert rel(out[0], e["s_eps"]) <= 1e-10
         assert np.abs(out[1:] - coup_ref).max() <= 1e-10 * np.abs(coup_ref).max()
+        assert rel(out[0], s_or) <= 1e-12
+        assert np.abs(out[1:] - coup_or).max() <= 1e-12 * np.abs(coup_or).max()
     assert np.array_equal(outs[0], outs[1])
 
 
