@@ -32,12 +32,12 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 HBM_FALLBACK_GBS = 6800.0
-# DRAM bytes (read + write) per launch from the ncu capture summarised in
-# profiles/traffic_sphere_L8_m16_mixed.md (level-8 sphere, m = 16, mixed; k_cg_a:
-# the mean of its even and odd forms, k_cg_b: the mean of five launches); valid
-# for that workload and those versions of the kernels only.  k_finish was
-# captured in its even form only.
-TRAFFIC = {"k_cg_a": 272.7e6, "k_start": 194.7e6, "k_cg_b": 91.6e6, "k_energy_check": 63.0e6, "k_finish": None}
+HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e, nominal
+# DRAM bytes (read + write) per launch of each hot-path kernel, from one ncu
+# capture of the level-8 sphere, m = 16, mixed precision (dram__bytes_read.sum
+# + dram__bytes_write.sum); valid only for the kernel versions captured (None:
+# no capture of the current version).
+TRAFFIC = {"k_cg_a": None, "k_start": None, "k_cg_b": None, "k_energy_check": None, "k_finish": None}
 KERNEL_ROLE = {
     "k_start": "start pass: r0 = -tau K X - A y for the predicted correction y, z0 = D^-1 r0, norms "
                "(issue and latency bound: three sparse products and three float-float sums per row)",
@@ -78,6 +78,13 @@ def parse():
     ap.add_argument("--serve-max-steps", type=int, default=300)
     ap.add_argument("--serve-quantum", type=int, default=16)
     ap.add_argument("--cpu-sample-seconds", type=float, default=20.0)
+    ap.add_argument("--setup-steps", type=int, default=1000,
+                    help="steps of the run before the autotuner and the timed window (not timed): the "
+                         "solves' predicted start settles over the first ~1000 steps of the 10000-step run, "
+                         "so a window after them matches the whole run's rate (full_run)")
+    ap.add_argument("--run-steps", type=int, default=10000,
+                    help="the configured run length: one fresh state runs it whole (0 disables)")
+    ap.add_argument("--other-m", default="8,32", help="further component counts timed at the same level")
     ap.add_argument("--reference-budget-seconds", type=float, default=150.0)
     return ap.parse_args()
 
@@ -204,18 +211,80 @@ def oracle_sample(level, m, eps, tau, seed, budget_s, max_cols=None):
     return xyz.shape[0] * c / dt, c, dt, 1
 
 
+def oracle_sample_all_cores(level, m, eps, tau, seed, steps, workers):
+    """Time the FP64 oracle with its m step-1 solves spread over `workers`
+    processes (oracle.parallel; steps 2 and 3 in the parent): `steps` full
+    steps of all m components.  Returns (DoF-steps/s, seconds, workers)."""
+    import workload as w
+    from oracle import parallel
+    from oracle import seg_oracle as o
+
+    xyz, tri = w.icosphere(level)
+    M, K = o.assemble(xyz, tri)
+    U = o.initial_state(M, w.uniform01(seed, xyz.shape[0], m))
+    with parallel.ColumnPool(M, K, tau, m, workers) as pool:
+        U = pool.step(U, eps)  # warm-up (workers started, caches filled)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            U = pool.step(U, eps)
+        dt = time.perf_counter() - t0
+        used = pool.workers
+    return xyz.shape[0] * m * steps / dt, dt, used
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            low = line.lower()
+            if low.startswith("model name") or low.startswith("cpu part") or low.startswith("hardware"):
+                model = line.split(":", 1)[1].strip()
+                if model:
+                    break
+        else:
+            model = None
+    except OSError:
+        model = None
+    try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+        for line in r.stdout.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    import platform
+
+    return f"{model or 'unknown'} ({platform.machine()})"
+
+
 def cpu_baseline(a):
+    """The oracle on the host cores: one thread, and all cores (the m step-1
+    solves in parallel worker processes)."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    ncores = os.cpu_count() or 1
     code = (f"import json,sys; sys.path.insert(0,{ROOT!r}); import bench; "
             f"r=bench.oracle_sample({a.level},{a.m},{a.eps},{a.tau},{a.seed},{a.cpu_sample_seconds}); "
             f"print(json.dumps(r))")
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
     if r.returncode != 0:
         return {"value": None, "unit": "DoF-steps/s", "cores": 1, "kind": "oracle", "error": r.stderr[-300:]}
-    rate, c, dt, threads = json.loads(r.stdout.strip().splitlines()[-1])
-    return {"value": rate, "unit": "DoF-steps/s", "cores": threads, "kind": "oracle",
-            "sample": f"one oracle step (FP64 numpy/scipy, single thread) of the first {c} of {a.m} components "
-                      f"on the level-{a.level} sphere, {dt:.1f} s"}
+    rate1, c, dt1, _ = json.loads(r.stdout.strip().splitlines()[-1])
+    code = (f"import json,sys; sys.path.insert(0,{ROOT!r}); import bench; "
+            f"r=bench.oracle_sample_all_cores({a.level},{a.m},{a.eps},{a.tau},{a.seed},2,{ncores}); "
+            f"print(json.dumps(r))")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    single = {"value": rate1, "cores": 1,
+              "sample": f"one oracle step (FP64 numpy/scipy, one thread) of the first {c} of {a.m} components "
+                        f"on the level-{a.level} sphere, {dt1:.1f} s"}
+    if r.returncode != 0:
+        return {"value": rate1, "unit": "DoF-steps/s", "cores": 1, "kind": "oracle", "sample": single["sample"],
+                "cpu_model": cpu_model(), "nproc": ncores, "all_cores_error": r.stderr[-300:]}
+    rate, dt, used = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": rate, "unit": "DoF-steps/s", "cores": used, "kind": "oracle",
+            "sample": f"2 oracle steps (FP64 numpy/scipy) of all {a.m} components on the level-{a.level} sphere, "
+                      f"the {a.m} step-1 solves spread over {used} worker processes (one BLAS thread each), "
+                      f"after one warm-up step, {dt:.1f} s",
+            "cpu_model": cpu_model(), "nproc": ncores, "single_thread": single}
 
 
 # ---------------------------------------------------------------- our arm
@@ -276,21 +345,31 @@ def run_ours(a, rank, ws, local):
 
     tunes = {}
 
-    def make(prec):
-        prob = seg.seg_assemble(mesh, a.tau, prec)
+    problems = {}
+
+    def make(prec, m=None, rtol=0.0, tune=True):
+        m = a.m if m is None else m
+        if prec not in problems:
+            problems[prec] = seg.seg_assemble(mesh, a.tau, prec)
+        prob = problems[prec]
         prm = seg.seg_params()
         prm.check_every = 1      # energy + stop-rule pass in every step
         prm.energy_tol = -1.0    # ... but never stop: time exactly K steps
         prm.launch_mode = 1 if a.launch_mode == "direct" else 0
         prm.grid_blocks = a.grid_blocks
-        st = seg.seg_state_create(prob, a.m, a.eps, seg.SEG_INIT_UNIFORM, a.seed, prm, stream.cuda_stream)
-        if not a.no_autotune:  # launch geometry by measurement, after 20 steps (setup, not timed)
-            seg.seg_step(st, 20)
-            tunes[prec] = seg.seg_autotune(st, 10)
+        prm.cg_rtol = rtol
+        st = seg.seg_state_create(prob, m, a.eps, seg.SEG_INIT_UNIFORM, a.seed, prm, stream.cuda_stream)
+        # the first steps of the run (set-up, not timed), then the launch
+        # geometry by measurement
+        seg.seg_step(st, a.setup_steps)
+        if tune and not a.no_autotune:
+            tunes[(prec, m, rtol)] = seg.seg_autotune(st, 10)
         return prob, st
 
-    def timed(st, K, W):
+    def timed(st, K, W, before=None):
         seg.seg_step(st, W)
+        if before is not None:
+            before(st)
         s0 = seg.seg_get_stats(st)
         barrier(ws)
         torch.cuda.synchronize()
@@ -305,18 +384,67 @@ def run_ours(a, rank, ws, local):
         s1 = seg.seg_get_stats(st)
         return ms, s0, s1
 
+    # clocks sampled from the set-up on: the timed window alone (K steps of
+    # ~0.3 ms) is shorter than nvidia-smi's 200 ms sampling period
+    clocks = ClockSampler(dev_index)
+    clocks.start()
     prob, st = make(seg.SEG_MIXED_FP32)
     info = seg.seg_problem_info(prob)
     li = seg.seg_launch_info(st)
-    clocks = ClockSampler(dev_index)
-    clocks.start()
-    ms, s0, s1 = timed(st, a.steps, a.warmup)
+    kept = {}
+
+    def keep_checkpoint(st_):
+        # the state at the start of the timed window, in pinned host memory:
+        # the end-to-end run below starts from it
+        buf = torch.empty(seg.seg_checkpoint_size(st_), dtype=torch.uint8).pin_memory()
+        seg.seg_get_checkpoint(st_, buf.numpy())
+        kept["ck"] = buf
+
+    ms, s0, s1 = timed(st, a.steps, a.warmup, keep_checkpoint)
     clk = clocks.stop()
+    clk["window"] = "the set-up steps, the autotuner and the timed steps of the headline state"
     ms = max_over_ranks(ms, ws)
     dcg = s1["cg_iterations"] - s0["cg_iterations"]
     launches = s1["kernel_launches"] - s0["kernel_launches"]  # counted on the device
     value = ws * n * a.m * a.steps / (ms / 1e3)
     e_final = seg.seg_energy(st)
+
+    e2e = None
+    if not a.no_e2e:
+        # the same K steps end to end through the public API: the state at the
+        # start of the window comes from pinned host memory (a checkpoint:
+        # the stored state, the corrections its next solves start from and
+        # the control block), every step's statistics (the energy of its
+        # stop-rule check) are read back -- step k's while step k + 1 runs --
+        # and the final state goes out to pinned host memory
+        ck = kept["ck"].numpy()
+        Uout = torch.empty((n, a.m), dtype=torch.float64).pin_memory()
+        barrier(ws)
+        t0 = time.perf_counter()
+        seg.seg_set_checkpoint(st, ck)
+        energies = []
+        prev = None
+        for _ in range(a.steps):
+            seg.seg_step_async(st, 1)
+            ticket = seg.seg_stats_enqueue(st)
+            if prev is not None:
+                energies.append(seg.seg_stats_wait(st, prev)["last_check_total"])
+            prev = ticket
+        energies.append(seg.seg_stats_wait(st, prev)["last_check_total"])
+        seg.seg_sync(st)
+        seg.seg_get_u(st, Uout)
+        t1 = time.perf_counter()
+        dt = max_over_ranks(t1 - t0, ws)
+        assert len(energies) == a.steps and all(math.isfinite(e) for e in energies)
+        # the same steps as the device-timed window: the same final energy
+        e_check = seg.seg_energy(st)["total"]
+        e2e = {"value": ws * n * a.m * a.steps / dt, "unit": "DoF-steps/s",
+               "h2d_bytes_per_step": ck.nbytes / a.steps,
+               "d2h_bytes_per_step": n * a.m * 8 / a.steps + seg.SEG_STATS_COPY_BYTES,
+               "same_final_energy_as_device_window": e_check == e_final["total"],
+               "note": "seg_set_checkpoint from pinned host (the state at the start of the timed window); "
+                       "K x (seg_step_async + seg_stats_enqueue, then seg_stats_wait of the step before: every "
+                       "step's statistics read back while the next step runs); seg_get_u to pinned host"}
 
     # live per-launch durations of the hot-path kernels with CUDA events on
     # the state's stream (same launch geometry as inside the step graph)
@@ -350,6 +478,7 @@ def run_ours(a, rank, ws, local):
         got = b / (t / 1e3) / 1e9
         return {"bound": "hbm", "kernel": f"{name} ({KERNEL_ROLE[name]})", "achieved": got, "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": got / peak, "traffic": TRAFFIC[name],
+                "frac_of_nominal": got / HBM_NOMINAL_GBS, "peak_nominal": HBM_NOMINAL_GBS,
                 "bytes_per_launch": b, "launch_ms": t, "launches_per_step": c,
                 "share_of_kernel_time": share[name] / tot_share}
 
@@ -380,7 +509,6 @@ def run_ours(a, rank, ws, local):
             "energy_every_step": True,
             "l2": "inputs larger than L2: 8 state vectors x 42 MB + 84 MB of padded-ELL matrices > 129 MB L2",
             "grid_blocks": li["grid_blocks"],
-            "autotune": tunes.get(seg.SEG_MIXED_FP32),
             "launch_mode": a.launch_mode,
             "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
         },
@@ -395,55 +523,112 @@ def run_ours(a, rank, ws, local):
         "step_roofline": {"bytes_per_step": sum(b * c for _, b, c in per.values()),
                           "achieved": sum(b * c for _, b, c in per.values()) / (ms / a.steps / 1e3) / 1e9,
                           "peak": peak, "unit": "GB/s",
-                          "frac": sum(b * c for _, b, c in per.values()) / (ms / a.steps / 1e3) / 1e9 / peak},
+                          "frac": sum(b * c for _, b, c in per.values()) / (ms / a.steps / 1e3) / 1e9 / peak,
+                          "bytes": "this design's streams (per-kernel model above) x launches per step"},
+        "step_roofline_method": method_roofline(n, int(tri.shape[0]), info["nnz"], li["padded_m"], 4, kcg,
+                                                ms / a.steps, peak),
         "kernels": kern,
     }
 
-    if not a.no_e2e:
-        # end to end through the public API: host (pinned) initial data in,
-        # every step's statistics (the energy of its stop-rule check) read
-        # back -- step k's while step k + 1 runs -- final state out to host
-        # memory
-        U0 = torch.from_numpy(w.uniform01(a.seed, n, a.m)).pin_memory()
-        Uout = torch.empty((n, a.m), dtype=torch.float64).pin_memory()
-        seg.seg_set_u(st, U0)
-        seg.seg_step(st, a.warmup)
-        barrier(ws)
-        t0 = time.perf_counter()
-        seg.seg_set_u(st, U0)
-        energies = []
-        prev = None
-        for _ in range(a.steps):
-            seg.seg_step_async(st, 1)
-            ticket = seg.seg_stats_enqueue(st)
-            if prev is not None:
-                energies.append(seg.seg_stats_wait(st, prev)["last_check_total"])
-            prev = ticket
-        energies.append(seg.seg_stats_wait(st, prev)["last_check_total"])
-        seg.seg_sync(st)
-        seg.seg_get_u(st, Uout)
-        t1 = time.perf_counter()
-        dt = max_over_ranks(t1 - t0, ws)
-        assert len(energies) == a.steps and all(math.isfinite(e) for e in energies)
-        out["e2e"] = {"value": ws * n * a.m * a.steps / dt, "unit": "DoF-steps/s",
-                      "h2d_bytes_per_step": n * a.m * 8 / a.steps,
-                      "d2h_bytes_per_step": n * a.m * 8 / a.steps + seg.SEG_STATS_COPY_BYTES,
-                      "note": "set_u from pinned host; K x (seg_step_async + seg_stats_enqueue, then "
-                              "seg_stats_wait of the step before: every step's statistics read back while "
-                              "the next step runs); get_u to pinned host"}
+    if e2e is not None:
+        out["e2e"] = e2e
+
+    out["config"]["autotune"] = tunes.get((seg.SEG_MIXED_FP32, a.m, 0.0))
+    out["config"]["setup_steps"] = a.setup_steps
+    out["config"]["timed_steps"] = f"steps {a.setup_steps + a.warmup + 1}..{a.setup_steps + a.warmup + a.steps} of the run"
+    del st
+
+    def arm(prec, m=None, rtol=0.0):
+        _, s_ = make(prec, m, rtol)
+        ms_, s0_, s1_ = timed(s_, a.steps, a.warmup)
+        ms_ = max_over_ranks(ms_, ws)
+        mm = a.m if m is None else m
+        return {"value": ws * n * mm * a.steps / (ms_ / 1e3), "unit": "DoF-steps/s", "steps": a.steps,
+                "ms_per_step": ms_ / a.steps,
+                "cg_iterations_per_step": (s1_["cg_iterations"] - s0_["cg_iterations"]) / a.steps,
+                "grid_blocks": seg.seg_launch_info(s_)["grid_blocks"]}
 
     if not a.no_fp64:
-        del st
-        prob64, st64 = make(seg.SEG_FP64)
-        k64 = max(3, a.steps // 3)
-        ms64, s0, s1 = timed(st64, k64, min(a.warmup, 3))
-        ms64 = max_over_ranks(ms64, ws)
-        out["fp64"] = {"value": ws * n * a.m * k64 / (ms64 / 1e3), "unit": "DoF-steps/s", "steps": k64,
-                       "ms_per_step": ms64 / k64,
-                       "cg_iterations_per_step": (s1["cg_iterations"] - s0["cg_iterations"]) / k64,
-                       "grid_blocks": seg.seg_launch_info(st64)["grid_blocks"], "autotune": tunes.get(seg.SEG_FP64)}
+        out["fp64"] = arm(seg.SEG_FP64)
+        out["fp64"]["cg_rtol"] = 1e-12
         out["mixed_over_fp64"] = out["value"] / out["fp64"]["value"]
+        out["mixed_over_fp64_is"] = ("precision (f32 vs f64 vectors) + CG tolerance (1e-7 vs 1e-12) + predictor "
+                                     "order (quadratic vs cubic): each mode at its own default")
+        out["fp64_rtol_1e-7"] = arm(seg.SEG_FP64, rtol=1e-7)
+        out["mixed_over_fp64_same_rtol"] = out["value"] / out["fp64_rtol_1e-7"]["value"]
+    others = {}
+    for mm in [int(x) for x in a.other_m.split(",") if x.strip()]:
+        if mm != a.m and 1 <= mm <= 32:
+            others[str(mm)] = arm(seg.SEG_MIXED_FP32, m=mm)
+    if others:
+        out["other_m"] = others
+    if a.run_steps > 0:
+        out["full_run"] = full_run(a, seg, problems[seg.SEG_MIXED_FP32], stream, n, ws)
     return out
+
+
+def method_roofline(n, ntri, nnz, m_pad, s, kcg, ms_step, peak):
+    """Bytes per step of the method (not of this design), per the scope of the
+    hot path: B_step = k_CG (A_b + 8V) + 4V + K_b + M_b with V = N m s one
+    state vector, A_b = K_b = M_b = 4 (N + 1) + nnz (4 + s) one CSR matrix, plus
+    the stop-rule energy pass V + 12 F (three corner indices per triangle),
+    which the bench runs every step."""
+    V = n * m_pad * s
+    Ab = 4 * (n + 1) + nnz * (4 + s)
+    b = kcg * (Ab + 8 * V) + 4 * V + 2 * Ab + V + 12 * ntri
+    got = b / (ms_step / 1e3) / 1e9
+    return {"bytes_per_step": b, "cg_iterations_per_step": kcg, "achieved": got, "unit": "GB/s", "peak": peak,
+            "frac": got / peak, "frac_of_nominal": got / HBM_NOMINAL_GBS,
+            "model": "k_CG (A_b + 8V) + 4V + K_b + M_b + (V + 12F), A_b = 4(N+1) + nnz(4+s), V = N m s"}
+
+
+def full_run(a, seg, prob, stream, n, ws):
+    """The configured run whole: a fresh state from the seeded initial data,
+    autotuned after --setup-steps, then stepped to --run-steps in chunks of
+    500 steps timed with CUDA events (the set-up and the autotuner's own
+    launches are outside the chunks).  Reports DoF-steps/s over all chunks
+    and, per chunk, ms per step and CG iterations per step: the solves start
+    from a correction predicted from the last ones, whose benefit grows over
+    the first hundreds of steps."""
+    import torch
+
+    prm = seg.seg_params()
+    prm.check_every = 1
+    prm.energy_tol = -1.0
+    st = seg.seg_state_create(prob, a.m, a.eps, seg.SEG_INIT_UNIFORM, a.seed, prm, stream.cuda_stream)
+    t_ms, chunks, done = 0.0, [], 0
+    first = min(a.setup_steps, a.run_steps)
+
+    def chunk(k):
+        s0 = seg.seg_get_stats(st)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        seg.seg_step(st, k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        s1 = seg.seg_get_stats(st)
+        return e0.elapsed_time(e1), (s1["cg_iterations"] - s0["cg_iterations"]) / k
+
+    if first:
+        ms_, cg_ = chunk(first)
+        t_ms += ms_
+        chunks.append([first, round(ms_ / first, 4), round(cg_, 2)])
+        done = first
+    if not a.no_autotune:
+        seg.seg_autotune(st, 10)
+    while done < a.run_steps:
+        k = min(500, a.run_steps - done)
+        ms_, cg_ = chunk(k)
+        t_ms += ms_
+        done += k
+        chunks.append([done, round(ms_ / k, 4), round(cg_, 2)])
+    t_ms = max_over_ranks(t_ms, ws)
+    return {"steps": a.run_steps, "value": ws * n * a.m * a.run_steps / (t_ms / 1e3), "unit": "DoF-steps/s",
+            "ms_per_step": t_ms / a.run_steps, "final_total_energy": seg.seg_energy(st)["total"],
+            "chunks": "[last step, ms per step, CG iterations per step] per chunk",
+            "per_chunk": chunks}
 
 
 SERVE_MESHES = [("sphere", 4), ("sphere", 5), ("sphere", 6), ("sphere", 7), ("torus", 128, 64),

@@ -401,9 +401,13 @@ def seg_checkpoint_size(state: State) -> int:
     return b.value
 
 
-def seg_get_checkpoint(state: State) -> np.ndarray:
-    """The state's checkpoint as a host byte array (see include/seg.h)."""
-    buf = np.empty(seg_checkpoint_size(state), dtype=np.uint8)
+def seg_get_checkpoint(state: State, out=None) -> np.ndarray:
+    """The state's checkpoint in a host byte array (see include/seg.h): `out`
+    (a contiguous uint8 numpy array of seg_checkpoint_size bytes, e.g. a view
+    of pinned memory) or a new one."""
+    buf = np.empty(seg_checkpoint_size(state), dtype=np.uint8) if out is None else out
+    if buf.dtype != np.uint8 or not buf.flags["C_CONTIGUOUS"]:
+        raise SegError(SEG_ERR_ARG, "checkpoint buffer must be a contiguous uint8 array")
     _check(lib.seg_get_checkpoint(state.ptr, _ptr(buf), buf.nbytes))
     return buf
 
