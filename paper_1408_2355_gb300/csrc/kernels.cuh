@@ -117,6 +117,78 @@ struct AccD {
   __device__ __forceinline__ double value() const { return v; }
 };
 
+// ------------------------------------------------- packed float32 pairs
+// The float passes do the arithmetic of a lane's VW = 4 values as two packed
+// pairs (FFMA2 / FADD2 / FMUL2: one instruction per pair, each element
+// rounded exactly as the scalar operation would be, so results are bitwise
+// those of the scalar code).  For double data the same helpers are scalar.
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+// x - y as one rounding of the exact difference (= __fsub_rn)
+__device__ __forceinline__ float2 sub2(float2 x, float2 y) { return __ffma2_rn(y, f2(-1.f, -1.f), x); }
+
+// acc[v] += s * x[v]
+__device__ __forceinline__ void v_axpy(float (&acc)[4], float s, const float (&x)[4]) {
+  const float2 a0 = __ffma2_rn(f2(s, s), f2(x[0], x[1]), f2(acc[0], acc[1]));
+  const float2 a1 = __ffma2_rn(f2(s, s), f2(x[2], x[3]), f2(acc[2], acc[3]));
+  acc[0] = a0.x; acc[1] = a0.y; acc[2] = a1.x; acc[3] = a1.y;
+}
+__device__ __forceinline__ void v_axpy(double (&acc)[2], double s, const double (&x)[2]) {
+  acc[0] = fma(s, x[0], acc[0]);
+  acc[1] = fma(s, x[1], acc[1]);
+}
+// out[v] = fma(x[v], y[v], z[v])
+__device__ __forceinline__ void v_fma(float (&out)[4], const float (&x)[4], const float (&y)[4], const float (&z)[4]) {
+  const float2 a0 = __ffma2_rn(f2(x[0], x[1]), f2(y[0], y[1]), f2(z[0], z[1]));
+  const float2 a1 = __ffma2_rn(f2(x[2], x[3]), f2(y[2], y[3]), f2(z[2], z[3]));
+  out[0] = a0.x; out[1] = a0.y; out[2] = a1.x; out[3] = a1.y;
+}
+__device__ __forceinline__ void v_fma(double (&out)[2], const double (&x)[2], const double (&y)[2],
+                                      const double (&z)[2]) {
+  out[0] = fma(x[0], y[0], z[0]);
+  out[1] = fma(x[1], y[1], z[1]);
+}
+// out[v] = s * x[v]
+__device__ __forceinline__ void v_scale(float (&out)[4], float s, const float (&x)[4]) {
+  const float2 a0 = __fmul2_rn(f2(s, s), f2(x[0], x[1]));
+  const float2 a1 = __fmul2_rn(f2(s, s), f2(x[2], x[3]));
+  out[0] = a0.x; out[1] = a0.y; out[2] = a1.x; out[3] = a1.y;
+}
+__device__ __forceinline__ void v_scale(double (&out)[2], double s, const double (&x)[2]) {
+  out[0] = s * x[0];
+  out[1] = s * x[1];
+}
+// out[v] = x[v] - y[v]
+__device__ __forceinline__ void v_sub(float (&out)[4], const float (&x)[4], const float (&y)[4]) {
+  const float2 a0 = sub2(f2(x[0], x[1]), f2(y[0], y[1]));
+  const float2 a1 = sub2(f2(x[2], x[3]), f2(y[2], y[3]));
+  out[0] = a0.x; out[1] = a0.y; out[2] = a1.x; out[3] = a1.y;
+}
+__device__ __forceinline__ void v_sub(double (&out)[2], const double (&x)[2], const double (&y)[2]) {
+  out[0] = x[0] - y[0];
+  out[1] = x[1] - y[1];
+}
+// Float-float accumulation of two values at once (AccF::add_prod on a pair).
+__device__ __forceinline__ void add_prod_pair(AccF& A, AccF& B, float a0, float b0, float a1, float b1) {
+  const float2 a = f2(a0, a1), b = f2(b0, b1);
+  const float2 p = __fmul2_rn(a, b);
+  const float2 pe = __ffma2_rn(a, b, f2(-p.x, -p.y));
+  const float2 hi = f2(A.hi, B.hi);
+  const float2 s = __fadd2_rn(hi, p);
+  const float2 bb = sub2(s, hi);
+  const float2 e = __fadd2_rn(sub2(hi, sub2(s, bb)), sub2(p, bb));
+  const float2 lo = __fadd2_rn(f2(A.lo, B.lo), __fadd2_rn(e, pe));
+  A.hi = s.x; B.hi = s.y; A.lo = lo.x; B.lo = lo.y;
+}
+// acc[v].add_prod(x[v], y[v])
+__device__ __forceinline__ void v_add_prods(AccF (&acc)[4], const float (&x)[4], const float (&y)[4]) {
+  add_prod_pair(acc[0], acc[1], x[0], y[0], x[1], y[1]);
+  add_prod_pair(acc[2], acc[3], x[2], y[2], x[3], y[3]);
+}
+__device__ __forceinline__ void v_add_prods(AccD (&acc)[2], const double (&x)[2], const double (&y)[2]) {
+  acc[0].add_prod(x[0], y[0]);
+  acc[1].add_prod(x[1], y[1]);
+}
+
 template <typename T>
 struct AccOf;
 template <>
@@ -722,40 +794,28 @@ __device__ __forceinline__ void body_start(const KArgs<T>& a, const int vb, cons
         for (int v = 0; v < VW; ++v) kx[v] = mx[v] = T(0);
 #pragma unroll
         for (int k = 0; k < W; ++k) {
-          const T kk = kv[k], mm = mv[k];
-#pragma unroll
-          for (int v = 0; v < VW; ++v) {
-            kx[v] = fma(kk, xj[k][v], kx[v]);
-            mx[v] = fma(mm, xj[k][v], mx[v]);
-          }
+          v_axpy(kx, kv[k], xj[k]);
+          v_axpy(mx, mv[k], xj[k]);
         }
         T ay[VW], av[W];
         lds_row<W>(av, sg.vals(2) + rs * W);
 #pragma unroll
         for (int v = 0; v < VW; ++v) ay[v] = T(0);
 #pragma unroll
-        for (int k = 0; k < W; ++k) {
-          const T ak = av[k];
+        for (int k = 0; k < W; ++k) v_axpy(ay, av[k], yj[k]);
+        T ra[VW], rb[VW], r[VW], z[VW];
+        v_scale(ra, -tau, kx);
+        v_sub(rb, ra, ay);
+        v_fma(pl[1], ra, ra, pl[1]);
+        v_fma(pl[2], rb, rb, pl[2]);
 #pragma unroll
-          for (int v = 0; v < VW; ++v) ay[v] = fma(ak, yj[k][v], ay[v]);
-        }
-        T r[VW], z[VW];
-#pragma unroll
-        for (int v = 0; v < VW; ++v) {
-          const T ra = -tau * kx[v], rb = ra - ay[v];
-          pl[1][v] = fma(ra, ra, pl[1][v]);
-          pl[2][v] = fma(rb, rb, pl[2][v]);
-          r[v] = (om >> v) & 1u ? rb : ra;
-          z[v] = di * r[v];
-        }
+        for (int v = 0; v < VW; ++v) r[v] = (om >> v) & 1u ? rb[v] : ra[v];
+        v_scale(z, di, r);
         st(a.Z + (row * ms + c0), z);
-#pragma unroll
-        for (int v = 0; v < VW; ++v) {
-          acc[0][v].add_prod(x[v], mx[v]);
-          acc[1][v].add_prod(x[v], kx[v]);
-          acc[2][v].add_prod(r[v], z[v]);
-          pl[0][v] = fma(mx[v], mx[v], pl[0][v]);
-        }
+        v_add_prods(acc[0], x, mx);
+        v_add_prods(acc[1], x, kx);
+        v_add_prods(acc[2], r, z);
+        v_fma(pl[0], mx, mx, pl[0]);
       });
   if (__syncthreads_or(!ok) && threadIdx.x == 0) report_timeout(ctl);
   __shared__ double tot[6][kMaxCols];
@@ -892,29 +952,28 @@ __device__ __forceinline__ void body_cg_a_rows(const KArgs<T>& a, const int vb, 
           T x[VW], pp[VW];
           lds(x, sg.vec(3 % Stage::kNvec) + rs * ms + c0);
           lds(pp, sg.vec(4 % Stage::kNvec) + rs * ms + c0);
+          T y0[VW];
 #pragma unroll
-          for (int v = 0; v < VW; ++v) x[v] = fma(al1[v], po[v], fma(al2[v], pp[v], ysc[v] * x[v]));
+          for (int v = 0; v < VW; ++v) y0[v] = ysc[v] * x[v];
+          v_fma(y0, al2, pp, y0);
+          v_fma(x, al1, po, y0);
           st(a.Y + (row * ms + c0), x);
         }
         T pn[VW], q[VW];
+        if (first) {
 #pragma unroll
-        for (int v = 0; v < VW; ++v) {
-          pn[v] = first ? zi[v] : fma(beta[v], po[v], zi[v]);
-          q[v] = T(0);
+          for (int v = 0; v < VW; ++v) pn[v] = zi[v];
+        } else {
+          v_fma(pn, beta, po, zi);
         }
 #pragma unroll
-        for (int k = 0; k < W; ++k) {
-          const T ak = av[k];
+        for (int v = 0; v < VW; ++v) q[v] = T(0);
 #pragma unroll
-          for (int v = 0; v < VW; ++v) q[v] = fma(ak, zj[k][v], q[v]);
-        }
-        if (!first)
-#pragma unroll
-          for (int v = 0; v < VW; ++v) q[v] = fma(beta[v], qo[v], q[v]);
+        for (int k = 0; k < W; ++k) v_axpy(q, av[k], zj[k]);
+        if (!first) v_fma(q, beta, qo, q);
         st(Pnew + (row * ms + c0), pn);
         st(a.Q + (row * ms + c0), q);
-#pragma unroll
-        for (int v = 0; v < VW; ++v) acc[0][v].add_prod(pn[v], q[v]);
+        v_add_prods(acc[0], pn, q);
       });
   if (__syncthreads_or(!ok) && threadIdx.x == 0) report_timeout(ctl);
   __shared__ double tot[1][kMaxCols];
@@ -1107,6 +1166,89 @@ constexpr double kQuadW1 = 0.22338158967801156;
 constexpr double kQuadA2 = 0.0915762135097707;
 constexpr double kQuadW2 = 0.10995174365532179;
 
+// The pair sums of the degree-4 rule over the components of one triangle:
+// at each of the 6 points q the value of u_i is a*tot + (b - a)*corner
+// (b = 1 - 2a, tot the sum of the corner values), and
+//   sum[q] = sum_i u_i(q)^2 sum_{j < i} u_j(q)^2   (prefix form).
+// Returns sum[0] + sum[1] + sum[2] (first orbit) and sum[3] + sum[4] +
+// sum[5] (second orbit).  The float version keeps the two orbits' points at
+// the same corner in one packed pair (points 0 and 3, 1 and 4, 2 and 5):
+// the same operations in the same order, three pairs instead of six values.
+template <int MS>
+__device__ __forceinline__ void quad_pairs(const double* X, unsigned z0, unsigned z1, unsigned z2,
+                                           const double* sinv, double A1, double B1mA1, double A2, double B2mA2,
+                                           double& sum1, double& sum2) {
+  typedef double T;
+  constexpr int VW = VecW<T>::W;
+  T pre[6], sum[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) pre[q] = sum[q] = T(0);
+#pragma unroll
+  for (int c = 0; c < MS; c += VW) {
+    T u0[VW], u1[VW], u2[VW];
+    ld_ro(u0, X + (z0 + c));
+    ld_ro(u1, X + (z1 + c));
+    ld_ro(u2, X + (z2 + c));
+#pragma unroll
+    for (int v = 0; v < VW; ++v) {
+      const T s = sinv[c + v];
+      const T b0 = u0[v] * s, b1 = u1[v] * s, b2 = u2[v] * s;
+      const T tot = b0 + b1 + b2;
+      const T o1 = A1 * tot, o2 = A2 * tot;
+      T val[6];
+      val[0] = fma(B1mA1, b0, o1);
+      val[1] = fma(B1mA1, b1, o1);
+      val[2] = fma(B1mA1, b2, o1);
+      val[3] = fma(B2mA2, b0, o2);
+      val[4] = fma(B2mA2, b1, o2);
+      val[5] = fma(B2mA2, b2, o2);
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        const T sq = val[q] * val[q];
+        sum[q] = fma(sq, pre[q], sum[q]);
+        pre[q] += sq;
+      }
+    }
+  }
+  sum1 = sum[0] + sum[1] + sum[2];
+  sum2 = sum[3] + sum[4] + sum[5];
+}
+template <int MS>
+__device__ __forceinline__ void quad_pairs(const float* X, unsigned z0, unsigned z1, unsigned z2, const float* sinv,
+                                             float A1, float B1mA1, float A2, float B2mA2, float& sum1, float& sum2) {
+  const float2 A = f2(A1, A2), B = f2(B1mA1, B2mA2);
+  float2 pre[3], sum[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) pre[k] = sum[k] = f2(0.f, 0.f);
+#pragma unroll
+  for (int c = 0; c < MS; c += 4) {
+    float u0[4], u1[4], u2[4];
+    ld_ro(u0, X + (z0 + c));
+    ld_ro(u1, X + (z1 + c));
+    ld_ro(u2, X + (z2 + c));
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const float s = sinv[c + v];
+      const float b0 = u0[v] * s, b1 = u1[v] * s, b2 = u2[v] * s;
+      const float tot = b0 + b1 + b2;
+      const float2 o = __fmul2_rn(A, f2(tot, tot));
+      float2 val[3];
+      val[0] = __ffma2_rn(B, f2(b0, b0), o);
+      val[1] = __ffma2_rn(B, f2(b1, b1), o);
+      val[2] = __ffma2_rn(B, f2(b2, b2), o);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float2 sq = __fmul2_rn(val[k], val[k]);
+        sum[k] = __ffma2_rn(sq, pre[k], sum[k]);
+        pre[k] = __fadd2_rn(pre[k], sq);
+      }
+    }
+  }
+  const float2 t = __fadd2_rn(__fadd2_rn(sum[0], sum[1]), sum[2]);
+  sum1 = t.x;
+  sum2 = t.y;
+}
+
 // S_eps of the normalised state for the stop rule (and seg_energy): one
 // thread per triangle, the degree-4 rule, and the pair sum in prefix form
 //   sum_{i != j} u_i^2 u_j^2 = 2 sum_i u_i^2 sum_{j < i} u_j^2
@@ -1136,38 +1278,9 @@ __device__ __forceinline__ void body_energy_check(const KArgs<T>& a, const int v
     const int* tr = a.tri + 3 * (size_t)t;
     const unsigned z0 = __ldg(tr) * ms, z1 = __ldg(tr + 1) * ms, z2 = __ldg(tr + 2) * ms;
     const T area = __ldg(a.tarea + t);
-    T pre[6], sum[6];
-#pragma unroll
-    for (int q = 0; q < 6; ++q) pre[q] = sum[q] = T(0);
-#pragma unroll
-    for (int c = 0; c < MS; c += VW) {
-      T u0[VW], u1[VW], u2[VW];
-      ld_ro(u0, a.X + (z0 + c));
-      ld_ro(u1, a.X + (z1 + c));
-      ld_ro(u2, a.X + (z2 + c));
-#pragma unroll
-      for (int v = 0; v < VW; ++v) {
-        const T s = sinv[c + v];
-        const T b0 = u0[v] * s, b1 = u1[v] * s, b2 = u2[v] * s;
-        const T tot = b0 + b1 + b2;
-        // values at the 6 points: a*tot + (b - a)*corner, b = 1 - 2a
-        const T o1 = A1 * tot, o2 = A2 * tot;
-        T val[6];
-        val[0] = fma(B1mA1, b0, o1);
-        val[1] = fma(B1mA1, b1, o1);
-        val[2] = fma(B1mA1, b2, o1);
-        val[3] = fma(B2mA2, b0, o2);
-        val[4] = fma(B2mA2, b1, o2);
-        val[5] = fma(B2mA2, b2, o2);
-#pragma unroll
-        for (int q = 0; q < 6; ++q) {
-          const T sq = val[q] * val[q];
-          sum[q] = fma(sq, pre[q], sum[q]);
-          pre[q] += sq;
-        }
-      }
-    }
-    const T st = T(2) * area * (W1 * (sum[0] + sum[1] + sum[2]) + W2 * (sum[3] + sum[4] + sum[5]));
+    T sum1, sum2;
+    quad_pairs<MS>(a.X, z0, z1, z2, sinv, A1, B1mA1, A2, B2mA2, sum1, sum2);
+    const T st = T(2) * area * (W1 * sum1 + W2 * sum2);
     acc.add_val(st);
   }
   __shared__ double tot;
@@ -1233,9 +1346,9 @@ __device__ __forceinline__ void body_cg_b(const KArgs<T>& a, const int vb, const
     pre_act[threadIdx.x] = ctl->active[threadIdx.x];
   }
   const unsigned ms = a.ms;
-  T al[VW];
+  T nal[VW];  // -alpha_j
 #pragma unroll
-  for (int v = 0; v < VW; ++v) al[v] = (T)ctl->alpha[(it + 1) & 1][c0 + v];
+  for (int v = 0; v < VW; ++v) nal[v] = -(T)ctl->alpha[(it + 1) & 1][c0 + v];
   Acc acc[2][VW];
 #pragma unroll
   for (int d = 0; d < 2; ++d)
@@ -1260,18 +1373,13 @@ __device__ __forceinline__ void body_cg_b(const KArgs<T>& a, const int vb, const
     for (int u = 0; u < RU; ++u) {
       const unsigned row = base + u * RPW + rs;
       if ((int)row < r1) {
-        T r[VW];
-#pragma unroll
-        for (int v = 0; v < VW; ++v) {
-          z[u][v] = fma(-al[v], di[u] * q[u][v], z[u][v]);
-          r[v] = dg[u] * z[u][v];
-        }
+        T r[VW], dq[VW];
+        v_scale(dq, di[u], q[u]);
+        v_fma(z[u], nal, dq, z[u]);
+        v_scale(r, dg[u], z[u]);
         st(a.Z + (row * ms + c0), z[u]);
-#pragma unroll
-        for (int v = 0; v < VW; ++v) {
-          acc[0][v].add_prod(r[v], z[u][v]);
-          rr[v] = fma(r[v], r[v], rr[v]);
-        }
+        v_add_prods(acc[0], r, z[u]);
+        v_fma(rr, r, r, rr);
       }
     }
   }
