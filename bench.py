@@ -42,10 +42,10 @@ KERNEL_ROLE = {
     "k_start": "start pass: r0 = -tau K X - A y for the predicted correction y, z0 = D^-1 r0, norms "
                "(issue and latency bound: three sparse products and three float-float sums per row)",
     "k_cg_a": "CG pass A: p = z + beta p, q = A z + beta q, p.q; the solve's correction updated every "
-              "second iteration (mean of its even and odd forms)",
+              "second iteration (its first, odd and later even forms weighted by their launches per step)",
     "k_cg_b": "CG pass B: z -= alpha D^-1 q, r.z, |r|^2, convergence and beta",
-    "k_finish": "finish pass: x = X + y, nodal segregation ODE, next predicted correction (mean of its "
-                "forms after an even and an odd iteration count)",
+    "k_finish": "finish pass: x = X + y, nodal segregation ODE, next predicted correction (its forms with "
+                "one and two pending updates weighted by their launches per step)",
     "k_energy_check": "S_eps by the degree-4 rule and the stop rule",
 }
 METRIC = "DoF-steps/s (N*m*steps) sphere 655k m=16 FP32-mix vs FP64; p50/p99 latency"
@@ -307,26 +307,48 @@ def kernel_bytes(n, ntri, m_pad, s, W=8):
     are W int32 columns plus W values per vertex, the Jacobi diagonal N * s.
       k_start  read X and the carried correction Y, write Z, columns + K + M + A values,
                Jacobi inverse diagonal
-      k_cg_a   even iterations: read Z, p_old, q_old; write p_new, q; columns + A values;
-               odd iterations also read Y and p_{j-2} and write Y (two solution updates)
+      k_cg_a   first iteration of a solve: read z; write p = z and q = A z; columns + A
+               values; later even iterations also read p_old and q_old; odd iterations
+               also read Y and p_{j-2} and write Y (two solution updates)
       k_cg_b   read Z, q; write Z; diagonal of A and its inverse
-      k_finish read X, Y, the last two corrections, p (and p of the iteration before after
-               an odd count); write X, the next step's predicted correction Y and this
-               step's correction (over the older of the two)
+      k_finish read X, Y, the last two corrections and p (with two pending updates, after an
+               odd count of 3 or more, also p of the iteration before); write X, the next
+               step's predicted correction Y and this step's correction (over the older of the
+               two)
       k_energy_check / k_energy  read X, triangle corners (3 int32) and areas
     """
     V = n * m_pad * s
     ell = n * W * 4
     return {
         "k_start": 3 * V + ell + 3 * n * W * s + n * s,
+        "k_cg_a_first": 3 * V + ell + n * W * s,
         "k_cg_a_even": 5 * V + ell + n * W * s,
         "k_cg_a_odd": 8 * V + ell + n * W * s,
         "k_cg_b": 3 * V + 2 * n * s,
-        "k_finish_even": 8 * V,
-        "k_finish_odd": 9 * V,
+        "k_finish_one": 8 * V,
+        "k_finish_two": 9 * V,
         "k_energy_check": V + ntri * (12 + s),
         "k_energy": V + ntri * (12 + s),
     }
+
+
+def pass_counts(kcg):
+    """Launches per step of each form of CG pass A and of the finish pass for
+    a mean of kcg CG iterations per step (linear between the two integer
+    counts around it): a solve of k >= 1 iterations runs pass A once in its
+    first form, floor(k / 2) times in its odd form and ceil(k / 2) - 1 times in
+    its later even form; its finish pass has two pending updates when k is
+    odd and at least 3."""
+    def at(k):
+        if k <= 0:
+            return {"first": 0.0, "odd": 0.0, "even": 0.0, "fin_one": 1.0, "fin_two": 0.0}
+        return {"first": 1.0, "odd": float(k // 2), "even": float((k + 1) // 2 - 1),
+                "fin_one": 0.0 if (k % 2 == 1 and k >= 3) else 1.0,
+                "fin_two": 1.0 if (k % 2 == 1 and k >= 3) else 0.0}
+    lo = int(math.floor(kcg))
+    f = kcg - lo
+    a, b = at(lo), at(lo + 1)
+    return {k: (1 - f) * a[k] + f * b[k] for k in a}
 
 
 def run_ours(a, rank, ws, local):
@@ -451,24 +473,32 @@ def run_ours(a, rank, ws, local):
     peak, peak_kind = measured_peak()
     kb = kernel_bytes(n, int(tri.shape[0]), li["padded_m"], 4)
     kern = {}
-    names = ["k_start", "k_cg_a_even", "k_cg_b", "k_finish_even", "k_energy_check", "k_energy", "k_cg_a_odd",
-             "k_finish_odd"]
-    for which, name in enumerate(names):
+    # seg_time_kernel selectors of each kernel form
+    names = {"k_start": 0, "k_cg_a_first": 1, "k_cg_b": 2, "k_finish_one": 3, "k_energy_check": 4, "k_energy": 5,
+             "k_cg_a_odd": 6, "k_finish_two": 7, "k_cg_a_even": 8}
+    for name, which in names.items():
         t = seg.seg_time_kernel(st, which, 20)
         kern[name] = {"ms": t, "bytes": kb[name], "GBps": kb[name] / (t / 1e3) / 1e9,
                       "frac": kb[name] / (t / 1e3) / 1e9 / peak}
-    # per-step kernel time: CG pass A alternates between its two forms and the
-    # finish pass has one form per parity of the iteration count (taken as
-    # equally likely); the energy check runs every step here
+    seg.seg_set_checkpoint(st, kept["ck"].numpy())  # the timing launches overwrote the state
+    # per-step kernel time: each form of CG pass A and of the finish pass
+    # weighted by its launches per step at the measured CG iterations per step
+    # (pass_counts); the energy check runs every step here
     kcg = dcg / a.steps
+    pc = pass_counts(kcg)
+
+    def mix(forms):
+        c = sum(w for _, w in forms)
+        if c <= 0:
+            return kern[forms[0][0]]["ms"], kb[forms[0][0]], 0.0
+        return (sum(kern[f]["ms"] * w for f, w in forms) / c, sum(kb[f] * w for f, w in forms) / c, c)
+
     per = {
         "k_start": (kern["k_start"]["ms"], kb["k_start"], 1.0),
         "k_energy_check": (kern["k_energy_check"]["ms"], kb["k_energy_check"], 1.0),
-        "k_cg_a": (0.5 * (kern["k_cg_a_even"]["ms"] + kern["k_cg_a_odd"]["ms"]),
-                   0.5 * (kb["k_cg_a_even"] + kb["k_cg_a_odd"]), kcg),
+        "k_cg_a": mix([("k_cg_a_first", pc["first"]), ("k_cg_a_odd", pc["odd"]), ("k_cg_a_even", pc["even"])]),
         "k_cg_b": (kern["k_cg_b"]["ms"], kb["k_cg_b"], kcg),
-        "k_finish": (0.5 * (kern["k_finish_even"]["ms"] + kern["k_finish_odd"]["ms"]),
-                     0.5 * (kb["k_finish_even"] + kb["k_finish_odd"]), 1.0),
+        "k_finish": mix([("k_finish_one", pc["fin_one"]), ("k_finish_two", pc["fin_two"])]),
     }
     share = {k: t * c for k, (t, _, c) in per.items()}
     tot_share = sum(share.values())

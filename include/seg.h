@@ -424,15 +424,17 @@ const char* seg_last_error(void);
 
 /* Time `reps` back-to-back launches of one hot-path kernel of this state on
  * its stream with CUDA events; *ms_per_launch receives the mean.  which:
- * 0 = start pass (residual, norms, Dirichlet energy), 1 = CG pass A (search
- * direction update + A p + p.Ap) as on an even iteration, 6 = CG pass A as on
- * an odd iteration (which also applies the two pending solution updates),
- * 2 = CG pass B (residual update + dots), 3 = finish pass (last solution
- * update + nodal ODE) after an even iteration count, 7 = the same after an odd
- * one (two pending updates), 4 = energy pass of the stop rule (S_eps), 5 =
- * energy pass with the per-component coupling integrals.  The
- * kernels run on the state's own buffers, so the state's values are undefined
- * afterwards: call seg_set_u before using it. */
+ * 0 = start pass (residual, norms, Dirichlet energy), 1 = CG pass A (A p +
+ * p.Ap) as in the first iteration of a solve (p = z, the only form a solve of
+ * one iteration runs), 8 = CG pass A as in a later even iteration (also the
+ * direction update p = z + beta p), 6 = CG pass A as in an odd iteration
+ * (which also applies the two pending solution updates), 2 = CG pass B
+ * (residual update + dots), 3 = finish pass (last solution update + nodal ODE)
+ * with one pending update, 7 = the same with two (after an odd count of 3 or
+ * more), 4 = energy pass of the stop rule (S_eps), 5 = energy pass with the
+ * per-component coupling integrals.  The kernels run on the state's own
+ * buffers, so the state's values are undefined afterwards: call seg_set_u
+ * (or seg_set_checkpoint) before using it. */
 seg_status seg_time_kernel(seg_state* s, int32_t which, int32_t reps, double* ms_per_launch);
 
 /* Launch geometry of the row kernels of a state (nullable outputs);

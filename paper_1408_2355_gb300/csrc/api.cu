@@ -263,16 +263,16 @@ seg_status direct_step(seg_state* s) {
 }
 
 // Mean duration of `reps` back-to-back launches of hot-path kernel `which`
-// (0 start, 1 CG A, 2 CG B, 3 finish, 4 energy check, 5 energy) on the
-// state's buffers, after one warm-up launch.
+// (see seg_time_kernel) on the state's buffers, after one warm-up launch.
 seg_status time_launches(seg_state* s, int which, int reps, double* ms_per_launch) {
   void* fns[] = {s->ks.start, s->ks.cg_a,         s->ks.cg_b, s->ks.finish,
-                 s->ks.energy_check, s->ks.energy, s->ks.cg_a, s->ks.finish};
-  if (which == 1 || which == 6 || which == 3 || which == 7) {
-    // CG pass A and the finish pass run as after an even (1, 3) or odd (6, 7)
-    // iteration count: odd pass A also applies the two pending solution
-    // updates, the finish pass after an odd count applies two instead of one
-    const int it = (which == 6 || which == 7) ? 1 : 0;
+                 s->ks.energy_check, s->ks.energy, s->ks.cg_a, s->ks.finish, s->ks.cg_a};
+  if (which == 1 || which == 6 || which == 8 || which == 3 || which == 7) {
+    // the iteration count the pass sees selects its form: CG pass A as the
+    // first iteration of a solve (1), an odd one (6: also the two pending
+    // solution updates) or a later even one (8); the finish pass with one
+    // pending update (3) or two (7, after an odd count of 3 or more)
+    const int it = which == 1 ? 0 : (which == 6 ? 1 : (which == 8 || which == 3 ? 2 : 3));
     SEG_CUDA(cudaMemcpyAsync(&s->ctl->it, &it, sizeof(int), cudaMemcpyHostToDevice, s->stream));
     SEG_CUDA(cudaStreamSynchronize(s->stream));
   }
@@ -1806,7 +1806,7 @@ seg_status seg_stats_wait(seg_state* s, int32_t ticket, seg_stats* out) {
 
 seg_status seg_time_kernel(seg_state* s, int32_t which, int32_t reps, double* ms_per_launch) {
   if (!s || !ms_per_launch) return fail(SEG_ERR_ARG, "state or output is NULL");
-  if (which < 0 || which > 7 || reps < 1) return fail(SEG_ERR_ARG, "which must be 0..7 and reps >= 1");
+  if (which < 0 || which > 8 || reps < 1) return fail(SEG_ERR_ARG, "which must be 0..8 and reps >= 1");
   SEG_CUDA(cudaSetDevice(s->p->device));
   seg_status st = time_launches(s, which, reps, ms_per_launch);
   s->pending = true;

@@ -723,8 +723,12 @@ __device__ __forceinline__ bool row_pipeline(unsigned char* smem_warp, unsigned 
 
 template <typename T, int LPR, int W>
 using StartStage = RowStage<T, LPR, W, 3, 1>;
-template <typename T, int LPR, int W, bool XUP>
-using CgAStage = RowStage<T, LPR, W, 1, XUP ? 5 : 3>;
+// CG pass A in three forms: the first iteration of a solve (kCgFirst: own
+// rows of z only), later even iterations (kCgEven: z, p_old, q_old) and odd
+// iterations (kCgOdd: also y and p_{j-2} for the two pending solution updates).
+constexpr int kCgFirst = 0, kCgEven = 1, kCgOdd = 2;
+template <typename T, int LPR, int W, int FORM>
+using CgAStage = RowStage<T, LPR, W, 1, FORM == kCgFirst ? 1 : (FORM == kCgOdd ? 5 : 3)>;
 
 // Start pass of the CG solve of step 1, (M + tau K) x = M X, fused with the
 // renormalisation of the previous step.  The iterate is x = X + y, with y
@@ -881,13 +885,15 @@ __device__ __forceinline__ void body_start(const KArgs<T>& a, const int vb, cons
 // y += alpha_{j-2} p_{j-2} + alpha_{j-1} p_{j-1},
 // the same sequence of operations as one lagged update per iteration, with
 // one read and write of y saved per two iterations; the finish pass applies
-// what is left.  In the first iteration of a step beta = 0 and alpha = 0
-// (any finite old values will do).
+// what is left.  The first iteration of a solve has no previous direction:
+// p_1 = z_0 and q_1 = A z_0, and the direction buffers (which hold values of
+// the previous solve) are neither staged nor read.
 // Padded ELL entries point at the row itself with value 0 (no branches).
-template <typename T, int LPR, int W, bool XUP>
+template <typename T, int LPR, int W, int FORM>
 __device__ __forceinline__ void body_cg_a_rows(const KArgs<T>& a, const int vb, const int vg, const int it) {
   typedef typename AccOf<T>::type Acc;
-  typedef CgAStage<T, LPR, W, XUP> Stage;
+  typedef CgAStage<T, LPR, W, FORM> Stage;
+  constexpr bool XUP = FORM == kCgOdd;
   DevCtl* ctl = a.ctl;
   SEG_ROW_SETUP
   extern __shared__ __align__(128) unsigned char dyn_smem[];
@@ -911,10 +917,6 @@ __device__ __forceinline__ void body_cg_a_rows(const KArgs<T>& a, const int vb, 
     al2[v] = (T)ctl->alpha[(it + 1) & 1][c0 + v];  // alpha_{j-2} (this pass overwrites it with alpha_j)
     ysc[v] = it == 1 ? (T)ctl->ysc[c0 + v] : T(1);  // the first update starts from w Y
   }
-  // the first iteration of a solve has no previous direction (p_1 = z_0,
-  // q_1 = A z_0): the direction buffers then hold values of the previous
-  // solve, which are not read at all (not even times beta = 0)
-  const bool first = it == 0;
   Acc acc[1][VW];
 #pragma unroll
   for (int v = 0; v < VW; ++v) acc[0][v].zero();
@@ -922,14 +924,16 @@ __device__ __forceinline__ void body_cg_a_rows(const KArgs<T>& a, const int vb, 
   src.ell = a.ell_col;
   src.val[0] = a.valA;
   src.vec[0] = a.Z;
-  src.vec[1] = Pold;
-  src.vec[2] = a.Q;
-  if (XUP) {
-    src.vec[3 % Stage::kNvec] = a.Y;
+  if constexpr (FORM != kCgFirst) {
+    src.vec[1] = Pold;
+    src.vec[2] = a.Q;
+  }
+  if constexpr (XUP) {
+    src.vec[3] = a.Y;
     // still p_{j-2}; in the second iteration (alpha_0 = 0) there is no p_0
     // and the buffer holds the previous solve's last direction: read the
     // fresh p_1 in its place, so that no value of the previous solve enters
-    src.vec[4 % Stage::kNvec] = it == 1 ? Pold : Pnew;
+    src.vec[4] = it == 1 ? Pold : Pnew;
   }
   const bool ok = row_pipeline<Stage>(
       dyn_smem + warp * Stage::kStages * Stage::kBytes, bars[warp], group_map(a.n, RPW, vb, vg), src, a.wait_ns,
@@ -944,33 +948,33 @@ __device__ __forceinline__ void body_cg_a_rows(const KArgs<T>& a, const int vb, 
         T zj[W][VW];
 #pragma unroll
         for (int k = 0; k < W; ++k) ld_ro(zj[k], a.Z + ((unsigned)cols[k] * ms + c0));
-        T zi[VW], po[VW], qo[VW];
+        T zi[VW], pn[VW], q[VW];
         lds(zi, sg.vec(0) + rs * ms + c0);
-        lds(po, sg.vec(1) + rs * ms + c0);
-        lds(qo, sg.vec(2) + rs * ms + c0);
-        if (XUP) {
-          T x[VW], pp[VW];
-          lds(x, sg.vec(3 % Stage::kNvec) + rs * ms + c0);
-          lds(pp, sg.vec(4 % Stage::kNvec) + rs * ms + c0);
-          T y0[VW];
-#pragma unroll
-          for (int v = 0; v < VW; ++v) y0[v] = ysc[v] * x[v];
-          v_fma(y0, al2, pp, y0);
-          v_fma(x, al1, po, y0);
-          st(a.Y + (row * ms + c0), x);
-        }
-        T pn[VW], q[VW];
-        if (first) {
-#pragma unroll
-          for (int v = 0; v < VW; ++v) pn[v] = zi[v];
-        } else {
-          v_fma(pn, beta, po, zi);
-        }
 #pragma unroll
         for (int v = 0; v < VW; ++v) q[v] = T(0);
 #pragma unroll
         for (int k = 0; k < W; ++k) v_axpy(q, av[k], zj[k]);
-        if (!first) v_fma(q, beta, qo, q);
+        if constexpr (FORM == kCgFirst) {
+#pragma unroll
+          for (int v = 0; v < VW; ++v) pn[v] = zi[v];
+        } else {
+          T po[VW], qo[VW];
+          lds(po, sg.vec(1) + rs * ms + c0);
+          lds(qo, sg.vec(2) + rs * ms + c0);
+          if constexpr (XUP) {
+            T x[VW], pp[VW];
+            lds(x, sg.vec(3) + rs * ms + c0);
+            lds(pp, sg.vec(4) + rs * ms + c0);
+            T y0[VW];
+#pragma unroll
+            for (int v = 0; v < VW; ++v) y0[v] = ysc[v] * x[v];
+            v_fma(y0, al2, pp, y0);
+            v_fma(x, al1, po, y0);
+            st(a.Y + (row * ms + c0), x);
+          }
+          v_fma(pn, beta, po, zi);
+          v_fma(q, beta, qo, q);
+        }
         st(Pnew + (row * ms + c0), pn);
         st(a.Q + (row * ms + c0), q);
         v_add_prods(acc[0], pn, q);
@@ -992,10 +996,12 @@ __device__ __forceinline__ void body_cg_a(const KArgs<T>& a, const int vb, const
   if (state_finished(a, ctl)) return;
   if (!ctl->cont && !a.force) return;  // this instance's CG loop has ended (timing runs: force)
   const int it = ctl->it;
-  if (it & 1)
-    body_cg_a_rows<T, LPR, W, true>(a, vb, vg, it);
+  if (it == 0)
+    body_cg_a_rows<T, LPR, W, kCgFirst>(a, vb, vg, it);
+  else if (it & 1)
+    body_cg_a_rows<T, LPR, W, kCgOdd>(a, vb, vg, it);
   else
-    body_cg_a_rows<T, LPR, W, false>(a, vb, vg, it);
+    body_cg_a_rows<T, LPR, W, kCgEven>(a, vb, vg, it);
 }
 
 // Per-component coupling integral on one flat triangle: with a = (u_i at the
@@ -1429,8 +1435,9 @@ __device__ __forceinline__ void body_cg_b(const KArgs<T>& a, const int vb, const
 // (In float32 the cubic rule's amplification of rounding outweighs its
 // better prediction.)  Any initial guess gives the same solution to the
 // solve's tolerance.
-// The solution updates CG pass A has not applied yet: alpha_k p_k, and
-// alpha_{k-1} p_{k-1} before it (TWO) when the iteration count k is odd.
+// The solution updates CG pass A has not applied yet: alpha_k p_k (none if
+// k = 0), and alpha_{k-1} p_{k-1} before it (TWO) when the iteration count k
+// is odd and at least 3.
 template <typename T, int LPR, int RU, bool TWO>
 __device__ __forceinline__ void body_finish_rows(const KArgs<T>& a, const int vb, const int vg, const int it) {
   DevCtl* ctl = a.ctl;
@@ -1476,7 +1483,7 @@ __device__ __forceinline__ void body_finish_rows(const KArgs<T>& a, const int vb
           ld(h1[u], Hm1 + (row * ms + c0));
           ld(h2[u], Hm2 + (row * ms + c0));
           if (NH == 3) ld(h3[NH == 3 ? u : 0], Hm3 + (row * ms + c0));
-          ld_ro(p[u], P + (row * ms + c0));
+          if (it > 0) ld_ro(p[u], P + (row * ms + c0));
         }
         if (two) ld_ro(p2[TWO ? u : 0], P2 + (row * ms + c0));
       }
@@ -1489,7 +1496,7 @@ __device__ __forceinline__ void body_finish_rows(const KArgs<T>& a, const int vb
         // (after one iteration there is no alpha_0 term, after none no
         // update: the direction buffers then hold the previous solve's)
         y[u][v] *= ysc[v];
-        if (two && it > 1) y[u][v] = fma(al2[v], p2[TWO ? u : 0][v], y[u][v]);
+        if (two) y[u][v] = fma(al2[v], p2[TWO ? u : 0][v], y[u][v]);
         if (it > 0) y[u][v] = fma(al[v], p[u][v], y[u][v]);  // the solve's correction y_k
         x[u][v] += y[u][v];
       }
@@ -1529,7 +1536,9 @@ __device__ __forceinline__ void body_finish(const KArgs<T>& a, const int vb, con
   // rows in flight per lane group: fewer where more vectors are read per row
   // (the registers of 2 resident blocks per SM)
   constexpr int RU = sizeof(T) == 8 ? kStreamRows / 2 : kStreamRows - 1;
-  if (a.apply_x && (it & 1))
+  // two pending updates after an odd count of 3 or more iterations (after
+  // one, the second term would be alpha_0 p_0: there is none)
+  if (a.apply_x && (it & 1) && it > 1)
     body_finish_rows<T, LPR, RU - 1, true>(a, vb, vg, it);
   else
     body_finish_rows<T, LPR, RU, false>(a, vb, vg, it);
@@ -1697,9 +1706,12 @@ bool fill_kernels(KernelSet* ks) {
   ks->b_energy_check = (void*)kb_energy_check<T, LPR>;
   ks->b_vote = (void*)k_batch_vote<T>;
   ks->smem_start = row_stage_smem<StartStage<T, LPR, W>>();
-  ks->smem_cg_a = row_stage_smem<CgAStage<T, LPR, W, true>>() > row_stage_smem<CgAStage<T, LPR, W, false>>()
-                      ? row_stage_smem<CgAStage<T, LPR, W, true>>()
-                      : row_stage_smem<CgAStage<T, LPR, W, false>>();
+  {
+    const unsigned f0 = row_stage_smem<CgAStage<T, LPR, W, kCgFirst>>();
+    const unsigned f1 = row_stage_smem<CgAStage<T, LPR, W, kCgEven>>();
+    const unsigned f2 = row_stage_smem<CgAStage<T, LPR, W, kCgOdd>>();
+    ks->smem_cg_a = f0 > f1 ? (f0 > f2 ? f0 : f2) : (f1 > f2 ? f1 : f2);
+  }
   return true;
 }
 
