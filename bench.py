@@ -70,13 +70,21 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch geometry")
     ap.add_argument("--grid-blocks", type=int, default=0, help="row-kernel blocks (0: default / autotuned)")
     ap.add_argument("--batch-steps", type=int, default=200, help="0 disables the two-instance batch run")
-    ap.add_argument("--serve-requests", type=int, default=256, help="0 disables the serving run")
+    ap.add_argument("--serve-requests", type=int, default=32,
+                    help="requests served (the first ones of the seeded 256-request stream); 0 disables")
     ap.add_argument("--serve-compare", type=int, default=24)
     ap.add_argument("--serve-rate", type=float, default=20.0)
-    ap.add_argument("--serve-check-every", type=int, default=25)
-    ap.add_argument("--serve-tol", type=float, default=1e-3)
-    ap.add_argument("--serve-max-steps", type=int, default=300)
-    ap.add_argument("--serve-quantum", type=int, default=16)
+    ap.add_argument("--serve-eps-min", type=float, default=5e-3,
+                    help="eps of the requests log-uniform in [eps-min, 1e-2]")
+    ap.add_argument("--serve-tau-factor", type=float, default=5.0, help="tau = factor * eps^2")
+    ap.add_argument("--serve-check-dt", type=float, default=0.01,
+                    help="stop-rule checks every round(dt / tau) steps (simulated time dt)")
+    ap.add_argument("--serve-rtol", type=float, default=1e-5,
+                    help="stop when the energy changes by at most rtol (relative) between checks")
+    ap.add_argument("--serve-t-max", type=float, default=10.0, help="step budget: simulated time t_max / tau")
+    ap.add_argument("--serve-compare-steps", type=int, default=400,
+                    help="steps per request of the burst / alone throughput comparison")
+    ap.add_argument("--serve-quantum", type=int, default=64)
     ap.add_argument("--cpu-sample-seconds", type=float, default=20.0)
     ap.add_argument("--setup-steps", type=int, default=1000,
                     help="steps of the run before the autotuner and the timed window (not timed): the "
@@ -675,42 +683,62 @@ def _serve_mesh(spec):
     return w.ellipsoid(spec[1], 1.0, 0.8, 0.6)
 
 
+SERVE_STREAM_LEN = 256
+
+
+def serve_eps(a, level):
+    """eps of level 0..7: geometric between --serve-eps-min and 1e-2."""
+    return a.serve_eps_min * (1e-2 / a.serve_eps_min) ** (level / 7)
+
+
 def serve_stream(a):
-    """The seeded request mix of the serving benchmark.
+    """The seeded request stream of the serving benchmark: 256 requests, of
+    which the first --serve-requests are served.
 
     Each request picks a mesh from SERVE_MESHES, m uniform in {2..24} and eps
-    log-uniform in [1e-3, 1e-2], drawn from 8 geometric levels so that the
-    (mesh, tau) problems are assembled once, before the stream starts, and
-    shared; tau = eps^2.  Arrival times are a Poisson process of rate
-    --serve-rate.
+    log-uniform in [--serve-eps-min, 1e-2], drawn from 8 geometric levels so
+    that the (mesh, tau) problems are assembled once, before the stream
+    starts, and shared; tau = --serve-tau-factor * eps^2.  Arrival times are a
+    Poisson process of rate --serve-rate.
     """
     import numpy as np
 
     rng = np.random.default_rng(a.seed + 5)
-    arrivals = np.cumsum(rng.exponential(1.0 / a.serve_rate, a.serve_requests))
+    arrivals = np.cumsum(rng.exponential(1.0 / a.serve_rate, SERVE_STREAM_LEN))
     reqs = [(int(rng.integers(len(SERVE_MESHES))), int(rng.integers(2, 25)), int(rng.integers(8)))
-            for _ in range(a.serve_requests)]
-    return arrivals, reqs
+            for _ in range(SERVE_STREAM_LEN)]
+    n = min(a.serve_requests, SERVE_STREAM_LEN)
+    return arrivals[:n], reqs[:n]
 
 
-def serve_problems(seg, reqs, prec):
-    """{(mesh index, eps level): (problem, eps)} for the requests' pairs."""
+def serve_problems(seg, a, reqs, prec):
+    """{(mesh index, eps level): (problem, eps, tau)} for the requests' pairs."""
     problems, meshes = {}, {}
     for mi, _, ci in reqs:
         if (mi, ci) in problems:
             continue
         if mi not in meshes:
             meshes[mi] = seg.seg_create_mesh(*_serve_mesh(SERVE_MESHES[mi]))
-        eps = 1e-3 * 10.0 ** (ci / 7)
-        problems[(mi, ci)] = (seg.seg_assemble(meshes[mi], eps * eps, prec), eps)
+        eps = serve_eps(a, ci)
+        tau = a.serve_tau_factor * eps * eps
+        problems[(mi, ci)] = (seg.seg_assemble(meshes[mi], tau, prec), eps, tau)
     return problems
 
 
-def serve_params(seg, a):
+def serve_params(seg, a, tau, converge=True):
+    """A request's parameters: checks every dt of simulated time, the relative
+    stop rule, a budget of t_max simulated time (converge=False: a fixed step
+    count and no stop rule, for throughput comparisons)."""
     prm = seg.seg_params()
-    prm.check_every = a.serve_check_every
-    prm.energy_tol = a.serve_tol
-    prm.max_steps = a.serve_max_steps
+    if converge:
+        prm.check_every = max(1, round(a.serve_check_dt / tau))
+        prm.energy_tol = -1.0
+        prm.energy_rtol = a.serve_rtol
+        prm.max_steps = max(1, round(a.serve_t_max / tau))
+    else:
+        prm.check_every = max(1, round(a.serve_check_dt / tau))
+        prm.energy_tol = -1.0
+        prm.max_steps = a.serve_compare_steps
     return prm
 
 
@@ -728,8 +756,7 @@ def run_serving(a, seg, prec, stream):
     arrivals, reqs = serve_stream(a)
     if not stream:
         arrivals, reqs = np.zeros(a.serve_compare), reqs[:a.serve_compare]
-    problems = serve_problems(seg, reqs, prec)
-    prm = serve_params(seg, a)
+    problems = serve_problems(seg, a, reqs, prec)
     sp = seg.seg_server_params()
     sp.steps_per_tick = a.serve_quantum
     srv = seg.seg_server_create(sp)
@@ -741,9 +768,9 @@ def run_serving(a, seg, prec, stream):
         now = seg.seg_server_clock(srv) - t_start
         while nxt < n_req and arrivals[nxt] <= now:
             mi, m, ci = reqs[nxt]
-            prob, eps = problems[(mi, ci)]
+            prob, eps, tau = problems[(mi, ci)]
             ids[nxt] = seg.seg_server_submit(srv, prob, m, eps, seg.SEG_INIT_UNIFORM,
-                                             a.seed + 1000 + nxt, prm)
+                                             a.seed + 1000 + nxt, serve_params(seg, a, tau, converge=stream))
             nxt += 1
         running, queued = seg.seg_server_tick(srv)
         if nxt == n_req and running == 0 and queued == 0:
@@ -751,24 +778,35 @@ def run_serving(a, seg, prec, stream):
         if running == 0 and queued == 0:
             time.sleep(max(0.0, min(0.01, arrivals[nxt] - now)))
     makespan = seg.seg_server_clock(srv) - t_start
-    lat, dof_steps, conv, failed = [], 0.0, 0, 0
+    lat, lat_conv, dof_steps, conv, failed, steps = [], [], 0.0, 0, 0, []
     for k, rid in enumerate(ids):
         info = seg.seg_server_info(srv, rid)
         if info["phase"] != 2:
             failed += 1
             continue
-        lat.append(info["t_done"] - t_start - arrivals[k])
+        t = info["t_done"] - t_start - arrivals[k]
+        lat.append(t)
+        if info["converged"]:
+            lat_conv.append(t)
+        steps.append(info["steps"])
         dof_steps += info["n_vert"] * info["m"] * info["steps"]
         conv += info["converged"]
     seg.seg_server_destroy(srv)
     lat = np.array(lat)
-    return {
+    out = {
         "value": dof_steps / makespan, "unit": "DoF-steps/s", "completed": int(len(lat)), "failed": failed,
         "converged_fraction": conv / max(1, len(lat)),
         "p50_latency_s": float(np.percentile(lat, 50)) if len(lat) else None,
         "p99_latency_s": float(np.percentile(lat, 99)) if len(lat) else None,
+        "latency": "arrival to completion (stop rule met, or the step budget)",
         "makespan_s": makespan, "dof_steps": dof_steps,
+        "steps_p50": float(np.percentile(steps, 50)) if steps else None,
+        "steps_max": int(max(steps)) if steps else None,
     }
+    if stream:
+        out["p50_time_to_converged_s"] = float(np.percentile(lat_conv, 50)) if lat_conv else None
+        out["p99_time_to_converged_s"] = float(np.percentile(lat_conv, 99)) if lat_conv else None
+    return out
 
 
 def run_alone(a, seg, prec):
@@ -776,22 +814,20 @@ def run_alone(a, seg, prec):
     import torch
 
     reqs = serve_stream(a)[1][:a.serve_compare]
-    problems = serve_problems(seg, reqs, prec)
-    prm = serve_params(seg, a)
-    dof_steps, conv = 0.0, 0
+    problems = serve_problems(seg, a, reqs, prec)
+    dof_steps = 0.0
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k, (mi, m, ci) in enumerate(reqs):
-        prob, eps = problems[(mi, ci)]
-        st = seg.seg_state_create(prob, m, eps, seg.SEG_INIT_UNIFORM, a.seed + 1000 + k, prm)
-        steps = seg.seg_step(st, a.serve_max_steps)
-        conv += seg.seg_get_stats(st)["converged"]
+        prob, eps, tau = problems[(mi, ci)]
+        st = seg.seg_state_create(prob, m, eps, seg.SEG_INIT_UNIFORM, a.seed + 1000 + k,
+                                  serve_params(seg, a, tau, converge=False))
+        steps = seg.seg_step(st, a.serve_compare_steps)
         seg.seg_get_u(st)
         dof_steps += seg.seg_problem_info(prob)["n_vert"] * m * steps
         del st
     dt = time.perf_counter() - t0
-    return {"value": dof_steps / dt, "unit": "DoF-steps/s", "seconds": dt, "dof_steps": dof_steps,
-            "converged_fraction": conv / len(reqs)}
+    return {"value": dof_steps / dt, "unit": "DoF-steps/s", "seconds": dt, "dof_steps": dof_steps}
 
 
 def batched_section(a):
@@ -845,12 +881,18 @@ def serving_section(a):
     precision (throughput)."""
     import paper_1408_2355_gb300 as seg
 
-    out = {"requests": a.serve_requests, "arrival_rate_per_s": a.serve_rate,
+    out = {"requests": min(a.serve_requests, SERVE_STREAM_LEN),
+           "stream": f"the first {min(a.serve_requests, SERVE_STREAM_LEN)} of a seeded {SERVE_STREAM_LEN}-request "
+                     f"stream, Poisson arrivals at {a.serve_rate:g}/s",
            "mix": "meshes " + ", ".join("-".join(map(str, s)) for s in SERVE_MESHES)
-                  + "; m ~ U{2..24}; eps log-uniform in [1e-3, 1e-2] on 8 levels; tau = eps^2",
+                  + f"; m ~ U{{2..24}}; eps log-uniform in [{a.serve_eps_min:g}, 1e-2] on 8 levels; "
+                    f"tau = {a.serve_tau_factor:g} eps^2; uniform random initial data",
+           "stop_rule": {"check_every": f"round({a.serve_check_dt:g} / tau) steps",
+                         "energy_rtol": a.serve_rtol,
+                         "meaning": "|E_k - E_prev| <= rtol |E_k| between checks",
+                         "budget": f"round({a.serve_t_max:g} / tau) steps"},
            "compared_requests": a.serve_compare,
-           "stop_rule": {"check_every": a.serve_check_every, "energy_tol": a.serve_tol,
-                         "max_steps": a.serve_max_steps},
+           "compare_steps": a.serve_compare_steps,
            "steps_per_tick": a.serve_quantum}
     out["stream_mixed"] = run_serving(a, seg, seg.SEG_MIXED_FP32, True)
     out["burst_mixed"] = run_serving(a, seg, seg.SEG_MIXED_FP32, False)

@@ -94,6 +94,11 @@ typedef struct {
                             engine (0: 1 s).  A wait that runs out records SEG_ERR_TIMEOUT and
                             halts the run; the copies still in flight are then waited for with
                             the 1 s limit before the kernel returns */
+  double energy_rtol;    /* relative form of the stop rule (0: off): stop also when
+                            |total_k - total_{k - M_tau}| <= energy_rtol |total_k|; with
+                            check_every = round(dt / tau) it bounds the energy's relative rate of
+                            change per simulated time dt, independent of the energy's scale.
+                            SEG_ERR_ARG if negative or not finite */
 } seg_params;
 
 typedef struct {

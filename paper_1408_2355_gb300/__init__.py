@@ -74,6 +74,7 @@ class seg_params(C.Structure):
         ("reserved", C.c_int32),
         ("max_steps", C.c_int64),
         ("wait_limit_ns", C.c_int64),
+        ("energy_rtol", C.c_double),
     ]
 
 

@@ -74,6 +74,7 @@ struct seg_state {
   int cg_maxit = 0;
   long long check_every = 0;
   double energy_tol = 0;
+  double energy_rtol = 0;
   long long max_steps = 0;
   unsigned long long wait_ns = kDefaultWaitNs;  // limit of one bounded device wait
   cudaStream_t stream = nullptr;
@@ -408,6 +409,7 @@ void fill_args(seg_state* s) {
   a.ntri = (int)p->f;
   a.check_every = s->check_every;
   a.energy_tol = s->energy_tol;
+  a.energy_rtol = s->energy_rtol;
   a.max_steps = s->max_steps;
   a.wait_ns = s->wait_ns;
 }
@@ -738,6 +740,11 @@ seg_status seg_state_create(const seg_problem* p, int32_t m, double eps, seg_ini
   s->check_every = prm.check_every > 0 ? prm.check_every
                                        : (prm.check_every < 0 ? 0 : std::max<long long>(1, std::llround(0.1 / p->tau)));
   s->energy_tol = prm.energy_tol > 0 ? prm.energy_tol : (prm.energy_tol < 0 ? -1.0 : 1e-6);
+  if (!(prm.energy_rtol >= 0.0) || !std::isfinite(prm.energy_rtol)) {
+    delete s;
+    return fail(SEG_ERR_ARG, "energy_rtol must be finite and >= 0");
+  }
+  s->energy_rtol = prm.energy_rtol;
   s->max_steps = prm.max_steps > 0 ? prm.max_steps : 0;
   s->wait_ns = prm.wait_limit_ns > 0 ? (unsigned long long)prm.wait_limit_ns : kDefaultWaitNs;
   if (prm.launch_mode != 0 && prm.launch_mode != 1) {

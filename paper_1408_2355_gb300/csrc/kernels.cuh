@@ -1004,6 +1004,16 @@ __device__ __forceinline__ void body_cg_a(const KArgs<T>& a, const int vb, const
     body_cg_a_rows<T, LPR, W, kCgEven>(a, vb, vg, it);
 }
 
+// The Sec. 2.2 stop rule at a check: the change of the total energy since
+// the previous check below energy_tol (absolute, the paper's form) or, if
+// energy_rtol > 0, at most energy_rtol times the energy (relative).
+template <typename T>
+__device__ __forceinline__ bool stop_rule_met(const KArgs<T>& a, double total, const DevCtl* ctl) {
+  if (!ctl->have_prev) return false;
+  const double d = fabs(total - ctl->e_prev);
+  return (a.energy_tol >= 0.0 && d < a.energy_tol) || (a.energy_rtol > 0.0 && d <= a.energy_rtol * fabs(total));
+}
+
 // Per-component coupling integral on one flat triangle: with a = (u_i at the
 // 3 corners) and B = sum_{j != i} a_j a_j^T the barycentric moments give
 //   int_T (a.lam)^2 (lam^T B lam) = |T|/360 [ (s^2 + |a|^2)(1^T B 1 + tr B)
@@ -1122,7 +1132,7 @@ __device__ __forceinline__ void body_energy(const KArgs<T>& a, const int vb, con
         ctl->halted = 2;
         stop = 1;
       } else {
-        if (ctl->have_prev && a.energy_tol >= 0.0 && fabs(total - ctl->e_prev) < a.energy_tol) {
+        if (stop_rule_met(a, total, ctl)) {
           ctl->halted = 1;
           stop = 1;
         }
@@ -1307,7 +1317,7 @@ __device__ __forceinline__ void body_energy_check(const KArgs<T>& a, const int v
         ctl->halted = 2;
         stop = 1;
       } else {
-        if (ctl->have_prev && a.energy_tol >= 0.0 && fabs(total - ctl->e_prev) < a.energy_tol) {
+        if (stop_rule_met(a, total, ctl)) {
           ctl->halted = 1;
           stop = 1;
         }

@@ -106,6 +106,7 @@ struct KArgs {
   int ntri;
   long long check_every;
   double energy_tol;
+  double energy_rtol;  // relative form of the stop rule (0: off)
   int force;       // timing/forced launches: energy regardless of the cadence, CG passes regardless of the loop state
   int apply_x;     // finish pass: x = X + y with the lagged CG updates of y (else x = X)
   int apply_ode;   // finish pass: apply the nodal segregation ODE

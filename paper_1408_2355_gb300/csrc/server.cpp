@@ -130,8 +130,8 @@ seg_status seg_server_submit(seg_server* srv, const seg_problem* p, int32_t m, d
   if (!srv || !p || !id) return fail(SEG_ERR_ARG, "server, problem or id is NULL");
   seg_params prm{};
   if (opt) prm = *opt;
-  if (prm.energy_tol < 0 && prm.max_steps <= 0)
-    return fail(SEG_ERR_ARG, "a request needs a stop rule (energy_tol >= 0) or max_steps");
+  if (prm.energy_tol < 0 && !(prm.energy_rtol > 0) && prm.max_steps <= 0)
+    return fail(SEG_ERR_ARG, "a request needs a stop rule (energy_tol >= 0 or energy_rtol > 0) or max_steps");
   if (prm.check_every < 0 && prm.max_steps <= 0)
     return fail(SEG_ERR_ARG, "a request without energy checks needs max_steps");
   uint64_t bytes = 0;

@@ -49,7 +49,7 @@ def test_no_oracle_in_the_library_path():
 
 
 def test_struct_layouts_match_header(seg):
-    assert C.sizeof(seg.seg_params) == 56
+    assert C.sizeof(seg.seg_params) == 64
     assert C.sizeof(seg.seg_server_params) == 16
     assert C.sizeof(seg.seg_request_info) == 64
     assert C.sizeof(seg.seg_stats) == 64

@@ -90,3 +90,62 @@ def test_server_rejects_requests_that_cannot_finish(seg):
     with pytest.raises(seg.SegError) as e:
         seg.seg_server_submit(srv, probs[0], 3, 0.05, seg.SEG_INIT_UNIFORM, 1, p)
     assert e.value.status == seg.SEG_ERR_ARG
+
+
+def test_served_requests_converge_and_match_the_oracle(seg):
+    """Requests served to the relative stop rule (checks every 0.01 of
+    simulated time, |E_k - E_prev| <= 1e-5 |E_k|) on the level-4 sphere,
+    eps = 1e-2, tau = 5 eps^2, mixed precision, uniform random data.  Each
+    must converge; its result is compared with the FP64 oracle run for the
+    same number of steps (relative total energy and per-component D_i within
+    1e-5, labels equal off the interface), and the oracle's own energies
+    must meet the stop rule at that check and not at the one before (up to
+    the float32 noise of the served energies: a relative change within 10%
+    of the tolerance counts as either)."""
+    from oracle import seg_oracle as o
+    from tests.gpu_helpers import check_labels, rel
+
+    xyz, tri = w.icosphere(4)
+    eps = 1e-2
+    tau = 5 * eps * eps
+    every = round(0.01 / tau)
+    rtol = 1e-5
+    prob = seg.seg_assemble(seg.seg_create_mesh(xyz, tri), tau, seg.SEG_MIXED_FP32)
+    p = seg.seg_params()
+    p.check_every = every
+    p.energy_tol = -1.0
+    p.energy_rtol = rtol
+    p.max_steps = round(10.0 / tau)
+    reqs = [(2, 301), (3, 302)]
+    srv = seg.seg_server_create()
+    ids = [seg.seg_server_submit(srv, prob, m, eps, seg.SEG_INIT_UNIFORM, sd, p) for m, sd in reqs]
+    while True:
+        running, queued = seg.seg_server_tick(srv)
+        if running == 0 and queued == 0:
+            break
+    M, K = o.assemble(xyz, tri)
+    for (m, sd), rid in zip(reqs, ids):
+        info = seg.seg_server_info(srv, rid)
+        assert info["phase"] == 2 and info["converged"] == 1, info
+        S = info["steps"]
+        assert S % every == 0 and S < p.max_steps
+        Ug = seg.seg_server_result(srv, rid)
+        U = o.initial_state(M, w.uniform01(sd, xyz.shape[0], m))
+        energies = {0: o.energy(xyz, tri, K, U, eps)["total"]}
+        for k in range(1, S + 1):
+            U = o.step(M, K, tau, eps, U)
+            if k % every == 0:
+                energies[k] = o.energy(xyz, tri, K, U, eps)["total"]
+        eo = o.energy(xyz, tri, K, U, eps)
+        assert rel(info["total_energy"], eo["total"]) <= 1e-5, (m, info["total_energy"], eo["total"])
+        change = {k: abs(energies[k] - energies[k - every]) / abs(energies[k]) for k in energies if k >= every}
+        assert change[S] <= 1.1 * rtol, (m, S, change[S])
+        assert all(c > 0.9 * rtol for k, c in change.items() if k < S - every), m
+        # the served state against the oracle's: energies, D_i, labels
+        e_sum = o.energy(xyz, tri, K, Ug, eps)
+        assert rel(e_sum["total"], eo["total"]) <= 1e-5
+        assert np.abs(e_sum["D"] - eo["D"]).max() <= 1e-5 * np.abs(eo["D"]).max()
+        st = seg.seg_state_create(prob, m, eps, seg.SEG_INIT_UNIFORM, sd, p)
+        seg.seg_set_u(st, Ug)
+        check_labels(seg, st, tri, U, Ug)
+    seg.seg_server_destroy(srv)
