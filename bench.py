@@ -854,24 +854,38 @@ def batched_section(a):
         probs.append(prob)
         states.append(st)
         dof += xyz.shape[0] * m
+    # both arms run the same steps from the same state (a checkpoint of each
+    # member after the set-up), so they do the same work
+    cks = [seg.seg_get_checkpoint(st) for st in states]
     batch = seg.seg_batch_create(states)
-    seg.seg_batch_step(batch, 3)  # warm-up
+    seg.seg_batch_step(batch, 3)  # warm-up (builds the batch's graph)
+    for st, ck in zip(states, cks):
+        seg.seg_set_checkpoint(st, ck)
+    it0 = [seg.seg_get_stats(st)["cg_iterations"] for st in states]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     seg.seg_batch_step(batch, steps)
     t_batch = time.perf_counter() - t0
+    e_batch = [seg.seg_energy(st)["total"] for st in states]
+    it_batch = [seg.seg_get_stats(st)["cg_iterations"] for st in states]
     del batch
-    for st in states:
-        seg.seg_step(st, 3)
+    for st, ck in zip(states, cks):
+        seg.seg_step(st, 3)  # warm-up (builds the member's own graph)
+        seg.seg_set_checkpoint(st, ck)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for st in states:
         seg.seg_step(st, steps)
     t_alone = time.perf_counter() - t0
+    e_alone = [seg.seg_energy(st)["total"] for st in states]
+    it_alone = [seg.seg_get_stats(st)["cg_iterations"] for st in states]
     return {"workload": "torus 1024x512 + ellipsoid level %d, m = 12, eps = %g, tau = %g, mixed" % (a.level, a.eps, a.tau),
             "steps": steps, "value": dof * steps / t_batch, "unit": "DoF-steps/s",
             "alone_one_after_the_other": dof * steps / t_alone, "batch_over_alone": t_alone / t_batch,
-            "timing": "host clock around synchronous calls, energy check every step"}
+            "same_results": e_batch == e_alone and it_batch == it_alone,
+            "cg_iterations_per_step": [(i - c) / steps for i, c in zip(it_batch, it0)],
+            "timing": "host clock around synchronous calls, both arms from the same checkpoint of the members "
+                      "after 20 set-up steps and the autotuner, energy check every step"}
 
 
 def serving_section(a):

@@ -282,18 +282,18 @@ seg_status seg_substep(seg_state* s, int32_t stage);
 
 /* Several states advanced together (states of different meshes, m and eps):
  * every pass of a step of Algorithm 2.2 is one kernel launch over all members,
- * each member on its own block range, and the members' CG loops run inside one
- * device-controlled loop that continues while any member iterates.  Members
- * must share the precision, the lanes-per-row class (padded m: 1-4, 5-8,
- * 9-16 or 17-32 components in float32; 1-2, 3-4, 5-8, 9-16, 17-32 in float64)
- * and the padded matrix row width, and be on one device; n <= 32.  Each member
- * runs on as many blocks as when stepped alone, and its results are then
- * bitwise the same, as long as the members' blocks together need no more
- * waves of resident blocks than the largest member alone; beyond that the
- * blocks are shared out in proportion to the members' work (the results then
- * differ from the member alone only by the summation order of the per-block
- * partial sums).  While a batch exists its members must not be stepped on
- * their own streams concurrently.
+ * and the members' CG loops run inside one device-controlled loop that
+ * continues while any member iterates.  Members must share the precision, the
+ * lanes-per-row class (padded m: 1-4, 5-8, 9-16 or 17-32 components in
+ * float32; 1-2, 3-4, 5-8, 9-16, 17-32 in float64) and the padded matrix row
+ * width, and be on one device; n <= 32.  Each member keeps the block
+ * decomposition of its own launch geometry (as "virtual" blocks), and a launch
+ * of at most the blocks resident at once runs the virtual blocks of every
+ * member taking part in the pass, so a member's results are bitwise those of
+ * the member stepped alone, and in a CG iteration that only some members need
+ * those members have the whole GPU.  The geometry is taken when the batch is
+ * built.  While a batch exists its members must not be stepped on their own
+ * streams concurrently.
  * cuda_stream = NULL: the batch's own stream. */
 typedef struct seg_batch seg_batch;
 seg_status seg_batch_create(seg_state* const* states, int32_t n, void* cuda_stream, seg_batch** out);

@@ -1275,7 +1275,7 @@ struct seg_batch {
   KernelSet ks{};
   cudaStream_t stream = nullptr;
   bool own_stream = false;
-  void* tab = nullptr;  // device KArgs<T>[n]
+  int* amap = nullptr;  // device [kMaxBatch]: members iterating in the current CG iteration
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaGraphConditionalHandle cond = 0;
@@ -1291,40 +1291,23 @@ namespace {
 
 template <typename T>
 cudaError_t add_batch_node(cudaGraphNode_t* node, cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps,
-                           void* fn, const BatchArgs<T>& b, int threads, unsigned smem) {
+                           void* fn, const BatchArgs<T>& b, int grid, int threads, unsigned smem) {
   BatchArgs<T> copy = b;
   void* args[] = {&copy};
   cudaKernelNodeParams kp{};
   kp.func = fn;
-  kp.gridDim = dim3(b.off[b.ninst] > 0 ? b.off[b.ninst] : 1);
+  kp.gridDim = dim3(grid > 0 ? grid : 1);
   kp.blockDim = dim3(threads);
   kp.sharedMemBytes = smem;
   kp.kernelParams = args;
   return cudaGraphAddKernelNode(node, g, deps, ndeps, &kp);
 }
 
-// Blocks of each member in a batched pass.  A member keeps its own grid
-// while the members' grids together take no more waves of resident blocks
-// than the member that needs the most (then results are bitwise those of the
-// member alone); otherwise that many waves are shared out in proportion to
-// the members' work (rows, or triangles for the energy check), at least one
-// block each: two members that each fill the GPU run side by side on half of
-// it instead of in twice the waves.
-void batch_grids(const std::vector<int>& own, const std::vector<int64_t>& work, int per_wave, std::vector<int>* out) {
-  const size_t n = own.size();
-  int64_t sum = 0, waves = 1, wsum = 0;
-  for (size_t i = 0; i < n; ++i) {
-    sum += own[i];
-    waves = std::max<int64_t>(waves, (own[i] + per_wave - 1) / per_wave);
-    wsum += work[i];
-  }
-  out->assign(own.begin(), own.end());
-  const int64_t cap = waves * per_wave;
-  if (sum <= cap || wsum <= 0) return;
-  for (size_t i = 0; i < n; ++i)
-    (*out)[i] = (int)std::max<int64_t>(1, std::min<int64_t>(own[i], cap * work[i] / wsum));
-}
-
+// The batch's step graph: the passes of Algorithm 2.2 as in the state's own
+// graph, each one launch for every member.  Member i runs each pass on the
+// virtual blocks of its own launch geometry (so its results are bitwise
+// those of the member stepped alone); the physical grid of a pass is the
+// members' virtual blocks together, at most the blocks resident at once.
 template <typename T>
 seg_status build_batch_t(seg_batch* b) {
   const int n = (int)b->members.size();
@@ -1332,21 +1315,7 @@ seg_status build_batch_t(seg_batch* b) {
   BatchArgs<T> rows[4] = {}, tris{}, vote{};
   int nsm = 0;
   SEG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->members[0]->p->device));
-  std::vector<int> grids[5];
-  {
-    std::vector<int64_t> nrow(n), ntri(n);
-    std::vector<int> own(n);
-    for (int i = 0; i < n; ++i) {
-      nrow[i] = b->members[i]->p->n;
-      ntri[i] = b->members[i]->p->f;
-    }
-    for (int k = 0; k < 4; ++k) {
-      for (int i = 0; i < n; ++i) own[i] = b->members[i]->grid[k];
-      batch_grids(own, nrow, nsm * (k == kPassStart ? kStartBlocksPerSM : kRowBlocksPerSM), &grids[k]);
-    }
-    for (int i = 0; i < n; ++i) own[i] = b->members[i]->grid_e;
-    batch_grids(own, ntri, nsm * kTriBlocksPerSM, &grids[4]);
-  }
+  int phys[5] = {0, 0, 0, 0, 0};
   for (int i = 0; i < n; ++i) {
     seg_state* s = b->members[i];
     Launch l;
@@ -1355,22 +1324,35 @@ seg_status build_batch_t(seg_batch* b) {
     l.apply_ode = 1;
     l.count_step = 1;
     tab[i] = make_args<T>(s, l);
-    for (int k = 0; k < 4; ++k) rows[k].off[i + 1] = rows[k].off[i] + grids[k][i];
-    tris.off[i + 1] = tris.off[i] + grids[4][i];
+    for (int k = 0; k < 4; ++k) {
+      rows[k].vg[i] = s->grid[k];
+      phys[k] += s->grid[k];
+    }
+    tris.vg[i] = s->grid_e;
+    phys[4] += s->grid_e;
   }
+  for (int k = 0; k < 4; ++k)
+    phys[k] = std::min(phys[k], nsm * (k == kPassStart ? kStartBlocksPerSM : kRowBlocksPerSM));
+  phys[4] = std::min(phys[4], nsm * kTriBlocksPerSM);
+  rows[kPassStart].map = kMapAll;
+  rows[kPassCgA].map = kMapCgA;
+  rows[kPassCgB].map = kMapCgB;
+  rows[kPassFinish].map = kMapAll;
+  tris.map = kMapAll;
 
   SEG_CUDA(cudaGraphCreate(&b->graph, 0));
   SEG_CUDA(cudaGraphConditionalHandleCreate(&b->cond, b->graph, 0, cudaGraphCondAssignDefault));
   for (BatchArgs<T>* x : {&rows[0], &rows[1], &rows[2], &rows[3], &tris, &vote}) {
     for (int i = 0; i < n; ++i) x->tab[i] = tab[i];
     x->ninst = n;
+    x->amap = b->amap;
     x->cond = (unsigned long long)b->cond;
   }
-  vote.off[n] = 1;  // one block
   cudaGraphNode_t n_start, n_energy, n_vote0, n_loop, n_a, n_b, n_vote, n_fin;
-  SEG_CUDA(add_batch_node<T>(&n_start, b->graph, nullptr, 0, b->ks.b_start, rows[kPassStart], kBlockThreads,
-                             b->ks.smem_start));
-  SEG_CUDA(add_batch_node<T>(&n_energy, b->graph, &n_start, 1, b->ks.b_energy_check, tris, kBlockThreads, 0));
+  SEG_CUDA(add_batch_node<T>(&n_start, b->graph, nullptr, 0, b->ks.b_start, rows[kPassStart], phys[kPassStart],
+                             kBlockThreads, b->ks.smem_start));
+  SEG_CUDA(add_batch_node<T>(&n_energy, b->graph, &n_start, 1, b->ks.b_energy_check, tris, phys[4], kBlockThreads,
+                             0));
   // as in the single-state graph: the first CG iterations (at first the
   // largest peel count of the members, then reviewed while stepping) as
   // plain nodes, then the vote and the loop
@@ -1379,12 +1361,13 @@ seg_status build_batch_t(seg_batch* b) {
   const int peel = b->peel;
   cudaGraphNode_t last = n_energy;
   for (int u = 0; u < peel; ++u) {
-    SEG_CUDA(add_batch_node<T>(&n_a, b->graph, &last, 1, b->ks.b_cg_a, rows[kPassCgA], kBlockThreads,
-                               b->ks.smem_cg_a));
-    SEG_CUDA(add_batch_node<T>(&n_b, b->graph, &n_a, 1, b->ks.b_cg_b, rows[kPassCgB], kBlockThreads, 0));
+    SEG_CUDA(add_batch_node<T>(&n_a, b->graph, &last, 1, b->ks.b_cg_a, rows[kPassCgA], phys[kPassCgA],
+                               kBlockThreads, b->ks.smem_cg_a));
+    SEG_CUDA(add_batch_node<T>(&n_b, b->graph, &n_a, 1, b->ks.b_cg_b, rows[kPassCgB], phys[kPassCgB],
+                               kBlockThreads, 0));
     last = n_b;
   }
-  SEG_CUDA(add_batch_node<T>(&n_vote0, b->graph, &last, 1, b->ks.b_vote, vote, kMaxBatch, 0));
+  SEG_CUDA(add_batch_node<T>(&n_vote0, b->graph, &last, 1, b->ks.b_vote, vote, 1, kMaxBatch, 0));
   cudaGraphNodeParams cp{};
   cp.type = cudaGraphNodeTypeConditional;
   cp.conditional.handle = b->cond;
@@ -1395,12 +1378,14 @@ seg_status build_batch_t(seg_batch* b) {
   cudaGraphNode_t prev = nullptr;
   for (int u = 0; u < kCgUnroll; ++u) {
     SEG_CUDA(add_batch_node<T>(&n_a, body, prev ? &prev : nullptr, prev ? 1 : 0, b->ks.b_cg_a, rows[kPassCgA],
-                               kBlockThreads, b->ks.smem_cg_a));
-    SEG_CUDA(add_batch_node<T>(&n_b, body, &n_a, 1, b->ks.b_cg_b, rows[kPassCgB], kBlockThreads, 0));
+                               phys[kPassCgA], kBlockThreads, b->ks.smem_cg_a));
+    SEG_CUDA(add_batch_node<T>(&n_b, body, &n_a, 1, b->ks.b_cg_b, rows[kPassCgB], phys[kPassCgB], kBlockThreads,
+                               0));
     prev = n_b;
   }
-  SEG_CUDA(add_batch_node<T>(&n_vote, body, &n_b, 1, b->ks.b_vote, vote, kMaxBatch, 0));
-  SEG_CUDA(add_batch_node<T>(&n_fin, b->graph, &n_loop, 1, b->ks.b_finish, rows[kPassFinish], kBlockThreads, 0));
+  SEG_CUDA(add_batch_node<T>(&n_vote, body, &n_b, 1, b->ks.b_vote, vote, 1, kMaxBatch, 0));
+  SEG_CUDA(add_batch_node<T>(&n_fin, b->graph, &n_loop, 1, b->ks.b_finish, rows[kPassFinish], phys[kPassFinish],
+                             kBlockThreads, 0));
   SEG_CUDA(cudaGraphInstantiate(&b->exec, b->graph, 0));
   return SEG_OK;
 }
@@ -1441,6 +1426,11 @@ seg_status seg_batch_create(seg_state* const* states, int32_t n, void* cuda_stre
   // members' pending work on their own streams must be done first
   for (int i = 0; i < n && st == SEG_OK; ++i) {
     e = cudaStreamSynchronize(states[i]->stream);
+    if (e != cudaSuccess) st = fail(SEG_ERR_CUDA, cudaGetErrorString(e));
+  }
+  if (st == SEG_OK) {
+    e = cudaMalloc((void**)&b->amap, kMaxBatch * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(b->amap, 0, kMaxBatch * sizeof(int));
     if (e != cudaSuccess) st = fail(SEG_ERR_CUDA, cudaGetErrorString(e));
   }
   if (st == SEG_OK) {
@@ -1607,7 +1597,7 @@ void seg_batch_destroy(seg_batch* b) {
   drop_batch_retired(b);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
-  if (b->tab) cudaFree(b->tab);
+  if (b->amap) cudaFree(b->amap);
   if (b->hsnap) cudaFreeHost(b->hsnap);
   for (cudaEvent_t e : b->snap_ev)
     if (e) cudaEventDestroy(e);

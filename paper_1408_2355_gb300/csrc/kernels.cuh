@@ -436,6 +436,12 @@ __device__ __forceinline__ unsigned smem_u32(const void* p) {
 __device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
+// Invalidate an mbarrier (all its phases complete, no copy in flight) so that
+// its shared memory may hold a new one: a block that runs several pipelines
+// (the virtual blocks of a batch) initialises its ring afresh for each.
+__device__ __forceinline__ void mbar_inval(unsigned long long* bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 __device__ __forceinline__ void mbar_init_fence() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
@@ -718,6 +724,11 @@ __device__ __forceinline__ bool row_pipeline(unsigned char* smem_warp, unsigned 
     for (int k = 0; k < NS; ++k)
       if (pending & (1u << k)) mbar_wait(&bars[k], (phase >> k) & 1u, kWaitNs);
   }
+  __syncwarp();
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < NS; ++k) mbar_inval(&bars[k]);
+  __syncwarp();
   return ok;
 }
 
@@ -1574,14 +1585,49 @@ __device__ __forceinline__ void body_finish(const KArgs<T>& a, const int vb, con
 // ------------------------------------------------- kernels and batch kernels
 
 // One launch per pass: the single-instance kernels run a body over the whole
-// grid; the batch kernels split the grid into per-instance block ranges
-// [off[i], off[i+1]) and run instance i's body on its range, so one launch
-// advances every instance of a batch.
-template <typename T>
-__device__ __forceinline__ int batch_slot(const BatchArgs<T>& b) {
-  int i = 0;
-  while (i + 1 < b.ninst && (int)blockIdx.x >= b.off[i + 1]) ++i;
-  return i;
+// grid; the batch kernels run the virtual blocks of the members taking part
+// (BatchArgs) on their physical blocks, block b taking virtual blocks b,
+// b + gridDim.x, ...  Members of CG pass A are those whose loop flag is set
+// (written before the launch by the previous pass B, the start pass or the
+// energy check); physical block 0 records them for pass B, whose own last
+// blocks rewrite the flags during its launch.  The other passes take every
+// member (a member that has stopped returns at once).
+template <typename T, typename Body>
+__device__ __forceinline__ void run_batch(const BatchArgs<T>& b, Body body) {
+  __shared__ int vstart[kMaxBatch + 1];
+  if (threadIdx.x < 32) {
+    // lane i decides for member i (all members' flags read at once), then an
+    // exclusive scan of the members' virtual blocks over the warp
+    const int i = threadIdx.x;
+    int take = 0;
+    if (i < b.ninst) {
+      take = 1;
+      if (b.map == kMapCgA) {
+        const KArgs<T>& a = b.tab[i];
+        take = (a.ctl->cont && !state_finished(a, a.ctl)) ? 1 : 0;
+        if (blockIdx.x == 0) b.amap[i] = take;
+      } else if (b.map == kMapCgB) {
+        take = b.amap[i];
+      }
+    }
+    const int cnt = take ? b.vg[i < b.ninst ? i : 0] : 0;
+    int incl = cnt;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, off);
+      if (i >= off) incl += y;
+    }
+    if (i < b.ninst) vstart[i] = incl - cnt;
+    if (i == b.ninst - 1) vstart[b.ninst] = incl;
+  }
+  __syncthreads();
+  const int total = vstart[b.ninst];
+  for (int v = blockIdx.x; v < total; v += gridDim.x) {
+    int i = 0;
+    while (i + 1 < b.ninst && v >= vstart[i + 1]) ++i;
+    body(b.tab[i], v - vstart[i], b.vg[i]);
+    __syncthreads();  // the next virtual block reuses the shared memory
+  }
 }
 
 #define SEG_DEFINE_PASS(NAME, MINB, TPL, ...)                                                           \
@@ -1589,9 +1635,7 @@ __device__ __forceinline__ int batch_slot(const BatchArgs<T>& b) {
     body_##NAME<__VA_ARGS__>(a, blockIdx.x, gridDim.x);                                             \
   }                                                                                                 \
   TPL __global__ void __launch_bounds__(kBlockThreads, MINB) kb_##NAME(const BatchArgs<T> b) {         \
-    const int i = batch_slot(b);                                                                    \
-    const KArgs<T>& a = b.tab[i];                                                                   \
-    body_##NAME<__VA_ARGS__>(a, (int)blockIdx.x - b.off[i], b.off[i + 1] - b.off[i]);               \
+    run_batch(b, [&](const KArgs<T>& a, int vb, int vg) { body_##NAME<__VA_ARGS__>(a, vb, vg); });   \
   }
 
 #define SEG_TPL_W template <typename T, int LPR, int W>

@@ -126,14 +126,22 @@ __device__ __forceinline__ bool state_finished(const KArgs<T>& a, const DevCtl* 
   return ctl->halted != 0 || (a.max_steps > 0 && ctl->step >= a.max_steps);
 }
 
-// Arguments of a batched launch: instance i owns blocks [off[i], off[i+1])
-// and runs with the arguments tab[i] (device memory).
+// Arguments of a batched launch.  Member i keeps the block decomposition it
+// has when stepped alone: vg[i] virtual blocks, each running the member's
+// pass body with the arguments tab[i] exactly as block vb of its own grid
+// would.  The launch has a fixed grid of physical blocks (as many as are
+// resident at once) that take the virtual blocks of the members taking part
+// in the pass in turn, so results are bitwise those of each member alone and
+// a member that has stopped iterating leaves the whole GPU to the others.
 constexpr int kMaxBatch = 32;
+enum BatchMap { kMapAll = 0, kMapCgA = 1, kMapCgB = 2 };
 template <typename T>
 struct BatchArgs {
   KArgs<T> tab[kMaxBatch];  // in the kernel's parameter space (read through the constant cache)
   int ninst;
-  int off[kMaxBatch + 1];
+  int vg[kMaxBatch];        // virtual blocks (own grid) of each member in this pass
+  int map;                  // BatchMap: which members take part
+  int* amap;                // [kMaxBatch] members iterating in the current CG iteration (device)
   unsigned long long cond;  // conditional handle of the batch's CG loop
 };
 

@@ -14,6 +14,10 @@ Cases (Algorithm 2.2 from uniform random initial data, Sec. 2.2):
   sphere8_m16              icosphere level 8 (N = 655 362), m = 16,
                            eps = 1e-3, tau = 5e-6, 1000 steps (t = 5e-3),
                            seed 1236
+  torus1024_m12,           the two-instance batched workload: the torus
+  ellipsoid8_m12           R = 1, r = 0.4 on a 1024 x 512 grid and the
+                           level-8 ellipsoid (1, 0.8, 0.6), m = 12,
+                           eps = 1e-3, tau = 5e-6, 50 steps, seeds 1237, 1238
 
 Each file ``longrun_<case>.json`` holds, at every checkpoint, the energy
 record of the oracle's state (total, functional, Dirichlet sum, S_eps, the
@@ -47,10 +51,23 @@ from oracle import parallel  # noqa: E402
 from oracle import seg_oracle as o  # noqa: E402
 
 CASES = {
-    "sphere7_m3": dict(level=7, m=3, eps=2e-3, tau=1e-5, steps=5000, every=500, seed=1235, samples=2048),
-    "sphere7_m2": dict(level=7, m=2, eps=2e-3, tau=1e-5, steps=5000, every=500, seed=1235, samples=2048),
-    "sphere8_m16": dict(level=8, m=16, eps=1e-3, tau=5e-6, steps=1000, every=100, seed=1236, samples=384),
+    "sphere7_m3": dict(mesh=("sphere", 7), m=3, eps=2e-3, tau=1e-5, steps=5000, every=500, seed=1235, samples=2048),
+    "sphere7_m2": dict(mesh=("sphere", 7), m=2, eps=2e-3, tau=1e-5, steps=5000, every=500, seed=1235, samples=2048),
+    "sphere8_m16": dict(mesh=("sphere", 8), m=16, eps=1e-3, tau=5e-6, steps=1000, every=100, seed=1236, samples=384),
+    "torus1024_m12": dict(mesh=("torus", 1024, 512, 1.0, 0.4), m=12, eps=1e-3, tau=5e-6, steps=50, every=25,
+                          seed=1237, samples=384),
+    "ellipsoid8_m12": dict(mesh=("ellipsoid", 8, 1.0, 0.8, 0.6), m=12, eps=1e-3, tau=5e-6, steps=50, every=25,
+                           seed=1238, samples=384),
 }
+
+
+def make_mesh(spec):
+    kind = spec[0]
+    if kind == "sphere":
+        return w.icosphere(spec[1]), f"icosphere level {spec[1]}"
+    if kind == "torus":
+        return w.torus(*spec[1:]), "torus %dx%d R=%g r=%g" % spec[1:]
+    return w.ellipsoid(*spec[1:]), "ellipsoid level %d semi-axes (%g, %g, %g)" % spec[1:]
 
 
 def one_ring_mixed(tri, labels, n):
@@ -77,13 +94,13 @@ def record(xyz, tri, K, U, eps):
 
 
 def run_case(name, spec, workers):
-    xyz, tri = w.icosphere(spec["level"])
+    (xyz, tri), mesh_name = make_mesh(spec["mesh"])
     n, m = xyz.shape[0], spec["m"]
     M, K = o.assemble(xyz, tri)
     U0 = w.uniform01(spec["seed"], n, m)
     out = {
         "case": name,
-        "mesh": f"icosphere level {spec['level']}",
+        "mesh": mesh_name,
         "n_vert": n,
         "m": m,
         "eps": spec["eps"],

@@ -1,7 +1,8 @@
 """Batched stepping: several states (different meshes, m, eps) advanced with
 one launch per pass.  Each member's result must be bitwise the same as the
-same state stepped alone, and the two-instance torus + ellipsoid workload
-must match the oracle."""
+same state stepped alone -- also when the members' grids together exceed the
+blocks resident at once, as for the two-instance torus + ellipsoid workload
+at full size -- and that workload must match the oracle over 50 steps."""
 
 import numpy as np
 import pytest
@@ -87,3 +88,71 @@ def test_torus_and_ellipsoid_batched_against_oracle(seg, m):
         Ug = seg.seg_get_u(st)
         assert np.abs(Ug - U).max() <= 1e-4 * np.abs(U).max()
         assert rel(seg.seg_energy(st)["total"], o.energy(xyz, tri, K, U, eps)["total"]) <= 1e-5
+
+
+def _pair(seg, m, seeds=(1237, 1238)):
+    meshes = [w.torus(1024, 512, 1.0, 0.4), w.ellipsoid(8, 1.0, 0.8, 0.6)]
+    states = [make_state(seg, xyz, tri, 5e-6, m, 1e-3, 1, seed=sd, check_every=1, energy_tol=-1.0)
+              for (xyz, tri), sd in zip(meshes, seeds)]
+    return meshes, states
+
+
+def test_full_size_pair_batched_is_bitwise_the_pair_alone(seg):
+    """The two-instance workload (torus 1024 x 512 and the level-8
+    ellipsoid, m = 12) in the default launch geometry (two blocks per SM for
+    each member, so the two grids together need twice the blocks resident at
+    once): 20 steps of each member alone, then 40 batched steps, equal 60
+    steps of each member alone."""
+    _, alone = _pair(seg, 12)
+    _, batched = _pair(seg, 12)
+    for sa, sb in zip(alone, batched):
+        seg.seg_step(sa, 60)
+        seg.seg_step(sb, 20)
+        assert seg.seg_launch_info(sa) == seg.seg_launch_info(sb)
+    b = seg.seg_batch_create(batched)
+    seg.seg_batch_step(b, 40)
+    for sa, sb in zip(alone, batched):
+        assert np.array_equal(seg.seg_get_u(sa), seg.seg_get_u(sb))
+        ta, tb = seg.seg_get_stats(sa), seg.seg_get_stats(sb)
+        assert ta["cg_iterations"] == tb["cg_iterations"] and ta["steps"] == tb["steps"]
+
+
+def test_full_size_pair_batched_50_steps_against_oracle(seg):
+    """Config 4 batched for 50 steps against the FP64 oracle (stored values
+    of tests/golden/longrun_torus1024_m12.json and _ellipsoid8_m12.json,
+    written by tests/golden/make_longrun.py from the oracle alone): total
+    energy and per-component D_i within 1e-5 at steps 25 and 50, sampled rows
+    within 1e-4, labels equal off the interface."""
+    import json
+    import os
+
+    gold = []
+    for name in ("torus1024_m12", "ellipsoid8_m12"):
+        with open(os.path.join(os.path.dirname(__file__), "golden", f"longrun_{name}.json")) as f:
+            gold.append(json.load(f))
+    meshes, states = _pair(seg, 12, seeds=(gold[0]["seed"], gold[1]["seed"]))
+    b = seg.seg_batch_create(states)
+    done = 0
+    for k, cp in enumerate(gold[0]["oracle"]["checkpoints"]):
+        if cp["step"] > done:
+            seg.seg_batch_step(b, cp["step"] - done)
+            done = cp["step"]
+        for g, st in zip(gold, states):
+            ref = g["oracle"]["checkpoints"][k]
+            assert ref["step"] == done
+            e = seg.seg_energy(st)
+            lam, _ = seg.seg_eigenvalue_estimates(st)
+            assert rel(e["total"], ref["total"]) <= 1e-5, (g["case"], done, e["total"], ref["total"])
+            D = np.array(ref["D"])
+            assert np.abs(lam - D).max() <= 1e-5 * np.abs(D).max(), (g["case"], done)
+    for g, st in zip(gold, states):
+        U = seg.seg_get_u(st)
+        idx = np.array(g["sample"]["vertices"])
+        Uo = np.array(g["sample"]["u"])
+        err = np.abs(U[idx] - Uo).max()
+        assert err <= 1e-4 * np.abs(Uo).max(), (g["case"], err)
+        am, _ = seg.seg_labels(st)
+        srt = np.sort(Uo, axis=1)
+        gap = srt[:, -1] - srt[:, -2]
+        off = (np.array(g["sample"]["ring_mixed"]) == 0) & (gap > 2 * err + 1e-6 * srt[:, -1])
+        assert np.array_equal(am[idx][off], np.array(g["sample"]["label"])[off])
