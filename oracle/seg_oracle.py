@@ -11,15 +11,21 @@ partition problem on surfaces").
 Everything is float64.  Arrays are vertex-major: ``U[z, i]`` is component i
 at vertex z.  Inputs (meshes, random initial values) come from ``workload``.
 
-Readings of the paper taken here (each is explained in the design notes):
+Readings of the paper taken here:
 
 * Step 2 exponent factor is 2*tau/eps^2 (the ODE of Algorithm 2.2 step 2 and
   its practical version agree on the 2; the displayed exact solution drops it).
-* Consistent mass matrix in steps 1 and 3, nodal values in step 2.
-* Reported "total energy" = sum_i D_i + S_eps (the tables of Sec. 3), with
+* Consistent mass matrix in steps 1 and 3 (the L2(Gamma_h) norm of step 3 is
+  the consistent one; step 1 is the Galerkin form), nodal values in step 2.
+* Reported "total energy" = sum_i D_i + S_eps (the tables of Sec. 3 add the
+  eigenvalue estimates and S_eps: e.g. 3 * 3.605 + 0.072 = 10.887), with
   D_i = |u_i|_{H^1}^2; the functional of Problem 2.1 = 0.5 sum_i D_i + S_eps.
+  Summing the lambda formula of Sec. 1.1 over i gives sum D_i + 2 S_eps,
+  twice the functional (the paper prints E + 2 int F, which does not follow
+  from its own definitions).
 * The quartic S_eps integrand is integrated exactly (the paper is silent).
-* The linear solve of step 1 is done to rtol 1e-14 (the paper gives none).
+* The linear solve of step 1 is done to rtol 1e-14 (the paper gives none;
+  with this tolerance the result does not depend on the solver's start).
 
 Parity status: every function below is pinned by tests in
 ``tests/test_oracle_pins.py`` against closed forms, textbook routines,

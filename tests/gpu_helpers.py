@@ -37,10 +37,11 @@ def oracle_run(xyz, tri, U0, tau, eps, steps):
 
 def interface_mask(tri, U, n, gap_tol=0.0):
     """Vertices whose 1-ring holds >= 2 distinct oracle labels, or whose
-    top-two gap is below max(1e-6 of the row maximum, gap_tol) (the
-    label-comparison exclusion of the design notes; pass gap_tol = twice the
-    observed max |u_gpu - u_oracle| so that no decision within the numerical
-    error is compared)."""
+    top-two gap is below max(1e-6 of the row maximum, gap_tol): the vertices
+    on or next to an interface between components, where the argmax label is
+    not determined by the solution to within the numerical error (pass gap_tol
+    = twice the observed max |u_gpu - u_oracle|, so that no decision within
+    that error is compared)."""
     am = np.argmax(U, axis=1)
     e = np.concatenate([tri[:, [0, 1]], tri[:, [1, 2]], tri[:, [2, 0]]], 0)
     A = sp.coo_matrix((np.ones(len(e)), (e[:, 0], e[:, 1])), shape=(n, n)).tocsr()
