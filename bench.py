@@ -34,10 +34,12 @@ if ROOT not in sys.path:
 HBM_FALLBACK_GBS = 6800.0
 HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e, nominal
 # DRAM bytes (read + write) per launch of each hot-path kernel, from one ncu
-# capture of the level-8 sphere, m = 16, mixed precision (dram__bytes_read.sum
-# + dram__bytes_write.sum); valid only for the kernel versions captured (None:
-# no capture of the current version).
-TRAFFIC = {"k_cg_a": None, "k_start": None, "k_cg_b": None, "k_energy_check": None, "k_finish": None}
+# capture of the level-8 sphere, m = 16, mixed precision, in the steady state
+# (one CG iteration per step: CG pass A in its first-iteration form, the
+# finish pass with one pending update; dram__bytes_read.sum +
+# dram__bytes_write.sum, mean of two launches, default geometry of 304
+# blocks); valid only for the kernel versions captured.
+TRAFFIC = {"k_cg_a": 118.3e6, "k_start": 197.5e6, "k_cg_b": 91.6e6, "k_energy_check": 63.1e6, "k_finish": 281.0e6}
 KERNEL_ROLE = {
     "k_start": "start pass: r0 = -tau K X - A y for the predicted correction y, z0 = D^-1 r0, norms "
                "(issue and latency bound: three sparse products and three float-float sums per row)",
