@@ -93,7 +93,8 @@ typedef struct {
   int64_t wait_limit_ns; /* limit of each bounded device wait for data staged by the bulk-copy
                             engine (0: 1 s).  A wait that runs out records SEG_ERR_TIMEOUT and
                             halts the run; the copies still in flight are then waited for with
-                            the 1 s limit before the kernel returns */
+                            the 1 s limit before the kernel returns.  Limits below 2 us are
+                            counted in SM clock cycles, 2 per ns */
   double energy_rtol;    /* relative form of the stop rule (0: off): stop also when
                             |total_k - total_{k - M_tau}| <= energy_rtol |total_k|; with
                             check_every = round(dt / tau) it bounds the energy's relative rate of
@@ -417,7 +418,7 @@ seg_status seg_get_stats(seg_state* s, seg_stats* out);
  * ticket stays valid until SEG_STATS_RING more copies have been enqueued
  * (SEG_ERR_ARG after that, or for a ticket never issued).  Each copy moves
  * SEG_STATS_COPY_BYTES bytes (the state's control block) from the device. */
-#define SEG_STATS_COPY_BYTES 2952
+#define SEG_STATS_COPY_BYTES 3208
 #define SEG_STATS_RING 8
 seg_status seg_stats_enqueue(seg_state* s, int32_t* ticket);
 seg_status seg_stats_wait(seg_state* s, int32_t ticket, seg_stats* out);

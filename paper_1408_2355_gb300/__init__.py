@@ -583,7 +583,7 @@ def seg_get_stats(state: State) -> dict:
 
 
 SEG_STATS_RING = 8
-SEG_STATS_COPY_BYTES = 2952
+SEG_STATS_COPY_BYTES = 3208
 
 
 def seg_stats_enqueue(state: State) -> int:

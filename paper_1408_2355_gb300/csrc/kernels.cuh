@@ -497,12 +497,16 @@ __device__ __forceinline__ bool mbar_test_wait(unsigned long long* bar, unsigned
 __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, unsigned long long limit_ns) {
   if (limit_ns < kSuspendNs) {
     // a limit shorter than one suspension: non-blocking probes only (a
-    // suspended try may outlast the limit by the time the data needs)
+    // suspended try may outlast the limit by the time the data needs),
+    // timed in SM clock cycles, 2 per ns (the global timer may tick only
+    // every microsecond, which would let data that takes less than that
+    // arrive within any shorter limit)
     if (mbar_test_wait(bar, parity)) return true;
-    const unsigned long long t0 = global_ns();
+    const long long t0 = clock64();
+    const long long cycles = 2 * (long long)limit_ns;
     for (unsigned n = 0; n < (1u << 26); ++n) {
       if (mbar_test_wait(bar, parity)) return true;
-      if (global_ns() - t0 > limit_ns) return false;
+      if (clock64() - t0 > cycles) return false;
     }
     return false;
   }
@@ -865,6 +869,7 @@ __device__ __forceinline__ void body_start(const KArgs<T>& a, const int vb, cons
     ctl->lam[c] = (real && n2 > 0.0) ? ukt / n2 : 0.0;
     ctl->tol2[c] = a.rtol2 * bbt;
     ctl->rz[c] = rz;
+    ctl->rr0[c] = rrt;
     ctl->alpha[0][c] = 0.0;
     ctl->alpha[1][c] = 0.0;
     ctl->beta[c] = 0.0;
@@ -875,6 +880,7 @@ __device__ __forceinline__ void body_start(const KArgs<T>& a, const int vb, cons
   const int anybad = __syncthreads_or(bad);
   if (threadIdx.x == 0) {
     ctl->it = 0;
+    ctl->dir_in_z = 0;
     int cont = (any && !anybad && ctl->halted != 2) ? 1 : 0;
     if (anybad) {
       ctl->status |= 2;
@@ -898,7 +904,10 @@ __device__ __forceinline__ void body_start(const KArgs<T>& a, const int vb, cons
 // one read and write of y saved per two iterations; the finish pass applies
 // what is left.  The first iteration of a solve has no previous direction:
 // p_1 = z_0 and q_1 = A z_0, and the direction buffers (which hold values of
-// the previous solve) are neither staged nor read.
+// the previous solve) are neither staged nor read.  That pass also finds the
+// residual norm after the iteration and ends the solve when every component
+// has converged, in which case CG pass B has nothing to do (once a run has
+// settled, the predicted start leaves one iteration per solve).
 // Padded ELL entries point at the row itself with value 0 (no branches).
 template <typename T, int LPR, int W, int FORM>
 __device__ __forceinline__ void body_cg_a_rows(const KArgs<T>& a, const int vb, const int vg, const int it) {
@@ -911,11 +920,13 @@ __device__ __forceinline__ void body_cg_a_rows(const KArgs<T>& a, const int vb, 
   __shared__ __align__(8) unsigned long long bars[NW][kPipeStages];
   // read now what the last block needs after the grid sum (written only by
   // other kernels), so that it does not wait for them at the end
-  __shared__ double pre_rz[kMaxCols];
+  __shared__ double pre_rz[kMaxCols], pre_tol2[kMaxCols], pre_rr0[kMaxCols];
   __shared__ int pre_act[kMaxCols];
   if ((int)threadIdx.x < a.ms) {
     pre_rz[threadIdx.x] = ctl->rz[threadIdx.x];
     pre_act[threadIdx.x] = ctl->active[threadIdx.x];
+    pre_tol2[threadIdx.x] = ctl->tol2[threadIdx.x];
+    pre_rr0[threadIdx.x] = ctl->rr0[threadIdx.x];
   }
   const T* Pold = (it & 1) ? a.P1 : a.P0;
   T* Pnew = (it & 1) ? a.P0 : a.P1;
@@ -928,9 +939,20 @@ __device__ __forceinline__ void body_cg_a_rows(const KArgs<T>& a, const int vb, 
     al2[v] = (T)ctl->alpha[(it + 1) & 1][c0 + v];  // alpha_{j-2} (this pass overwrites it with alpha_j)
     ysc[v] = it == 1 ? (T)ctl->ysc[c0 + v] : T(1);  // the first update starts from w Y
   }
-  Acc acc[1][VW];
+  // p.q; in the first iteration also r0.q and q.q (r0 = D z0), from which
+  // and the start pass's ||r0||^2 the last block finds the residual of the
+  // iterate after this iteration without CG pass B.  A lane sums its rows'
+  // terms of these two in plain T (few registers: the gathers of the
+  // neighbour rows keep theirs) and adds the sums to the grid sum at the end.
+  constexpr int ND = FORM == kCgFirst ? 3 : 1;
+  Acc acc[ND][VW];
 #pragma unroll
-  for (int v = 0; v < VW; ++v) acc[0][v].zero();
+  for (int d = 0; d < ND; ++d)
+#pragma unroll
+    for (int v = 0; v < VW; ++v) acc[d][v].zero();
+  T rq[VW], qq[VW];
+#pragma unroll
+  for (int v = 0; v < VW; ++v) rq[v] = qq[v] = T(0);
   typename Stage::Src src;
   src.ell = a.ell_col;
   src.val[0] = a.valA;
@@ -986,17 +1008,59 @@ __device__ __forceinline__ void body_cg_a_rows(const KArgs<T>& a, const int vb, 
           v_fma(pn, beta, po, zi);
           v_fma(q, beta, qo, q);
         }
-        st(Pnew + (row * ms + c0), pn);
+        // (p_1 = z_0 stays in Z: CG pass B copies it to P1 if the solve goes on)
+        if constexpr (FORM != kCgFirst) st(Pnew + (row * ms + c0), pn);
         st(a.Q + (row * ms + c0), q);
         v_add_prods(acc[0], pn, q);
+        if constexpr (FORM == kCgFirst) {
+          T r0[VW];
+          v_scale(r0, __ldg(a.diagA + row), zi);
+          v_fma(rq, r0, q, rq);
+          v_fma(qq, q, q, qq);
+        }
       });
+  if constexpr (FORM == kCgFirst) {
+#pragma unroll
+    for (int v = 0; v < VW; ++v) {
+      acc[1 % ND][v].add_val(rq[v]);
+      acc[2 % ND][v].add_val(qq[v]);
+    }
+  }
   if (__syncthreads_or(!ok) && threadIdx.x == 0) report_timeout(ctl);
-  __shared__ double tot[1][kMaxCols];
-  if (!grid_reduce<T, LPR, 1>(acc, a, kCtrCgA, tot, vb, vg)) return;
+  __shared__ double tot[ND][kMaxCols];
+  if (!grid_reduce<T, LPR, ND>(acc, a, kCtrCgA, tot, vb, vg)) return;
   const int c = threadIdx.x;
+  int open = 0;
   if (c < a.ms) {
     const double pq = tot[0][c];
-    ctl->alpha[(it + 1) & 1][c] = (pre_act[c] && pq > 0.0) ? pre_rz[c] / pq : 0.0;
+    const double al = (pre_act[c] && pq > 0.0) ? pre_rz[c] / pq : 0.0;
+    ctl->alpha[(it + 1) & 1][c] = al;
+    if constexpr (FORM == kCgFirst) {
+      // ||r1||^2 = ||r0 - alpha q||^2 = r0.r0 - 2 alpha r0.q + alpha^2 q.q.
+      // The lanes' plain sums of a few dozen rows are accurate to well
+      // within 1e-4 (float) or 1e-10 (double) of sum |terms|, and
+      // 2 |alpha r0.q| <= r0.r0 + alpha^2 q.q, so that margin times
+      // (r0.r0 + alpha^2 q.q) bounds the rounding of the difference: a
+      // component within it of its tolerance is left to CG pass B
+      const double rr0 = pre_rr0[c], qqs = tot[2 % ND][c];
+      const double r1sq = rr0 - 2.0 * al * tot[1 % ND][c] + al * al * qqs;
+      const double margin = (sizeof(T) == 4 ? 1e-4 : 1e-10) * (rr0 + al * al * qqs);
+      open = (pre_act[c] && !(r1sq + margin <= pre_tol2[c])) ? 1 : 0;
+    }
+  }
+  if constexpr (FORM == kCgFirst) {
+    // every component converged in this first iteration: the solve ends here
+    // and CG pass B (residual update, r.z, beta) is not needed.  (Timing runs
+    // repeat the pass on the same data and leave the counters alone.)
+    if (!a.force && !__syncthreads_or(open)) {
+      if (c < a.ms) ctl->active[c] = 0;
+      if (threadIdx.x == 0) {
+        ctl->it = 1;
+        ctl->cont = 0;
+        ctl->dir_in_z = 1;
+        if (a.set_cond) cudaGraphSetConditional(a.cond, 0);
+      }
+    }
   }
 }
 
@@ -1400,6 +1464,7 @@ __device__ __forceinline__ void body_cg_b(const KArgs<T>& a, const int vb, const
     for (int u = 0; u < RU; ++u) {
       const unsigned row = base + u * RPW + rs;
       if ((int)row < r1) {
+        if (it == 0) st(a.P1 + (row * ms + c0), z[u]);  // p_1 = z_0, left in Z by the first pass A
         T r[VW], dq[VW];
         v_scale(dq, di[u], q[u]);
         v_fma(z[u], nal, dq, z[u]);
@@ -1464,7 +1529,9 @@ __device__ __forceinline__ void body_finish_rows(const KArgs<T>& a, const int vb
   DevCtl* ctl = a.ctl;
   SEG_ROW_SETUP
   const int lbase = lane - cg;
-  const T* P = (it & 1) ? a.P1 : a.P0;
+  // the last direction; after a solve of one iteration that ended in CG
+  // pass A it is z_0, still in Z
+  const T* P = (it == 1 && ctl->dir_in_z) ? a.Z : ((it & 1) ? a.P1 : a.P0);
   const T* P2 = (it & 1) ? a.P0 : a.P1;
   // history slots of the corrections: two (quadratic prediction) for
   // float, three (cubic) for double; step j's correction is in H[j % NH]

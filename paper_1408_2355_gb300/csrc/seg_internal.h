@@ -40,6 +40,7 @@ struct DevCtl {
   double lam[kMaxCols];       // D_i = u_i^T K u_i of the normalised state
   double tol2[kMaxCols];      // (cg_rtol ||M X_i||_2)^2
   double rz[kMaxCols];        // r^T D^-1 r of the current CG iterate
+  double rr0[kMaxCols];       // ||r_0||_2^2, the initial residual of the current solve
   double alpha[2][kMaxCols];  // CG step length of the last two iterations
   double beta[kMaxCols];      // CG direction update factor
   double coup[kMaxCols];      // int u_i^2 sum_{j != i} u_j^2 (normalised state)
@@ -60,7 +61,7 @@ struct DevCtl {
   double e_s;
   double e_prev;              // total of the previous stop-rule check
   int have_prev;
-  int pad0;
+  int dir_in_z;               // the solve ended after one iteration in CG pass A: its direction p_1 = z_0 is in Z
   long long step_mark;        // ctl->step when the last batch of steps was enqueued
   unsigned long long launches;  // hot-path kernel launches (block 0 counts each)
   unsigned int counters[kNumCounters];
