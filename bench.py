@@ -39,7 +39,7 @@ HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e, nominal
 # finish pass with one pending update; dram__bytes_read.sum +
 # dram__bytes_write.sum, mean of two launches, default geometry of 304
 # blocks); valid only for the kernel versions captured.
-TRAFFIC = {"k_cg_a": 118.3e6, "k_start": 197.5e6, "k_cg_b": 91.6e6, "k_energy_check": 63.1e6, "k_finish": 281.0e6}
+TRAFFIC = {"k_cg_a": None, "k_start": None, "k_cg_b": None, "k_energy_check": None, "k_finish": None}
 KERNEL_ROLE = {
     "k_start": "start pass: r0 = -tau K X - A y for the predicted correction y, z0 = D^-1 r0, norms "
                "(issue and latency bound: three sparse products and three float-float sums per row)",
@@ -300,6 +300,32 @@ def cpu_baseline(a):
 # ---------------------------------------------------------------- our arm
 
 
+class nvtx_range:
+    """An NVTX push/pop range (a no-op where NVTX is unavailable): the kernel
+    timing launches run inside "time_<kernel>", so that a profiler capture
+    can select them (ncu --nvtx --nvtx-include "time_<kernel>/")."""
+
+    def __init__(self, name):
+        self.name, self.pushed = name, False
+
+    def __enter__(self):
+        try:
+            import torch
+
+            torch.cuda.nvtx.range_push(self.name)
+            self.pushed = True
+        except Exception:
+            pass
+        return self
+
+    def __exit__(self, *exc):
+        if self.pushed:
+            import torch
+
+            torch.cuda.nvtx.range_pop()
+        return False
+
+
 def measured_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -317,10 +343,12 @@ def kernel_bytes(n, ntri, m_pad, s, W=8):
     are W int32 columns plus W values per vertex, the Jacobi diagonal N * s.
       k_start  read X and the carried correction Y, write Z, columns + K + M + A values,
                Jacobi inverse diagonal
-      k_cg_a   first iteration of a solve: read z; write p = z and q = A z; columns + A
-               values; later even iterations also read p_old and q_old; odd iterations
-               also read Y and p_{j-2} and write Y (two solution updates)
-      k_cg_b   read Z, q; write Z; diagonal of A and its inverse
+      k_cg_a   first iteration of a solve: read z and the diagonal of A; write q = A z
+               (p = z stays in Z); columns + A values; later even iterations also read
+               p_old and q_old and write p; odd iterations also read Y and p_{j-2} and
+               write Y (two solution updates)
+      k_cg_b   read Z, q; write Z; diagonal of A and its inverse; in the first iteration of
+               a solve that goes on also write p_1 = z_0
       k_finish read X, Y, the last two corrections and p (with two pending updates, after an
                odd count of 3 or more, also p of the iteration before); write X, the next
                step's predicted correction Y and this step's correction (over the older of the
@@ -331,10 +359,11 @@ def kernel_bytes(n, ntri, m_pad, s, W=8):
     ell = n * W * 4
     return {
         "k_start": 3 * V + ell + 3 * n * W * s + n * s,
-        "k_cg_a_first": 3 * V + ell + n * W * s,
+        "k_cg_a_first": 2 * V + ell + n * W * s + n * s,
         "k_cg_a_even": 5 * V + ell + n * W * s,
         "k_cg_a_odd": 8 * V + ell + n * W * s,
         "k_cg_b": 3 * V + 2 * n * s,
+        "k_cg_b_first": 4 * V + 2 * n * s,
         "k_finish_one": 8 * V,
         "k_finish_two": 9 * V,
         "k_energy_check": V + ntri * (12 + s),
@@ -343,16 +372,21 @@ def kernel_bytes(n, ntri, m_pad, s, W=8):
 
 
 def pass_counts(kcg):
-    """Launches per step of each form of CG pass A and of the finish pass for
-    a mean of kcg CG iterations per step (linear between the two integer
+    """Launches per step of each form of the CG passes and of the finish pass
+    for a mean of kcg CG iterations per step (linear between the two integer
     counts around it): a solve of k >= 1 iterations runs pass A once in its
     first form, floor(k / 2) times in its odd form and ceil(k / 2) - 1 times in
-    its later even form; its finish pass has two pending updates when k is
-    odd and at least 3."""
+    its later even form; pass B not at all when k = 1 (the first pass A ends
+    the solve), else once in its first form and k - 1 times in its later form;
+    the finish pass has two pending updates when k is odd and at least 3.
+    (A solve of one iteration whose residual lies within the first pass A's
+    rounding margin of the tolerance also runs pass B; not counted.)"""
     def at(k):
         if k <= 0:
-            return {"first": 0.0, "odd": 0.0, "even": 0.0, "fin_one": 1.0, "fin_two": 0.0}
+            return {"first": 0.0, "odd": 0.0, "even": 0.0, "b_first": 0.0, "b_later": 0.0,
+                    "fin_one": 1.0, "fin_two": 0.0}
         return {"first": 1.0, "odd": float(k // 2), "even": float((k + 1) // 2 - 1),
+                "b_first": 1.0 if k >= 2 else 0.0, "b_later": float(k - 1) if k >= 2 else 0.0,
                 "fin_one": 0.0 if (k % 2 == 1 and k >= 3) else 1.0,
                 "fin_two": 1.0 if (k % 2 == 1 and k >= 3) else 0.0}
     lo = int(math.floor(kcg))
@@ -408,7 +442,8 @@ def run_ours(a, rank, ws, local):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        seg.seg_step(st, K)  # the public call: enqueues in chunks, reviewing the step graph as it goes
+        with nvtx_range("timed_window"):
+            seg.seg_step(st, K)  # the public call: enqueues in chunks, reviewing the step graph as it goes
         e1.record(stream)
         torch.cuda.synchronize()
         barrier(ws)
@@ -485,9 +520,10 @@ def run_ours(a, rank, ws, local):
     kern = {}
     # seg_time_kernel selectors of each kernel form
     names = {"k_start": 0, "k_cg_a_first": 1, "k_cg_b": 2, "k_finish_one": 3, "k_energy_check": 4, "k_energy": 5,
-             "k_cg_a_odd": 6, "k_finish_two": 7, "k_cg_a_even": 8}
+             "k_cg_a_odd": 6, "k_finish_two": 7, "k_cg_a_even": 8, "k_cg_b_first": 9}
     for name, which in names.items():
-        t = seg.seg_time_kernel(st, which, 20)
+        with nvtx_range("time_" + name):
+            t = seg.seg_time_kernel(st, which, 20)
         kern[name] = {"ms": t, "bytes": kb[name], "GBps": kb[name] / (t / 1e3) / 1e9,
                       "frac": kb[name] / (t / 1e3) / 1e9 / peak}
     seg.seg_set_checkpoint(st, kept["ck"].numpy())  # the timing launches overwrote the state
@@ -507,7 +543,7 @@ def run_ours(a, rank, ws, local):
         "k_start": (kern["k_start"]["ms"], kb["k_start"], 1.0),
         "k_energy_check": (kern["k_energy_check"]["ms"], kb["k_energy_check"], 1.0),
         "k_cg_a": mix([("k_cg_a_first", pc["first"]), ("k_cg_a_odd", pc["odd"]), ("k_cg_a_even", pc["even"])]),
-        "k_cg_b": (kern["k_cg_b"]["ms"], kb["k_cg_b"], kcg),
+        "k_cg_b": mix([("k_cg_b_first", pc["b_first"]), ("k_cg_b", pc["b_later"])]),
         "k_finish": mix([("k_finish_one", pc["fin_one"]), ("k_finish_two", pc["fin_two"])]),
     }
     share = {k: t * c for k, (t, _, c) in per.items()}

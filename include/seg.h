@@ -253,6 +253,15 @@ seg_status seg_set_checkpoint(seg_state* s, const void* buf, uint64_t bytes);
  * was built with. */
 seg_status seg_set_wait_limit(seg_state* s, int64_t ns);
 
+/* Testing aid for the failure path (on != 0 / 0 = off).  While on, every
+ * staged pass of the state's steps first waits, with the state's wait limit,
+ * on a device barrier that nothing completes, so that the wait runs out: the
+ * step records SEG_ERR_TIMEOUT and halts the run exactly as when staged data
+ * does not arrive in time.  The copies already issued still land and are
+ * waited for before the kernel returns; no GPU fault is involved.  Takes
+ * effect at the next step (not in batches built earlier). */
+seg_status seg_set_wait_stall(seg_state* s, int32_t on);
+
 /* ------------------------------------------------------------------- steps */
 
 /* Algorithm 2.2: advance up to nsteps steps.  Stops early when the Sec. 2.2
@@ -435,7 +444,9 @@ const char* seg_last_error(void);
  * one iteration runs), 8 = CG pass A as in a later even iteration (also the
  * direction update p = z + beta p), 6 = CG pass A as in an odd iteration
  * (which also applies the two pending solution updates), 2 = CG pass B
- * (residual update + dots), 3 = finish pass (last solution update + nodal ODE)
+ * (residual update + dots) in a later iteration, 9 = CG pass B in the first
+ * iteration of a solve that goes on (which also copies p_1 = z_0 out of the
+ * residual buffer), 3 = finish pass (last solution update + nodal ODE)
  * with one pending update, 7 = the same with two (after an odd count of 3 or
  * more), 4 = energy pass of the stop rule (S_eps), 5 = energy pass with the
  * per-component coupling integrals.  The kernels run on the state's own

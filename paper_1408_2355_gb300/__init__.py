@@ -53,7 +53,7 @@ EXPORTED = [
     "seg_batch_create", "seg_batch_step", "seg_batch_step_async", "seg_batch_sync", "seg_batch_destroy",
     "seg_server_create", "seg_server_submit", "seg_server_tick", "seg_server_info", "seg_server_result",
     "seg_server_clock", "seg_server_destroy", "seg_state_bytes",
-    "seg_checkpoint_size", "seg_get_checkpoint", "seg_set_checkpoint", "seg_set_wait_limit",
+    "seg_checkpoint_size", "seg_get_checkpoint", "seg_set_checkpoint", "seg_set_wait_limit", "seg_set_wait_stall",
 ]
 
 
@@ -187,6 +187,7 @@ _SIG = {
     "seg_get_checkpoint": [_vp, _vp, C.c_uint64],
     "seg_set_checkpoint": [_vp, _vp, C.c_uint64],
     "seg_set_wait_limit": [_vp, _i64],
+    "seg_set_wait_stall": [_vp, _i32],
 }
 for _name, _args in _SIG.items():
     _f = getattr(lib, _name)
@@ -420,6 +421,10 @@ def seg_set_checkpoint(state: State, buf):
 
 def seg_set_wait_limit(state: State, ns: int):
     _check(lib.seg_set_wait_limit(state.ptr, int(ns)))
+
+
+def seg_set_wait_stall(state: State, on: bool):
+    _check(lib.seg_set_wait_stall(state.ptr, 1 if on else 0))
 
 
 def seg_step(state: State, nsteps: int, ok_not_converged: bool = False) -> int:

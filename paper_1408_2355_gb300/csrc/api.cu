@@ -77,6 +77,7 @@ struct seg_state {
   double energy_rtol = 0;
   long long max_steps = 0;
   unsigned long long wait_ns = kDefaultWaitNs;  // limit of one bounded device wait
+  int stall_waits = 0;                          // seg_set_wait_stall
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int launch_mode = 0;
@@ -266,14 +267,17 @@ seg_status direct_step(seg_state* s) {
 // Mean duration of `reps` back-to-back launches of hot-path kernel `which`
 // (see seg_time_kernel) on the state's buffers, after one warm-up launch.
 seg_status time_launches(seg_state* s, int which, int reps, double* ms_per_launch) {
-  void* fns[] = {s->ks.start, s->ks.cg_a,         s->ks.cg_b, s->ks.finish,
-                 s->ks.energy_check, s->ks.energy, s->ks.cg_a, s->ks.finish, s->ks.cg_a};
-  if (which == 1 || which == 6 || which == 8 || which == 3 || which == 7) {
+  void* fns[] = {s->ks.start,        s->ks.cg_a,   s->ks.cg_b,   s->ks.finish, s->ks.energy_check,
+                 s->ks.energy,       s->ks.cg_a,   s->ks.finish, s->ks.cg_a,   s->ks.cg_b};
+  if (which != 0 && which != 4 && which != 5) {
     // the iteration count the pass sees selects its form: CG pass A as the
     // first iteration of a solve (1), an odd one (6: also the two pending
-    // solution updates) or a later even one (8); the finish pass with one
-    // pending update (3) or two (7, after an odd count of 3 or more)
-    const int it = which == 1 ? 0 : (which == 6 ? 1 : (which == 8 || which == 3 ? 2 : 3));
+    // solution updates) or a later even one (8); CG pass B in a later
+    // iteration (2) or the first (9: also copies p_1 = z_0); the finish pass
+    // with one pending update (3) or two (7, after an odd count of 3 or more).
+    // Forced launches leave the count as it is.
+    static const int it_of[] = {0, 0, 1, 2, 0, 0, 1, 3, 2, 0};
+    const int it = it_of[which];
     SEG_CUDA(cudaMemcpyAsync(&s->ctl->it, &it, sizeof(int), cudaMemcpyHostToDevice, s->stream));
     SEG_CUDA(cudaStreamSynchronize(s->stream));
   }
@@ -412,6 +416,7 @@ void fill_args(seg_state* s) {
   a.energy_rtol = s->energy_rtol;
   a.max_steps = s->max_steps;
   a.wait_ns = s->wait_ns;
+  a.stall_waits = s->stall_waits;
 }
 
 template <typename T>
@@ -1097,6 +1102,17 @@ seg_status seg_set_wait_limit(seg_state* s, int64_t ns) {
   else
     args_of<double>(s).wait_ns = s->wait_ns;
   retire_graph(s);  // the step graph holds the arguments it was built with
+  return SEG_OK;
+}
+
+seg_status seg_set_wait_stall(seg_state* s, int32_t on) {
+  if (!s) return fail(SEG_ERR_ARG, "state is NULL");
+  s->stall_waits = on != 0 ? 1 : 0;
+  if (s->prec == SEG_MIXED_FP32)
+    args_of<float>(s).stall_waits = s->stall_waits;
+  else
+    args_of<double>(s).stall_waits = s->stall_waits;
+  retire_graph(s);
   return SEG_OK;
 }
 
@@ -1803,7 +1819,7 @@ seg_status seg_stats_wait(seg_state* s, int32_t ticket, seg_stats* out) {
 
 seg_status seg_time_kernel(seg_state* s, int32_t which, int32_t reps, double* ms_per_launch) {
   if (!s || !ms_per_launch) return fail(SEG_ERR_ARG, "state or output is NULL");
-  if (which < 0 || which > 8 || reps < 1) return fail(SEG_ERR_ARG, "which must be 0..8 and reps >= 1");
+  if (which < 0 || which > 9 || reps < 1) return fail(SEG_ERR_ARG, "which must be 0..9 and reps >= 1");
   SEG_CUDA(cudaSetDevice(s->p->device));
   seg_status st = time_launches(s, which, reps, ms_per_launch);
   s->pending = true;
@@ -1821,9 +1837,12 @@ seg_status seg_autotune(seg_state* s, int32_t reps, seg_tune_result* out) {
   if (st != SEG_OK) return st;
   // CG iterations per step so far (the weight of the two CG passes)
   const double k = s->hctl->step > 0 ? (double)s->hctl->cg_total / (double)s->hctl->step : 8.0;
+  // CG pass B launches per step: none in a solve of one iteration (it ends
+  // in CG pass A), j in a solve of j >= 2 (mixing counts of 1 and 2 below 2)
+  const double kb = k >= 2.0 ? k : std::max(0.0, 2.0 * (k - 1.0));
   // save the data the timing launches overwrite: X, Y, H0, H1 and the control block;
   // Z, P and Q are rewritten by every step before they are read (the first
-  // CG pass multiplies the old P by beta = 0, so any finite P will do)
+  // CG pass of a solve does not read P)
   const size_t vbytes = (size_t)s->p->n * s->ms * vsize(s->prec);
   void* saved_x = nullptr;  // X, Y and the history slots
   DevCtl* saved_ctl = nullptr;
@@ -1882,7 +1901,7 @@ seg_status seg_autotune(seg_state* s, int32_t reps, seg_tune_result* out) {
     if (st == SEG_OK) st = time_launches(s, 6, reps, &t_odd);
     if (st != SEG_OK) break;
     t[1] = 0.5 * (t[1] + t_odd);
-    const double model = t[0] + k * (t[1] + t[2]) + t[3];
+    const double model = t[0] + k * t[1] + kb * t[2] + t[3];
     if (out->n_candidates < SEG_TUNE_MAX) {
       out->cand_grid[out->n_candidates] = g;
       out->cand_ms[out->n_candidates] = model;
@@ -1894,7 +1913,7 @@ seg_status seg_autotune(seg_state* s, int32_t reps, seg_tune_result* out) {
         best[w] = g;
       }
   }
-  const double best_ms = best_t[0] + k * (best_t[1] + best_t[2]) + best_t[3];
+  const double best_ms = best_t[0] + k * best_t[1] + kb * best_t[2] + best_t[3];
   for (size_t c = 0; c < tris_c.size() && st == SEG_OK; ++c) {
     const int g = tris_c[c];
     if (g > s->grid_e_cap) continue;

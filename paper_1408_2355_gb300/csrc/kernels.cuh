@@ -17,8 +17,12 @@
 //                   renormalisation of the previous step (step 3) is fused here
 //   k_energy_check  (every check_every steps) S_eps and the stop rule
 //   k_cg_a          p = z + beta p_old, q = A z + beta q_old, p.q; every second
-//                   iteration y += the two pending alpha p terms
+//                   iteration y += the two pending alpha p terms.  In the
+//                   first iteration of a solve (p = z) also r.q and q.q, from
+//                   which it finds ||r - alpha q|| and ends the solve when
+//                   every component has converged
 //   k_cg_b          z -= alpha D^-1 q, r.z and r.r (r = D z); convergence, beta
+//                   (not needed after a solve that ended in k_cg_a)
 //   k_finish        x = X + y with the updates still pending, then the exact
 //                   nodal ODE of step 2
 // The two gather kernels stage each warp's next groups of rows (ELL indices,
@@ -664,7 +668,8 @@ __device__ __forceinline__ GroupMap group_map(int n, int rpw, int vb, int vg) {
 // block exits.
 template <typename Stage, typename Body>
 __device__ __forceinline__ bool row_pipeline(unsigned char* smem_warp, unsigned long long* bars, const GroupMap& gm,
-                                             const typename Stage::Src& src, unsigned long long wait_ns, Body body) {
+                                             const typename Stage::Src& src, unsigned long long wait_ns, bool stall,
+                                             Body body) {
   constexpr int NW = kBlockThreads / 32;
   constexpr int RPW = Stage::RPW;
   constexpr int NS = Stage::kStages;
@@ -697,9 +702,23 @@ __device__ __forceinline__ bool row_pipeline(unsigned char* smem_warp, unsigned 
     }
   }
   bool ok = true;
+  if (stall) {
+    // testing aid for the failure path: a bounded wait on a barrier that
+    // nothing completes runs out exactly as a wait for data that does not
+    // arrive would (the copies issued above land and are drained below)
+    __shared__ __align__(8) unsigned long long never[NW];
+    if (lane == 0) {
+      mbar_init(&never[warp], 1);
+      mbar_init_fence();
+    }
+    __syncwarp();
+    ok = __all_sync(0xffffffffu, mbar_wait(&never[warp], 0u, wait_ns));
+    __syncwarp();
+    if (lane == 0) mbar_inval(&never[warp]);
+  }
   unsigned phase = 0;  // bit k: parity of the next completion of stage k
   int s = 0;
-  for (int gi = warp; gi < ngroups; gi += NW) {
+  for (int gi = ok ? warp : ngroups; gi < ngroups; gi += NW) {
     // refill the stage consumed in the previous iteration
     const int gn = gi + (NS - 1) * NW;
     const int sn = s == 0 ? NS - 1 : s - 1;
@@ -788,7 +807,7 @@ __device__ __forceinline__ void body_start(const KArgs<T>& a, const int vb, cons
   src.vec[0] = a.X;
   const bool ok = row_pipeline<Stage>(
       dyn_smem + warp * Stage::kStages * Stage::kBytes, bars[warp], group_map(a.n, RPW, vb, vg), src, a.wait_ns,
-      [&](const Stage& sg, int row0, int nr) {
+      a.stall_waits != 0, [&](const Stage& sg, int row0, int nr) {
         if (rs >= nr) return;
         const unsigned row = row0 + rs;
         int cols[W];
@@ -970,7 +989,7 @@ __device__ __forceinline__ void body_cg_a_rows(const KArgs<T>& a, const int vb, 
   }
   const bool ok = row_pipeline<Stage>(
       dyn_smem + warp * Stage::kStages * Stage::kBytes, bars[warp], group_map(a.n, RPW, vb, vg), src, a.wait_ns,
-      [&](const Stage& sg, int row0, int nr) {
+      a.stall_waits != 0, [&](const Stage& sg, int row0, int nr) {
         if (rs >= nr) return;
         const unsigned row = row0 + rs;
         int cols[W];
@@ -1050,13 +1069,15 @@ __device__ __forceinline__ void body_cg_a_rows(const KArgs<T>& a, const int vb, 
   }
   if constexpr (FORM == kCgFirst) {
     // every component converged in this first iteration: the solve ends here
-    // and CG pass B (residual update, r.z, beta) is not needed.  (Timing runs
-    // repeat the pass on the same data and leave the counters alone.)
+    // and CG pass B (residual update, r.z, beta) has nothing to do.  The loop
+    // flag is left to pass B, which returns at once and clears it: a batched
+    // pass A maps its blocks to the members from their flags as its blocks
+    // start, so no flag may change while it runs.  (Timing runs repeat the
+    // pass on the same data and leave the counters alone.)
     if (!a.force && !__syncthreads_or(open)) {
       if (c < a.ms) ctl->active[c] = 0;
       if (threadIdx.x == 0) {
         ctl->it = 1;
-        ctl->cont = 0;
         ctl->dir_in_z = 1;
         if (a.set_cond) cudaGraphSetConditional(a.cond, 0);
       }
@@ -1426,6 +1447,14 @@ __device__ __forceinline__ void body_cg_b(const KArgs<T>& a, const int vb, const
     return;
   }
   if (!ctl->cont && !a.force) return;  // this instance's CG loop has ended (timing runs: force)
+  if (ctl->dir_in_z && !a.force) {
+    // the solve ended in its first CG pass A: end the loop
+    if (vb == 0 && threadIdx.x == 0) {
+      ctl->cont = 0;
+      if (a.set_cond) cudaGraphSetConditional(a.cond, 0);
+    }
+    return;
+  }
   SEG_ROW_SETUP
   const int it = ctl->it;
   // read now what the last block needs after the grid sum
@@ -1495,7 +1524,7 @@ __device__ __forceinline__ void body_cg_b(const KArgs<T>& a, const int vb, const
   const int anybad = __syncthreads_or(bad);
   if (threadIdx.x == 0) {
     const int it1 = it + 1;
-    ctl->it = it1;
+    ctl->it = a.force ? it : it1;  // (timing runs repeat the same iteration)
     int cont = (any && it1 < a.maxit && ctl->halted != 2) ? 1 : 0;
     if (any && it1 >= a.maxit) ctl->status |= 1;
     if (anybad) {

@@ -115,6 +115,7 @@ struct KArgs {
   int ignore_halt; // run even if the control block is halted (direct calls)
   long long max_steps;  // > 0: the state is finished once step >= max_steps
   unsigned long long wait_ns;  // limit of one bounded wait for staged data (default 1 s)
+  int stall_waits;             // testing aid: the staged passes first wait on a barrier nothing completes
   int norm_only;   // start pass: the normalisation and D_i only (reading the state between steps)
 };
 

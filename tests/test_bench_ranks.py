@@ -92,27 +92,37 @@ def test_kernel_byte_model_matches_the_design_table():
     V = n * 16 * 4
     ell = n * 8 * 4
     assert kb["k_start"] == 3 * V + ell + 3 * n * 8 * 4 + n * 4
-    assert kb["k_cg_a_first"] == 3 * V + ell + n * 8 * 4
+    assert kb["k_cg_a_first"] == 2 * V + ell + n * 8 * 4 + n * 4
     assert kb["k_cg_a_even"] == 5 * V + ell + n * 8 * 4
     assert kb["k_cg_a_odd"] == 8 * V + ell + n * 8 * 4
     assert kb["k_cg_b"] == 3 * V + 2 * n * 4
+    assert kb["k_cg_b_first"] == 4 * V + 2 * n * 4
     assert (kb["k_finish_one"], kb["k_finish_two"]) == (8 * V, 9 * V)
     assert kb["k_energy_check"] == V + ntri * 16
-    # the per-launch figures, MB: start 212.3, CG pass A 167.8 / 251.7 / 377.5
-    # (first / even / odd form), CG pass B 131.1, finish 335.5 / 377.5, energy 62.9
-    quoted = {"k_start": 212.3, "k_cg_a_first": 167.8, "k_cg_a_even": 251.7, "k_cg_a_odd": 377.5,
-              "k_cg_b": 131.1, "k_finish_one": 335.5, "k_finish_two": 377.5, "k_energy_check": 62.9}
+    # the per-launch figures, MB: start 212.3, CG pass A 128.5 / 251.7 / 377.5
+    # (first / even / odd form), CG pass B 131.1 / 173.0 (later / first
+    # iteration), finish 335.5 / 377.5, energy 62.9
+    quoted = {"k_start": 212.3, "k_cg_a_first": 128.5, "k_cg_a_even": 251.7, "k_cg_a_odd": 377.5,
+              "k_cg_b": 131.1, "k_cg_b_first": 173.0, "k_finish_one": 335.5, "k_finish_two": 377.5,
+              "k_energy_check": 62.9}
     for k, mb in quoted.items():
         assert abs(kb[k] / 1e6 - mb) < 0.06, (k, kb[k] / 1e6)
 
 
 def test_pass_counts_per_step():
-    """Launches per step of each form of CG pass A and of the finish pass."""
+    """Launches per step of each form of the CG passes and of the finish
+    pass: a solve of one iteration ends in CG pass A (no pass B); one of k >= 2
+    runs pass B k times, the first in its first-iteration form."""
     sys.path.insert(0, ROOT)
     import bench
 
     one = bench.pass_counts(1.0)
     assert (one["first"], one["odd"], one["even"], one["fin_one"], one["fin_two"]) == (1, 0, 0, 1, 0)
+    assert (one["b_first"], one["b_later"]) == (0, 0)
+    two = bench.pass_counts(2.0)
+    assert (two["b_first"], two["b_later"]) == (1, 1)
+    three = bench.pass_counts(3.0)
+    assert (three["b_first"], three["b_later"]) == (1, 2)
     four = bench.pass_counts(4.0)  # first, odd, even, odd
     assert (four["first"], four["odd"], four["even"], four["fin_one"], four["fin_two"]) == (1, 2, 1, 1, 0)
     five = bench.pass_counts(5.0)  # first, odd, even, odd, even; two pending updates at the end

@@ -11,10 +11,12 @@ seg_eigenvalue_estimates, seg_labels) must not change the steps that follow.
 
 Bounded wait: every wait of a kernel for data staged by the bulk-copy engine
 gives up after the state's wait limit, records SEG_ERR_TIMEOUT and halts the
-run (the copies still in flight are drained with the default 1 s limit).  A
-limit of 1 ns makes the waits run out on data that does arrive; the state is
-then halted, and seg_set_wait_limit + seg_set_u bring it back to normal
-steps.  No GPU fault or hang is involved: the copies complete.
+run (the copies still in flight are drained with the default 1 s limit).
+seg_set_wait_stall makes the staged passes wait on a barrier that nothing
+completes, so the wait runs out after the limit (1 ms here); the state is
+then halted -- alone, when it is stepped in a batch -- and turning the stall
+off plus seg_set_u bring it back to normal steps.  No GPU fault or hang is
+involved: every copy that was issued completes.
 """
 
 import numpy as np
@@ -133,7 +135,10 @@ def test_bounded_wait_runs_out_and_the_state_recovers(seg, mode):
     assert seg.seg_step(ref, 3) == 3
     want = seg.seg_get_u(ref)
 
-    st = make_state(seg, xyz, tri, tau, m, eps, 1, seed=seed, launch_mode=mode, wait_limit_ns=1)
+    # every staged pass first waits on a barrier that nothing completes, with
+    # a 1 ms limit
+    st = make_state(seg, xyz, tri, tau, m, eps, 1, seed=seed, launch_mode=mode, wait_limit_ns=1_000_000)
+    seg.seg_set_wait_stall(st, True)
     with pytest.raises(seg.SegError) as err:
         seg.seg_step(st, 3)
     assert err.value.status == seg.SEG_ERR_TIMEOUT
@@ -143,9 +148,35 @@ def test_bounded_wait_runs_out_and_the_state_recovers(seg, mode):
     # the state stays halted: further steps do nothing
     assert seg.seg_step(st, 1) == 0
     assert seg.seg_get_stats(st)["steps"] == 0
-    # normal limit and fresh data: the state steps again, bitwise like the reference
+    # the waits back to normal and fresh data: the state steps again, bitwise
+    # like the reference
+    seg.seg_set_wait_stall(st, False)
     seg.seg_set_wait_limit(st, 0)
     seg.seg_set_u(st, U0)
     assert seg.seg_step(st, 3) == 3
     assert seg.seg_get_stats(st)["status_bits"] == 0
     assert np.array_equal(seg.seg_get_u(st), want)
+
+
+def test_a_member_whose_wait_runs_out_halts_alone_in_a_batch(seg):
+    """Two states stepped as a batch, the waits of the second made to run
+    out: the batch step reports SEG_ERR_TIMEOUT, the second member is halted
+    before its first step, and the first member's steps are bitwise those of
+    the same state stepped alone."""
+    xyz, tri = w.icosphere(5)
+    m, tau, eps = 6, 1e-4, 2e-2
+    alone = make_state(seg, xyz, tri, tau, m, eps, 1, seed=21, check_every=1, energy_tol=-1.0)
+    assert seg.seg_step(alone, 8) == 8
+    a = make_state(seg, xyz, tri, tau, m, eps, 1, seed=21, check_every=1, energy_tol=-1.0)
+    b = make_state(seg, xyz, tri, tau, m, eps, 1, seed=22, check_every=1, energy_tol=-1.0,
+                   wait_limit_ns=1_000_000)
+    seg.seg_set_wait_stall(b, True)
+    batch = seg.seg_batch_create([a, b])
+    with pytest.raises(seg.SegError) as err:
+        seg.seg_batch_step(batch, 8)
+    assert err.value.status == seg.SEG_ERR_TIMEOUT
+    sb = seg.seg_get_stats(b)
+    assert sb["steps"] == 0 and sb["status_bits"] & 4
+    assert seg.seg_get_stats(a)["steps"] == 8
+    assert np.array_equal(seg.seg_get_u(a), seg.seg_get_u(alone))
+    seg.seg_batch_destroy(batch)
