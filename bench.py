@@ -33,13 +33,14 @@ if ROOT not in sys.path:
 
 HBM_FALLBACK_GBS = 6800.0
 HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e, nominal
-# DRAM bytes (read + write) per launch of each hot-path kernel, from one ncu
-# capture of the level-8 sphere, m = 16, mixed precision, in the steady state
-# (one CG iteration per step: CG pass A in its first-iteration form, the
-# finish pass with one pending update; dram__bytes_read.sum +
-# dram__bytes_write.sum, mean of two launches, default geometry of 304
-# blocks); valid only for the kernel versions captured.
-TRAFFIC = {"k_cg_a": None, "k_start": None, "k_cg_b": None, "k_energy_check": None, "k_finish": None}
+# DRAM bytes (read + write) per launch of each form of the hot-path kernels,
+# from one ncu capture of the level-8 sphere, m = 16, mixed precision, 1000
+# steps in, default geometry of 304 blocks: dram__bytes_read.sum +
+# dram__bytes_write.sum of the bench's own kernel timing launches (selected by
+# their NVTX range), mean of the second and third launch; valid only for the
+# kernel versions captured.
+TRAFFIC = {"k_start": 196.3e6, "k_cg_a_first": 97.2e6, "k_cg_b": 90.6e6, "k_cg_b_first": 113.8e6,
+           "k_finish_one": 279.5e6, "k_energy_check": 63.0e6}
 KERNEL_ROLE = {
     "k_start": "start pass: r0 = -tau K X - A y for the predicted correction y, z0 = D^-1 r0, norms "
                "(issue and latency bound: three sparse products and three float-float sums per row)",
@@ -534,26 +535,31 @@ def run_ours(a, rank, ws, local):
     pc = pass_counts(kcg)
 
     def mix(forms):
+        # (mean ms, mean bytes, launches per step, the form with the most launches)
         c = sum(w for _, w in forms)
+        top = max(forms, key=lambda fw: fw[1])[0]
         if c <= 0:
-            return kern[forms[0][0]]["ms"], kb[forms[0][0]], 0.0
-        return (sum(kern[f]["ms"] * w for f, w in forms) / c, sum(kb[f] * w for f, w in forms) / c, c)
+            return kern[forms[0][0]]["ms"], kb[forms[0][0]], 0.0, forms[0][0]
+        return (sum(kern[f]["ms"] * w for f, w in forms) / c, sum(kb[f] * w for f, w in forms) / c, c, top)
 
     per = {
-        "k_start": (kern["k_start"]["ms"], kb["k_start"], 1.0),
-        "k_energy_check": (kern["k_energy_check"]["ms"], kb["k_energy_check"], 1.0),
+        "k_start": (kern["k_start"]["ms"], kb["k_start"], 1.0, "k_start"),
+        "k_energy_check": (kern["k_energy_check"]["ms"], kb["k_energy_check"], 1.0, "k_energy_check"),
         "k_cg_a": mix([("k_cg_a_first", pc["first"]), ("k_cg_a_odd", pc["odd"]), ("k_cg_a_even", pc["even"])]),
         "k_cg_b": mix([("k_cg_b_first", pc["b_first"]), ("k_cg_b", pc["b_later"])]),
         "k_finish": mix([("k_finish_one", pc["fin_one"]), ("k_finish_two", pc["fin_two"])]),
     }
-    share = {k: t * c for k, (t, _, c) in per.items()}
+    share = {k: t * c for k, (t, _, c, _) in per.items()}
     tot_share = sum(share.values())
 
     def roofline_of(name):
-        t, b, c = per[name]
+        t, b, c, form = per[name]
         got = b / (t / 1e3) / 1e9
+        # the captured traffic of the form the figures are (mostly) of, if only that form runs
+        single = (t == kern[form]["ms"])
         return {"bound": "hbm", "kernel": f"{name} ({KERNEL_ROLE[name]})", "achieved": got, "peak": peak,
-                "peak_kind": peak_kind, "unit": "GB/s", "frac": got / peak, "traffic": TRAFFIC[name],
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": got / peak,
+                "traffic": TRAFFIC.get(form) if single else None, "form": form,
                 "frac_of_nominal": got / HBM_NOMINAL_GBS, "peak_nominal": HBM_NOMINAL_GBS,
                 "bytes_per_launch": b, "launch_ms": t, "launches_per_step": c,
                 "share_of_kernel_time": share[name] / tot_share}
@@ -596,10 +602,10 @@ def run_ours(a, rank, ws, local):
         # CG pass A, the bandwidth-bound pass of the solve
         "roofline": roofline_of(dominant),
         "roofline_cg_a": roofline_of("k_cg_a"),
-        "step_roofline": {"bytes_per_step": sum(b * c for _, b, c in per.values()),
-                          "achieved": sum(b * c for _, b, c in per.values()) / (ms / a.steps / 1e3) / 1e9,
+        "step_roofline": {"bytes_per_step": sum(b * c for _, b, c, _ in per.values()),
+                          "achieved": sum(b * c for _, b, c, _ in per.values()) / (ms / a.steps / 1e3) / 1e9,
                           "peak": peak, "unit": "GB/s",
-                          "frac": sum(b * c for _, b, c in per.values()) / (ms / a.steps / 1e3) / 1e9 / peak,
+                          "frac": sum(b * c for _, b, c, _ in per.values()) / (ms / a.steps / 1e3) / 1e9 / peak,
                           "bytes": "this design's streams (per-kernel model above) x launches per step"},
         "step_roofline_method": method_roofline(n, int(tri.shape[0]), info["nnz"], li["padded_m"], 4, kcg,
                                                 ms / a.steps, peak),

@@ -149,3 +149,42 @@ def test_served_requests_converge_and_match_the_oracle(seg):
         seg.seg_set_u(st, Ug)
         check_labels(seg, st, tri, U, Ug)
     seg.seg_server_destroy(srv)
+
+
+def test_concurrent_classes_with_one_iteration_solves_equal_alone(seg):
+    """Requests of three classes (m = 3, 6, 16: three lane layouts, so three
+    batches on their own streams, running at the same time) in the regime
+    where nearly every solve takes one CG iteration and ends in CG pass A:
+    each result is bitwise the request stepped alone.  (A batched pass maps
+    its blocks to the members as its blocks start, while other classes'
+    kernels hold SMs; no member's flags may change meanwhile.)"""
+    xyz, tri = w.icosphere(5)
+    tau, steps = 1e-6, 600
+    prob = seg.seg_assemble(seg.seg_create_mesh(xyz, tri), tau, 1)
+    p = seg.seg_params()
+    p.check_every = 1
+    p.energy_tol = -1.0
+    p.max_steps = steps
+    reqs = [(3, 5e-3), (6, 4e-3), (16, 6e-3), (3, 7e-3), (6, 5e-3), (16, 4e-3), (6, 8e-3), (16, 5e-3)]
+    sp = seg.seg_server_params()
+    sp.steps_per_tick = 64
+    srv = seg.seg_server_create(sp)
+    ids = [seg.seg_server_submit(srv, prob, m, eps, seg.SEG_INIT_UNIFORM, 400 + i, p) for i, (m, eps) in enumerate(reqs)]
+    ticks = 0
+    while True:
+        running, queued = seg.seg_server_tick(srv)
+        ticks += 1
+        if running == 0 and queued == 0:
+            break
+        assert ticks < 100
+    one_iteration = 0  # solves of one iteration (the rest here take two, a few at the start more)
+    for i, rid in enumerate(ids):
+        info = seg.seg_server_info(srv, rid)
+        assert info["phase"] == 2 and info["steps"] == steps, info
+        m, eps = reqs[i]
+        st = seg.seg_state_create(prob, m, eps, seg.SEG_INIT_UNIFORM, 400 + i, p)
+        assert seg.seg_step(st, steps) == steps
+        assert np.array_equal(seg.seg_get_u(st), seg.seg_server_result(srv, rid)), i
+        one_iteration += max(0, 2 * steps - seg.seg_get_stats(st)["cg_iterations"])
+    assert one_iteration >= 0.1 * steps * len(reqs)  # the regime is the one meant
+    seg.seg_server_destroy(srv)
