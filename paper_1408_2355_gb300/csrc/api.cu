@@ -3,13 +3,15 @@
 // launch-geometry autotuner.
 //
 // The step graph is
-//     k_start -> k_energy_check -> (k_cg_a -> k_cg_b) x cg_peel
-//             -> WHILE(cond) { (k_cg_a -> k_cg_b) x kCgUnroll } -> k_finish
-// where the WHILE node's condition is set on the device by the last block of
-// k_start (any component still above tolerance), k_energy_check (stop rule)
-// and k_cg_b (convergence / iteration cap); passes after the loop has ended
-// return at once.  A whole step -- including the data-dependent CG iteration
-// count -- runs without a host round trip.
+//     k_start -> k_energy_check -> k_cg_a -> (k_cg_b -> k_cg_a) x (cg_peel - 1)
+//             -> WHILE(cond) { (k_cg_b -> k_cg_a) x kCgUnroll } -> k_finish
+// where the WHILE node's condition (CG pass B needed next) is set on the
+// device by the last block of k_start (any component still above tolerance),
+// k_energy_check (stop rule), the first k_cg_a of a solve (its only iteration
+// converged) and k_cg_b (convergence / iteration cap); passes after the loop
+// has ended return at once.  A step whose solve ends in its first pass A runs
+// no pass B at all.  A whole step -- including the data-dependent CG
+// iteration count -- runs without a host round trip.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -345,12 +347,15 @@ seg_status build_graph_t(seg_state* s) {
   SEG_CUDA(add_kernel_node<T>(&n_energy, s->graph, &n_start, 1, s->ks.energy_check, s->grid_e, base, 0));
   // the first cg_peel CG iterations are plain graph nodes (a pass after the
   // loop has ended returns at once), the rest a WHILE node: an evaluation of
-  // the loop condition costs more than a pass that returns at once
-  cudaGraphNode_t last = n_energy;
-  for (int u = 0; u < s->cg_peel; ++u) {
-    SEG_CUDA(add_kernel_node<T>(&n_a, s->graph, &last, 1, s->ks.cg_a, s->grid[kPassCgA], base, s->ks.smem_cg_a));
-    SEG_CUDA(add_kernel_node<T>(&n_b, s->graph, &n_a, 1, s->ks.cg_b, s->grid[kPassCgB], base, 0));
-    last = n_b;
+  // the loop condition costs more than a pass that returns at once.  An
+  // iteration's pass B comes after the loop's condition, so that a solve
+  // that ends in its first pass A launches no pass B.
+  SEG_CUDA(add_kernel_node<T>(&n_a, s->graph, &n_energy, 1, s->ks.cg_a, s->grid[kPassCgA], base, s->ks.smem_cg_a));
+  cudaGraphNode_t last = n_a;
+  for (int u = 1; u < s->cg_peel; ++u) {
+    SEG_CUDA(add_kernel_node<T>(&n_b, s->graph, &last, 1, s->ks.cg_b, s->grid[kPassCgB], base, 0));
+    SEG_CUDA(add_kernel_node<T>(&n_a, s->graph, &n_b, 1, s->ks.cg_a, s->grid[kPassCgA], base, s->ks.smem_cg_a));
+    last = n_a;
   }
   cudaGraphNodeParams cp{};
   cp.type = cudaGraphNodeTypeConditional;
@@ -359,14 +364,15 @@ seg_status build_graph_t(seg_state* s) {
   cp.conditional.size = 1;
   SEG_CUDA(cudaGraphAddNode(&n_loop, s->graph, &last, nullptr, 1, &cp));
   cudaGraph_t body = cp.conditional.phGraph_out[0];
-  // kCgUnroll CG iterations per evaluation of the loop condition; passes of
-  // an iteration after the loop has ended return at once (ctl->cont == 0)
+  // kCgUnroll CG iterations per evaluation of the loop condition, each the
+  // pass B of one iteration and the pass A of the next; passes after the
+  // loop has ended return at once (ctl->cont == 0)
   cudaGraphNode_t prev = nullptr;
   for (int u = 0; u < kCgUnroll; ++u) {
-    SEG_CUDA(add_kernel_node<T>(&n_a, body, prev ? &prev : nullptr, prev ? 1 : 0, s->ks.cg_a, s->grid[kPassCgA],
-                                base, s->ks.smem_cg_a));
-    SEG_CUDA(add_kernel_node<T>(&n_b, body, &n_a, 1, s->ks.cg_b, s->grid[kPassCgB], base, 0));
-    prev = n_b;
+    SEG_CUDA(add_kernel_node<T>(&n_b, body, prev ? &prev : nullptr, prev ? 1 : 0, s->ks.cg_b, s->grid[kPassCgB],
+                                base, 0));
+    SEG_CUDA(add_kernel_node<T>(&n_a, body, &n_b, 1, s->ks.cg_a, s->grid[kPassCgA], base, s->ks.smem_cg_a));
+    prev = n_a;
   }
   KArgs<T> fin = base;
   fin.apply_x = 1;
@@ -1375,13 +1381,15 @@ seg_status build_batch_t(seg_batch* b) {
   if (b->peel <= 0)
     for (seg_state* m : b->members) b->peel = std::max(b->peel, m->cg_peel);
   const int peel = b->peel;
-  cudaGraphNode_t last = n_energy;
-  for (int u = 0; u < peel; ++u) {
-    SEG_CUDA(add_batch_node<T>(&n_a, b->graph, &last, 1, b->ks.b_cg_a, rows[kPassCgA], phys[kPassCgA],
-                               kBlockThreads, b->ks.smem_cg_a));
-    SEG_CUDA(add_batch_node<T>(&n_b, b->graph, &n_a, 1, b->ks.b_cg_b, rows[kPassCgB], phys[kPassCgB],
+  SEG_CUDA(add_batch_node<T>(&n_a, b->graph, &n_energy, 1, b->ks.b_cg_a, rows[kPassCgA], phys[kPassCgA],
+                             kBlockThreads, b->ks.smem_cg_a));
+  cudaGraphNode_t last = n_a;
+  for (int u = 1; u < peel; ++u) {
+    SEG_CUDA(add_batch_node<T>(&n_b, b->graph, &last, 1, b->ks.b_cg_b, rows[kPassCgB], phys[kPassCgB],
                                kBlockThreads, 0));
-    last = n_b;
+    SEG_CUDA(add_batch_node<T>(&n_a, b->graph, &n_b, 1, b->ks.b_cg_a, rows[kPassCgA], phys[kPassCgA],
+                               kBlockThreads, b->ks.smem_cg_a));
+    last = n_a;
   }
   SEG_CUDA(add_batch_node<T>(&n_vote0, b->graph, &last, 1, b->ks.b_vote, vote, 1, kMaxBatch, 0));
   cudaGraphNodeParams cp{};
@@ -1393,13 +1401,13 @@ seg_status build_batch_t(seg_batch* b) {
   cudaGraph_t body = cp.conditional.phGraph_out[0];
   cudaGraphNode_t prev = nullptr;
   for (int u = 0; u < kCgUnroll; ++u) {
-    SEG_CUDA(add_batch_node<T>(&n_a, body, prev ? &prev : nullptr, prev ? 1 : 0, b->ks.b_cg_a, rows[kPassCgA],
-                               phys[kPassCgA], kBlockThreads, b->ks.smem_cg_a));
-    SEG_CUDA(add_batch_node<T>(&n_b, body, &n_a, 1, b->ks.b_cg_b, rows[kPassCgB], phys[kPassCgB], kBlockThreads,
-                               0));
-    prev = n_b;
+    SEG_CUDA(add_batch_node<T>(&n_b, body, prev ? &prev : nullptr, prev ? 1 : 0, b->ks.b_cg_b, rows[kPassCgB],
+                               phys[kPassCgB], kBlockThreads, 0));
+    SEG_CUDA(add_batch_node<T>(&n_a, body, &n_b, 1, b->ks.b_cg_a, rows[kPassCgA], phys[kPassCgA], kBlockThreads,
+                               b->ks.smem_cg_a));
+    prev = n_a;
   }
-  SEG_CUDA(add_batch_node<T>(&n_vote, body, &n_b, 1, b->ks.b_vote, vote, 1, kMaxBatch, 0));
+  SEG_CUDA(add_batch_node<T>(&n_vote, body, &n_a, 1, b->ks.b_vote, vote, 1, kMaxBatch, 0));
   SEG_CUDA(add_batch_node<T>(&n_fin, b->graph, &n_loop, 1, b->ks.b_finish, rows[kPassFinish], phys[kPassFinish],
                              kBlockThreads, 0));
   SEG_CUDA(cudaGraphInstantiate(&b->exec, b->graph, 0));

@@ -1748,13 +1748,15 @@ SEG_DEFINE_PASS(energy_check, kTriBlocksPerSM, SEG_TPL, T, LPR)
 #undef SEG_TPL_W
 #undef SEG_DEFINE_PASS
 
-// Condition of a batch's CG loop: continue while any instance is iterating.
+// Condition of a batch's CG loop (after a CG pass A): continue while any
+// instance needs a pass B, i.e. is iterating and did not end its solve in
+// its first pass A.
 template <typename T>
 __global__ void k_batch_vote(const BatchArgs<T> b) {
   int go = 0;
   if ((int)threadIdx.x < b.ninst) {
     const KArgs<T>& a = b.tab[threadIdx.x];
-    go = (a.ctl->cont && !state_finished(a, a.ctl)) ? 1 : 0;
+    go = (a.ctl->cont && !a.ctl->dir_in_z && !state_finished(a, a.ctl)) ? 1 : 0;
   }
   const int any = __syncthreads_or(go);
   if (threadIdx.x == 0) cudaGraphSetConditional(b.cond, any);
