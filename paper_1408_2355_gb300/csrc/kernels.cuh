@@ -79,6 +79,16 @@ __device__ __forceinline__ void ld_ro(double (&d)[2], const double* p) {
 __device__ __forceinline__ void st(double* p, const double (&d)[2]) {
   *reinterpret_cast<double2*>(p) = make_double2(d[0], d[1]);
 }
+// 32-byte read-only loads (one 256-bit load instruction, sm_100 and later;
+// p must be 32-byte aligned)
+__device__ __forceinline__ void ld_ro32(float (&d)[8], const float* p) {
+  asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3]), "=f"(d[4]), "=f"(d[5]), "=f"(d[6]), "=f"(d[7])
+      : "l"(p));
+}
+__device__ __forceinline__ void ld_ro32(double (&d)[4], const double* p) {
+  asm("ld.global.nc.v4.f64 {%0, %1, %2, %3}, [%4];" : "=d"(d[0]), "=d"(d[1]), "=d"(d[2]), "=d"(d[3]) : "l"(p));
+}
 
 __device__ __forceinline__ float t_exp(float x) { return expf(x); }
 __device__ __forceinline__ double t_exp(double x) { return exp(x); }
@@ -1291,16 +1301,24 @@ __device__ __forceinline__ void quad_pairs(const double* X, unsigned z0, unsigne
                                            const double* sinv, double A1, double B1mA1, double A2, double B2mA2,
                                            double& sum1, double& sum2) {
   typedef double T;
-  constexpr int VW = VecW<T>::W;
+  // the rows in 32-byte pieces where they hold whole ones (fewer, wider
+  // scattered loads: the pass is bound by the L1's handling of them)
+  constexpr int VW = MS % 4 == 0 ? 4 : VecW<T>::W;
   T pre[6], sum[6];
 #pragma unroll
   for (int q = 0; q < 6; ++q) pre[q] = sum[q] = T(0);
 #pragma unroll
   for (int c = 0; c < MS; c += VW) {
     T u0[VW], u1[VW], u2[VW];
-    ld_ro(u0, X + (z0 + c));
-    ld_ro(u1, X + (z1 + c));
-    ld_ro(u2, X + (z2 + c));
+    if constexpr (VW == 4) {
+      ld_ro32(u0, X + (z0 + c));
+      ld_ro32(u1, X + (z1 + c));
+      ld_ro32(u2, X + (z2 + c));
+    } else {
+      ld_ro(u0, X + (z0 + c));
+      ld_ro(u1, X + (z1 + c));
+      ld_ro(u2, X + (z2 + c));
+    }
 #pragma unroll
     for (int v = 0; v < VW; ++v) {
       const T s = sinv[c + v];
@@ -1329,17 +1347,25 @@ template <int MS>
 __device__ __forceinline__ void quad_pairs(const float* X, unsigned z0, unsigned z1, unsigned z2, const float* sinv,
                                              float A1, float B1mA1, float A2, float B2mA2, float& sum1, float& sum2) {
   const float2 A = f2(A1, A2), B = f2(B1mA1, B2mA2);
+  // the rows in 32-byte pieces where they hold whole ones (see above)
+  constexpr int CW = MS % 8 == 0 ? 8 : 4;
   float2 pre[3], sum[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) pre[k] = sum[k] = f2(0.f, 0.f);
 #pragma unroll
-  for (int c = 0; c < MS; c += 4) {
-    float u0[4], u1[4], u2[4];
-    ld_ro(u0, X + (z0 + c));
-    ld_ro(u1, X + (z1 + c));
-    ld_ro(u2, X + (z2 + c));
+  for (int c = 0; c < MS; c += CW) {
+    float u0[CW], u1[CW], u2[CW];
+    if constexpr (CW == 8) {
+      ld_ro32(u0, X + (z0 + c));
+      ld_ro32(u1, X + (z1 + c));
+      ld_ro32(u2, X + (z2 + c));
+    } else {
+      ld_ro(u0, X + (z0 + c));
+      ld_ro(u1, X + (z1 + c));
+      ld_ro(u2, X + (z2 + c));
+    }
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
+    for (int v = 0; v < CW; ++v) {
       const float s = sinv[c + v];
       const float b0 = u0[v] * s, b1 = u1[v] * s, b2 = u2[v] * s;
       const float tot = b0 + b1 + b2;
