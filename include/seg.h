@@ -316,6 +316,19 @@ seg_status seg_batch_step_async(seg_batch* b, int64_t nsteps);
 seg_status seg_batch_sync(seg_batch* b);
 void seg_batch_destroy(seg_batch* b);
 
+/* Persistent mode of a batch (on != 0; 0, the default, restores the step
+ * graph).  Each seg_batch_step / seg_batch_step_async call then runs all of
+ * its steps of every member in ONE cooperative kernel launch that stays
+ * resident on the GPU (one block per SM): every pass of Algorithm 2.2 is a
+ * phase over the members' virtual blocks (each member keeps its own block
+ * decomposition, so results are bitwise those of the member stepped alone),
+ * separated by grid barriers, and the CG loop, the stop rule and the step
+ * limits are decided on the device.  The launch ends early once every member
+ * has finished.  Barrier waits are bounded (1 s); one that runs out halts
+ * every member with SEG_ERR_TIMEOUT.  SEG_ERR_UNSUPPORTED where cooperative
+ * launches are not available. */
+seg_status seg_batch_set_persistent(seg_batch* b, int32_t on);
+
 /* ----------------------------------------------------------------- serving */
 
 /* A request server with continuous batching: requests (a problem, m, eps,

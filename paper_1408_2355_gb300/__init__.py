@@ -51,6 +51,7 @@ EXPORTED = [
     "seg_stats_enqueue", "seg_stats_wait", "seg_last_error",
     "seg_time_kernel", "seg_launch_info", "seg_autotune", "seg_s_eps_noalloc",
     "seg_batch_create", "seg_batch_step", "seg_batch_step_async", "seg_batch_sync", "seg_batch_destroy",
+    "seg_batch_set_persistent",
     "seg_server_create", "seg_server_submit", "seg_server_tick", "seg_server_info", "seg_server_result",
     "seg_server_clock", "seg_server_destroy", "seg_state_bytes",
     "seg_checkpoint_size", "seg_get_checkpoint", "seg_set_checkpoint", "seg_set_wait_limit", "seg_set_wait_stall",
@@ -177,6 +178,7 @@ _SIG = {
     "seg_batch_step": [_vp, _i64],
     "seg_batch_step_async": [_vp, _i64],
     "seg_batch_sync": [_vp],
+    "seg_batch_set_persistent": [_vp, _i32],
     "seg_server_create": [_vp, _pp],
     "seg_server_submit": [_vp, _vp, _i32, _d, C.c_int, C.c_uint64, _vp, _vp],
     "seg_server_tick": [_vp, _vp, _vp],
@@ -471,6 +473,10 @@ def seg_batch_step_async(batch: Batch, nsteps: int):
 
 def seg_batch_sync(batch: Batch):
     _check(lib.seg_batch_sync(batch.ptr))
+
+
+def seg_batch_set_persistent(batch: Batch, on: bool = True):
+    _check(lib.seg_batch_set_persistent(batch.ptr, 1 if on else 0))
 
 
 def seg_batch_destroy(batch: Batch):

@@ -1307,6 +1307,11 @@ struct seg_batch {
   long long* hsnap = nullptr;  // pinned: 2 slots x members x (step, cg_total)
   cudaEvent_t snap_ev[2] = {nullptr, nullptr};
   std::vector<long long> mark_step, mark_it;  // members' counters at the last peel review
+  // persistent mode: every seg_batch_step call is one cooperative launch
+  bool persistent = false;
+  PersistCtl* pc = nullptr;  // device: grid barrier and phase decisions
+  int persist_grid = 0;      // resident blocks of the persistent kernel
+  unsigned persist_smem = 0;
 };
 
 namespace {
@@ -1497,7 +1502,41 @@ seg_status begin_batch_steps(seg_batch* b) {
   return SEG_OK;
 }
 
+template <typename T>
+seg_status launch_persistent_t(seg_batch* b, int64_t nsteps) {
+  PersistArgs<T> pa{};
+  pa.ninst = (int)b->members.size();
+  for (int i = 0; i < pa.ninst; ++i) {
+    seg_state* s = b->members[i];
+    Launch l;
+    l.ignore_halt = 0;
+    l.apply_x = 1;
+    l.apply_ode = 1;
+    l.count_step = 1;
+    pa.tab[i] = make_args<T>(s, l);
+    for (int k = 0; k < 4; ++k) pa.vg[k][i] = s->grid[k];
+    pa.vg[4][i] = s->grid_e;
+  }
+  pa.pc = b->pc;
+  pa.nsteps = nsteps;
+  pa.wait_ns = kDefaultWaitNs;
+  SEG_CUDA(cudaMemsetAsync(b->pc, 0, sizeof(PersistCtl), b->stream));
+  void* args[] = {&pa};
+  SEG_CUDA(cudaLaunchCooperativeKernel(b->ks.persist, dim3(b->persist_grid), dim3(kBlockThreads), args,
+                                       b->persist_smem, b->stream));
+  return SEG_OK;
+}
+
 seg_status enqueue_batch_steps(seg_batch* b, int64_t nsteps) {
+  if (b->persistent) {
+    if (nsteps > 0) {
+      const seg_status st =
+          b->prec == SEG_MIXED_FP32 ? launch_persistent_t<float>(b, nsteps) : launch_persistent_t<double>(b, nsteps);
+      if (st != SEG_OK) return st;
+      for (seg_state* s : b->members) s->pending = true;
+    }
+    return SEG_OK;
+  }
   if (!b->exec) {
     const seg_status gs = b->prec == SEG_MIXED_FP32 ? build_batch_t<float>(b) : build_batch_t<double>(b);
     if (gs != SEG_OK) {
@@ -1583,7 +1622,7 @@ seg_status seg_batch_step(seg_batch* b, int64_t nsteps) {
   if (nsteps < 0) return fail(SEG_ERR_ARG, "nsteps must be >= 0");
   seg_status st = begin_batch_steps(b);
   if (st != SEG_OK) return st;
-  if (nsteps < 4 * kReviewChunk) {
+  if (nsteps < 4 * kReviewChunk || b->persistent) {  // (a persistent batch: one launch)
     st = enqueue_batch_steps(b, nsteps);
     if (st != SEG_OK) return st;
     return seg_batch_sync(b);
@@ -1622,11 +1661,44 @@ void seg_batch_destroy(seg_batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->amap) cudaFree(b->amap);
+  if (b->pc) cudaFree(b->pc);
   if (b->hsnap) cudaFreeHost(b->hsnap);
   for (cudaEvent_t e : b->snap_ev)
     if (e) cudaEventDestroy(e);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
+}
+
+seg_status seg_batch_set_persistent(seg_batch* b, int32_t on) {
+  if (!b) return fail(SEG_ERR_ARG, "batch is NULL");
+  if (!on) {
+    b->persistent = false;
+    return SEG_OK;
+  }
+  const int dev = b->members[0]->p->device;
+  SEG_CUDA(cudaSetDevice(dev));
+  int coop = 0, nsm = 0;
+  SEG_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  SEG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  if (!coop) return fail(SEG_ERR_UNSUPPORTED, "the device does not support cooperative launches");
+  const unsigned smem = std::max(b->ks.smem_start, b->ks.smem_cg_a);
+  SEG_CUDA(cudaFuncSetAttribute(b->ks.persist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int occ = 0;
+  SEG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, b->ks.persist, kBlockThreads, smem));
+  if (occ < 1) return fail(SEG_ERR_UNSUPPORTED, "the persistent kernel does not fit on a multiprocessor");
+  if (!b->pc) {
+    cudaError_t e = cudaMalloc((void**)&b->pc, sizeof(PersistCtl));
+    if (e == cudaSuccess) e = cudaMemset(b->pc, 0, sizeof(PersistCtl));
+    if (e != cudaSuccess) {
+      if (b->pc) cudaFree(b->pc);
+      b->pc = nullptr;
+      return fail(SEG_ERR_NO_MEMORY, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+  }
+  b->persist_smem = smem;
+  b->persist_grid = occ * nsm;
+  b->persistent = true;
+  return SEG_OK;
 }
 
 // ---------------------------------------------------------------- outputs

@@ -79,8 +79,36 @@ __device__ __forceinline__ void ld_ro(double (&d)[2], const double* p) {
 __device__ __forceinline__ void st(double* p, const double (&d)[2]) {
   *reinterpret_cast<double2*>(p) = make_double2(d[0], d[1]);
 }
-// 32-byte read-only loads (one 256-bit load instruction, sm_100 and later;
-// p must be 32-byte aligned)
+// Loads of state vectors in the step passes: through the read-only cache
+// (CO = false) when the launch does not write them, else coherent loads (a
+// persistent launch writes them in its earlier phases).
+template <bool CO>
+__device__ __forceinline__ void ldv(float (&d)[4], const float* p) {
+  if constexpr (CO)
+    ld(d, p);
+  else
+    ld_ro(d, p);
+}
+template <bool CO>
+__device__ __forceinline__ void ldv(double (&d)[2], const double* p) {
+  if constexpr (CO)
+    ld(d, p);
+  else
+    ld_ro(d, p);
+}
+// 32-byte loads (one 256-bit load instruction, sm_100 and later; p must be
+// 32-byte aligned): read-only (ld_ro32) and coherent (ld32)
+// (the "memory" clobber keeps the coherent loads after the grid barrier
+// that orders them with the writes of an earlier phase)
+__device__ __forceinline__ void ld32(float (&d)[8], const float* p) {
+  asm("ld.global.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3]), "=f"(d[4]), "=f"(d[5]), "=f"(d[6]), "=f"(d[7])
+      : "l"(p)
+      : "memory");
+}
+__device__ __forceinline__ void ld32(double (&d)[4], const double* p) {
+  asm("ld.global.v4.f64 {%0, %1, %2, %3}, [%4];" : "=d"(d[0]), "=d"(d[1]), "=d"(d[2]), "=d"(d[3]) : "l"(p) : "memory");
+}
 __device__ __forceinline__ void ld_ro32(float (&d)[8], const float* p) {
   asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
       : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3]), "=f"(d[4]), "=f"(d[5]), "=f"(d[6]), "=f"(d[7])
@@ -691,6 +719,9 @@ __device__ __forceinline__ bool row_pipeline(unsigned char* smem_warp, unsigned 
 #pragma unroll
     for (int k = 0; k < NS; ++k) mbar_init(&bars[k], 1);
     mbar_init_fence();
+    // the stages may have been read through the generic proxy (an earlier
+    // pipeline of this block): order those reads before the copies below
+    fence_proxy_async_smem();
   }
   __syncwarp();
   auto stage = [&](int k) {
@@ -785,7 +816,7 @@ using CgAStage = RowStage<T, LPR, W, 1, FORM == kCgFirst ? 1 : (FORM == kCgOdd ?
 // thread (they only set the tolerance and the choice of w), ||M X||_2^2 and
 // the squared norms of the residuals of both starts, -tau K X and
 // -tau K X - A Y.  The next step uses w = 1 where the second was smaller.
-template <typename T, int LPR, int W>
+template <typename T, int LPR, int W, bool CO = false>
 __device__ __forceinline__ void body_start(const KArgs<T>& a, const int vb, const int vg) {
   typedef typename AccOf<T>::type Acc;
   typedef StartStage<T, LPR, W> Stage;
@@ -834,8 +865,8 @@ __device__ __forceinline__ void body_start(const KArgs<T>& a, const int vb, cons
 #pragma unroll
         for (int k = 0; k < W; ++k) {
           const unsigned o = (unsigned)cols[k] * ms + c0;
-          ld_ro(xj[k], a.X + o);
-          ld_ro(yj[k], a.Y + o);
+          ldv<CO>(xj[k], a.X + o);
+          ldv<CO>(yj[k], a.Y + o);
         }
         T kx[VW], mx[VW];
 #pragma unroll
@@ -938,7 +969,7 @@ __device__ __forceinline__ void body_start(const KArgs<T>& a, const int vb, cons
 // has converged, in which case CG pass B has nothing to do (once a run has
 // settled, the predicted start leaves one iteration per solve).
 // Padded ELL entries point at the row itself with value 0 (no branches).
-template <typename T, int LPR, int W, int FORM>
+template <typename T, int LPR, int W, int FORM, bool CO>
 __device__ __forceinline__ void body_cg_a_rows(const KArgs<T>& a, const int vb, const int vg, const int it) {
   typedef typename AccOf<T>::type Acc;
   typedef CgAStage<T, LPR, W, FORM> Stage;
@@ -1009,7 +1040,7 @@ __device__ __forceinline__ void body_cg_a_rows(const KArgs<T>& a, const int vb, 
         // all neighbour rows of z in flight at once
         T zj[W][VW];
 #pragma unroll
-        for (int k = 0; k < W; ++k) ld_ro(zj[k], a.Z + ((unsigned)cols[k] * ms + c0));
+        for (int k = 0; k < W; ++k) ldv<CO>(zj[k], a.Z + ((unsigned)cols[k] * ms + c0));
         T zi[VW], pn[VW], q[VW];
         lds(zi, sg.vec(0) + rs * ms + c0);
 #pragma unroll
@@ -1095,7 +1126,7 @@ __device__ __forceinline__ void body_cg_a_rows(const KArgs<T>& a, const int vb, 
   }
 }
 
-template <typename T, int LPR, int W>
+template <typename T, int LPR, int W, bool CO = false>
 __device__ __forceinline__ void body_cg_a(const KArgs<T>& a, const int vb, const int vg) {
   DevCtl* ctl = a.ctl;
   count_launch(ctl, vb);
@@ -1103,11 +1134,11 @@ __device__ __forceinline__ void body_cg_a(const KArgs<T>& a, const int vb, const
   if (!ctl->cont && !a.force) return;  // this instance's CG loop has ended (timing runs: force)
   const int it = ctl->it;
   if (it == 0)
-    body_cg_a_rows<T, LPR, W, kCgFirst>(a, vb, vg, it);
+    body_cg_a_rows<T, LPR, W, kCgFirst, CO>(a, vb, vg, it);
   else if (it & 1)
-    body_cg_a_rows<T, LPR, W, kCgOdd>(a, vb, vg, it);
+    body_cg_a_rows<T, LPR, W, kCgOdd, CO>(a, vb, vg, it);
   else
-    body_cg_a_rows<T, LPR, W, kCgEven>(a, vb, vg, it);
+    body_cg_a_rows<T, LPR, W, kCgEven, CO>(a, vb, vg, it);
 }
 
 // The Sec. 2.2 stop rule at a check: the change of the total energy since
@@ -1296,7 +1327,7 @@ constexpr double kQuadW2 = 0.10995174365532179;
 // sum[5] (second orbit).  The float version keeps the two orbits' points at
 // the same corner in one packed pair (points 0 and 3, 1 and 4, 2 and 5):
 // the same operations in the same order, three pairs instead of six values.
-template <int MS>
+template <int MS, bool CO>
 __device__ __forceinline__ void quad_pairs(const double* X, unsigned z0, unsigned z1, unsigned z2,
                                            const double* sinv, double A1, double B1mA1, double A2, double B2mA2,
                                            double& sum1, double& sum2) {
@@ -1310,14 +1341,18 @@ __device__ __forceinline__ void quad_pairs(const double* X, unsigned z0, unsigne
 #pragma unroll
   for (int c = 0; c < MS; c += VW) {
     T u0[VW], u1[VW], u2[VW];
-    if constexpr (VW == 4) {
+    if constexpr (VW == 4 && CO) {
+      ld32(u0, X + (z0 + c));
+      ld32(u1, X + (z1 + c));
+      ld32(u2, X + (z2 + c));
+    } else if constexpr (VW == 4) {
       ld_ro32(u0, X + (z0 + c));
       ld_ro32(u1, X + (z1 + c));
       ld_ro32(u2, X + (z2 + c));
     } else {
-      ld_ro(u0, X + (z0 + c));
-      ld_ro(u1, X + (z1 + c));
-      ld_ro(u2, X + (z2 + c));
+      ldv<CO>(u0, X + (z0 + c));
+      ldv<CO>(u1, X + (z1 + c));
+      ldv<CO>(u2, X + (z2 + c));
     }
 #pragma unroll
     for (int v = 0; v < VW; ++v) {
@@ -1343,7 +1378,7 @@ __device__ __forceinline__ void quad_pairs(const double* X, unsigned z0, unsigne
   sum1 = sum[0] + sum[1] + sum[2];
   sum2 = sum[3] + sum[4] + sum[5];
 }
-template <int MS>
+template <int MS, bool CO>
 __device__ __forceinline__ void quad_pairs(const float* X, unsigned z0, unsigned z1, unsigned z2, const float* sinv,
                                              float A1, float B1mA1, float A2, float B2mA2, float& sum1, float& sum2) {
   const float2 A = f2(A1, A2), B = f2(B1mA1, B2mA2);
@@ -1355,14 +1390,18 @@ __device__ __forceinline__ void quad_pairs(const float* X, unsigned z0, unsigned
 #pragma unroll
   for (int c = 0; c < MS; c += CW) {
     float u0[CW], u1[CW], u2[CW];
-    if constexpr (CW == 8) {
+    if constexpr (CW == 8 && CO) {
+      ld32(u0, X + (z0 + c));
+      ld32(u1, X + (z1 + c));
+      ld32(u2, X + (z2 + c));
+    } else if constexpr (CW == 8) {
       ld_ro32(u0, X + (z0 + c));
       ld_ro32(u1, X + (z1 + c));
       ld_ro32(u2, X + (z2 + c));
     } else {
-      ld_ro(u0, X + (z0 + c));
-      ld_ro(u1, X + (z1 + c));
-      ld_ro(u2, X + (z2 + c));
+      ldv<CO>(u0, X + (z0 + c));
+      ldv<CO>(u1, X + (z1 + c));
+      ldv<CO>(u2, X + (z2 + c));
     }
 #pragma unroll
     for (int v = 0; v < CW; ++v) {
@@ -1392,7 +1431,7 @@ __device__ __forceinline__ void quad_pairs(const float* X, unsigned z0, unsigned
 //   sum_{i != j} u_i^2 u_j^2 = 2 sum_i u_i^2 sum_{j < i} u_j^2
 // (non-negative terms only, no cancellation).  Components are visited in
 // chunks of VW so that only one chunk of the three corner rows is live.
-template <typename T, int LPR>
+template <typename T, int LPR, bool CO = false>
 __device__ __forceinline__ void body_energy_check(const KArgs<T>& a, const int vb, const int vg) {
   typedef typename AccOf<T>::type Acc;
   constexpr int VW = VecW<T>::W;
@@ -1417,7 +1456,7 @@ __device__ __forceinline__ void body_energy_check(const KArgs<T>& a, const int v
     const unsigned z0 = __ldg(tr) * ms, z1 = __ldg(tr + 1) * ms, z2 = __ldg(tr + 2) * ms;
     const T area = __ldg(a.tarea + t);
     T sum1, sum2;
-    quad_pairs<MS>(a.X, z0, z1, z2, sinv, A1, B1mA1, A2, B2mA2, sum1, sum2);
+    quad_pairs<MS, CO>(a.X, z0, z1, z2, sinv, A1, B1mA1, A2, B2mA2, sum1, sum2);
     const T st = T(2) * area * (W1 * sum1 + W2 * sum2);
     acc.add_val(st);
   }
@@ -1461,7 +1500,7 @@ constexpr int kStreamRows = 4;
 // CG pass B of iteration j: z_j = z_{j-1} - alpha_j D^-1 q_j (= D^-1 r_j),
 // r_j = D z_j; per component r_j.z_j (float-float) and ||r_j||^2 (float32
 // per thread, tolerance only); convergence test and beta for iteration j+1.
-template <typename T, int LPR>
+template <typename T, int LPR, bool CO = false>
 __device__ __forceinline__ void body_cg_b(const KArgs<T>& a, const int vb, const int vg) {
   typedef typename AccOf<T>::type Acc;
   constexpr int RU = kStreamRows;
@@ -1510,7 +1549,7 @@ __device__ __forceinline__ void body_cg_b(const KArgs<T>& a, const int vb, const
       const unsigned row = base + u * RPW + rs;
       if ((int)row < r1) {
         ld(z[u], a.Z + (row * ms + c0));
-        ld_ro(q[u], a.Q + (row * ms + c0));
+        ldv<CO>(q[u], a.Q + (row * ms + c0));
         di[u] = __ldg(a.dinv + row);
         dg[u] = __ldg(a.diagA + row);
       }
@@ -1579,7 +1618,7 @@ __device__ __forceinline__ void body_cg_b(const KArgs<T>& a, const int vb, const
 // The solution updates CG pass A has not applied yet: alpha_k p_k (none if
 // k = 0), and alpha_{k-1} p_{k-1} before it (TWO) when the iteration count k
 // is odd and at least 3.
-template <typename T, int LPR, int RU, bool TWO>
+template <typename T, int LPR, int RU, bool TWO, bool CO>
 __device__ __forceinline__ void body_finish_rows(const KArgs<T>& a, const int vb, const int vg, const int it) {
   DevCtl* ctl = a.ctl;
   SEG_ROW_SETUP
@@ -1626,9 +1665,9 @@ __device__ __forceinline__ void body_finish_rows(const KArgs<T>& a, const int vb
           ld(h1[u], Hm1 + (row * ms + c0));
           ld(h2[u], Hm2 + (row * ms + c0));
           if (NH == 3) ld(h3[NH == 3 ? u : 0], Hm3 + (row * ms + c0));
-          if (it > 0) ld_ro(p[u], P + (row * ms + c0));
+          if (it > 0) ldv<CO>(p[u], P + (row * ms + c0));
         }
-        if (two) ld_ro(p2[TWO ? u : 0], P2 + (row * ms + c0));
+        if (two) ldv<CO>(p2[TWO ? u : 0], P2 + (row * ms + c0));
       }
     }
 #pragma unroll
@@ -1670,7 +1709,7 @@ __device__ __forceinline__ void body_finish_rows(const KArgs<T>& a, const int vb
   }
 }
 
-template <typename T, int LPR>
+template <typename T, int LPR, bool CO = false>
 __device__ __forceinline__ void body_finish(const KArgs<T>& a, const int vb, const int vg) {
   DevCtl* ctl = a.ctl;
   count_launch(ctl, vb);
@@ -1682,9 +1721,9 @@ __device__ __forceinline__ void body_finish(const KArgs<T>& a, const int vb, con
   // two pending updates after an odd count of 3 or more iterations (after
   // one, the second term would be alpha_0 p_0: there is none)
   if (a.apply_x && (it & 1) && it > 1)
-    body_finish_rows<T, LPR, RU - 1, true>(a, vb, vg, it);
+    body_finish_rows<T, LPR, RU - 1, true, CO>(a, vb, vg, it);
   else
-    body_finish_rows<T, LPR, RU, false>(a, vb, vg, it);
+    body_finish_rows<T, LPR, RU, false, CO>(a, vb, vg, it);
   if (a.count_step) {
     // the step is counted by the last block to finish, after every block has
     // passed its own state_finished() test (a block that started after an
@@ -1788,6 +1827,157 @@ __global__ void k_batch_vote(const BatchArgs<T> b) {
   if (threadIdx.x == 0) cudaGraphSetConditional(b.cond, any);
 }
 
+// ------------------------------------------------ persistent batched steps
+
+__device__ __forceinline__ int vld(const int* p) { return *(const volatile int*)p; }
+__device__ __forceinline__ long long vld(const long long* p) { return *(const volatile long long*)p; }
+
+// state_finished() from the control block as it is now in memory (the last
+// block of a barrier reads what other blocks wrote in the phase before).
+template <typename T>
+__device__ __forceinline__ bool finished_now(const KArgs<T>& a) {
+  const int halted = vld(&a.ctl->halted);
+  return halted != 0 || (a.max_steps > 0 && vld(&a.ctl->step) >= a.max_steps);
+}
+
+enum PersistSync { kSyncPlain = 0, kSyncMapA = 1, kSyncAfterA = 2, kSyncEnd = 3 };
+
+// Grid barrier of a cooperative launch.  Thread 0 of each block arrives on a
+// counter; in the block that arrives last, warp 0 computes the decisions of
+// `kind` from the members' control blocks (lane i for member i, all loads
+// in one round), then thread 0 releases the others by advancing the
+// generation.  Waits are bounded by wait_ns: a wait that runs out (or sees
+// that another block's did) marks every member halted with a timeout and
+// returns false, and the kernel returns.  After the barrier the bulk-copy
+// engine may read what the phase before wrote (proxy fence).
+template <typename T>
+__device__ __noinline__ bool persist_sync(const PersistArgs<T>& p, const int kind) {
+  PersistCtl* pc = p.pc;
+  __shared__ int last_s, ok_s;
+  __shared__ unsigned gen_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned g = *(volatile unsigned*)&pc->gen;
+    __threadfence();
+    const int last = atomicAdd(&pc->count, 1u) == gridDim.x - 1;
+    if (last) pc->count = 0u;
+    last_s = last;
+    gen_s = g;
+    ok_s = 1;
+  }
+  __syncthreads();
+  if (last_s) {
+    if (threadIdx.x < 32) {
+      const int i = threadIdx.x;
+      int go = 0, act = 0;
+      if (i < p.ninst) {
+        const KArgs<T>& a = p.tab[i];
+        const bool fin = finished_now(a);
+        act = fin ? 0 : 1;
+        if (kind == kSyncMapA) {
+          *(volatile int*)&pc->map_a[i] = (vld(&a.ctl->cont) && !fin) ? 1 : 0;
+        } else if (kind == kSyncAfterA) {
+          *(volatile int*)&pc->map_b[i] = vld(&pc->map_a[i]);
+          go = (vld(&a.ctl->cont) && !vld(&a.ctl->dir_in_z) && !fin) ? 1 : 0;
+        }
+      }
+      go = __any_sync(0xffffffffu, go);
+      act = __any_sync(0xffffffffu, act);
+      if (i == 0) {
+        if (kind == kSyncAfterA) *(volatile int*)&pc->go = go;
+        if (kind == kSyncEnd) *(volatile int*)&pc->active = act;
+        __threadfence();
+        atomicExch(&pc->gen, gen_s + 1u);
+      }
+    }
+  } else if (threadIdx.x == 0) {
+    const unsigned long long t0 = global_ns();
+    int ok = 1;
+    for (unsigned n = 0;; ++n) {
+      if (*(volatile unsigned*)&pc->gen != gen_s) break;
+      if ((n & 63u) == 63u && (vld(&pc->status) != 0 || global_ns() - t0 > p.wait_ns || n > (1u << 30))) {
+        ok = 0;
+        break;
+      }
+      if (n > 4096) __nanosleep(32);
+    }
+    __threadfence();
+    ok_s = ok;
+  }
+  if (threadIdx.x == 0) {
+    if (!ok_s || vld(&pc->status) != 0) {
+      ok_s = 0;
+      atomicOr(&pc->status, 1);
+      for (int i = 0; i < p.ninst; ++i) report_timeout(p.tab[i].ctl);
+    }
+  }
+  __syncthreads();
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+  return ok_s != 0;
+}
+
+// One phase: the virtual blocks of the members taking part (take[i] != 0,
+// or all with take == nullptr), block b taking virtual blocks b, b +
+// gridDim.x, ... in member order.
+template <typename T, typename Body>
+__device__ __forceinline__ void persist_phase(const PersistArgs<T>& p, const int* vgs, const int* take, Body body) {
+  __shared__ int vstart[kMaxBatch + 1];
+  if (threadIdx.x < 32) {
+    const int i = threadIdx.x;
+    int t = 0;
+    if (i < p.ninst) t = take ? vld(take + i) : 1;
+    const int cnt = t ? vgs[i < p.ninst ? i : 0] : 0;
+    int incl = cnt;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, off);
+      if (i >= off) incl += y;
+    }
+    if (i < p.ninst) vstart[i] = incl - cnt;
+    if (i == p.ninst - 1) vstart[p.ninst] = incl;
+  }
+  __syncthreads();
+  const int total = vstart[p.ninst];
+  for (int v = blockIdx.x; v < total; v += gridDim.x) {
+    int i = 0;
+    while (i + 1 < p.ninst && v >= vstart[i + 1]) ++i;
+    body(p.tab[i], v - vstart[i], vgs[i]);
+    __syncthreads();  // the next virtual block reuses the shared memory
+  }
+}
+
+// Up to p.nsteps whole steps of every member (Algorithm 2.2, the same passes
+// and the same arithmetic as the step graph; coherent loads for the vectors,
+// which earlier phases of the launch write).  Ends early once every member
+// has finished (stop rule, step limit or error).
+template <typename T, int LPR, int W>
+__global__ void __launch_bounds__(kBlockThreads, 1) k_persist(const PersistArgs<T> p) {
+  PersistCtl* pc = p.pc;
+  for (long long step = 0; step < p.nsteps; ++step) {
+    persist_phase(p, p.vg[kPassStart], nullptr,
+                  [&](const KArgs<T>& a, int vb, int vg) { body_start<T, LPR, W, true>(a, vb, vg); });
+    if (!persist_sync(p, kSyncPlain)) return;
+    persist_phase(p, p.vg[4], nullptr,
+                  [&](const KArgs<T>& a, int vb, int vg) { body_energy_check<T, LPR, true>(a, vb, vg); });
+    if (!persist_sync(p, kSyncMapA)) return;
+    persist_phase(p, p.vg[kPassCgA], pc->map_a,
+                  [&](const KArgs<T>& a, int vb, int vg) { body_cg_a<T, LPR, W, true>(a, vb, vg); });
+    if (!persist_sync(p, kSyncAfterA)) return;
+    while (vld(&pc->go)) {
+      persist_phase(p, p.vg[kPassCgB], pc->map_b,
+                    [&](const KArgs<T>& a, int vb, int vg) { body_cg_b<T, LPR, true>(a, vb, vg); });
+      if (!persist_sync(p, kSyncMapA)) return;
+      persist_phase(p, p.vg[kPassCgA], pc->map_a,
+                    [&](const KArgs<T>& a, int vb, int vg) { body_cg_a<T, LPR, W, true>(a, vb, vg); });
+      if (!persist_sync(p, kSyncAfterA)) return;
+    }
+    persist_phase(p, p.vg[kPassFinish], nullptr,
+                  [&](const KArgs<T>& a, int vb, int vg) { body_finish<T, LPR, true>(a, vb, vg); });
+    if (!persist_sync(p, kSyncEnd)) return;
+    if (!vld(&pc->active)) return;
+  }
+}
+
 // ------------------------------------------------------- auxiliary kernels
 
 __device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
@@ -1883,6 +2073,7 @@ bool fill_kernels(KernelSet* ks) {
   ks->b_finish = (void*)kb_finish<T, LPR>;
   ks->b_energy_check = (void*)kb_energy_check<T, LPR>;
   ks->b_vote = (void*)k_batch_vote<T>;
+  ks->persist = (void*)k_persist<T, LPR, W>;
   ks->smem_start = row_stage_smem<StartStage<T, LPR, W>>();
   {
     const unsigned f0 = row_stage_smem<CgAStage<T, LPR, W, kCgFirst>>();

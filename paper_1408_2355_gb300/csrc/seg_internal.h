@@ -147,6 +147,33 @@ struct BatchArgs {
   unsigned long long cond;  // conditional handle of the batch's CG loop
 };
 
+// A persistent batched launch runs whole steps of every member in one
+// cooperative kernel: each pass of Algorithm 2.2 is a phase in which the
+// physical blocks take the members' virtual blocks (as in BatchArgs), and a
+// grid barrier separates the phases.  The block that arrives last at a
+// barrier publishes what the next phase needs (which members take part, and
+// whether the CG loop goes on), so that every block reads the same values.
+struct PersistCtl {
+  unsigned int count;   // blocks arrived at the current barrier
+  unsigned int gen;     // barrier generation (released by the last arrival)
+  int status;           // bit 0: a barrier wait ran out
+  int go;               // the CG loop runs another pass B
+  int active;           // some member still steps
+  int pad;
+  int map_a[kMaxBatch];  // members of the next CG pass A
+  int map_b[kMaxBatch];  // members of the next CG pass B
+};
+constexpr int kNumPhasePasses = 5;  // start, CG pass A, CG pass B, finish (RowPass order), then the energy check
+template <typename T>
+struct PersistArgs {
+  KArgs<T> tab[kMaxBatch];  // in the kernel's parameter space
+  int ninst;
+  int vg[kNumPhasePasses][kMaxBatch];  // virtual blocks of each member in each pass (its own grids)
+  PersistCtl* pc;
+  long long nsteps;
+  unsigned long long wait_ns;  // limit of one barrier wait
+};
+
 // Function table of one (precision, lanes-per-row) specialisation.
 struct KernelSet {
   void* start;
@@ -165,6 +192,7 @@ struct KernelSet {
   void* b_finish;
   void* b_energy_check;
   void* b_vote;         // one block: the batch's CG loop condition
+  void* persist;        // persistent batched steps (PersistArgs, cooperative launch)
   unsigned smem_start;  // dynamic shared memory of k_start (bytes)
   unsigned smem_cg_a;   // dynamic shared memory of k_cg_a (bytes)
 };

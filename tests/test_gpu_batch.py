@@ -58,6 +58,56 @@ def test_batch_members_equal_alone(seg, prec, steps):
     assert np.array_equal(seg.seg_get_u(alone[0]), seg.seg_get_u(batched[0]))
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("steps", [30, 100])
+def test_persistent_batch_members_equal_alone(seg, prec, steps):
+    """The persistent mode (one cooperative launch per call, grid barriers
+    between the passes, the CG loop and the stop rules decided on the
+    device): every member bitwise equal to itself stepped alone, counters
+    included; the steps may be split over several calls and the batch may
+    go back to the step graph."""
+    alone = _members(seg, prec)
+    for s_ in alone:
+        seg.seg_step(s_, steps)
+    batched = _members(seg, prec)
+    b = seg.seg_batch_create(batched)
+    seg.seg_batch_set_persistent(b, True)
+    seg.seg_batch_step(b, steps // 3)
+    seg.seg_batch_step(b, steps - steps // 3 - 5)
+    seg.seg_batch_set_persistent(b, False)
+    seg.seg_batch_step(b, 5)
+    for sa, sb in zip(alone, batched):
+        assert np.array_equal(seg.seg_get_u(sa), seg.seg_get_u(sb))
+        ta, tb = seg.seg_get_stats(sa), seg.seg_get_stats(sb)
+        for k in ("steps", "cg_iterations", "cg_max", "converged", "checks"):
+            assert ta[k] == tb[k], k
+        assert ta["last_check_total"] == tb["last_check_total"]
+    seg.seg_batch_destroy(b)
+
+
+def test_persistent_batch_member_whose_wait_runs_out_halts_alone(seg):
+    """In the persistent mode a member whose staged-data waits run out (the
+    stall aid, 1 ms limit) halts with SEG_ERR_TIMEOUT in its first step; the
+    grid barriers go on and the other member's steps are bitwise those of it
+    stepped alone."""
+    xyz, tri = w.icosphere(5)
+    alone = make_state(seg, xyz, tri, 1e-4, 6, 2e-2, 1, seed=21, check_every=1, energy_tol=-1.0)
+    assert seg.seg_step(alone, 8) == 8
+    a = make_state(seg, xyz, tri, 1e-4, 6, 2e-2, 1, seed=21, check_every=1, energy_tol=-1.0)
+    b = make_state(seg, xyz, tri, 1e-4, 6, 2e-2, 1, seed=22, check_every=1, energy_tol=-1.0, wait_limit_ns=1_000_000)
+    seg.seg_set_wait_stall(b, True)
+    batch = seg.seg_batch_create([a, b])
+    seg.seg_batch_set_persistent(batch, True)
+    with pytest.raises(seg.SegError) as err:
+        seg.seg_batch_step(batch, 8)
+    assert err.value.status == seg.SEG_ERR_TIMEOUT
+    sb = seg.seg_get_stats(b)
+    assert sb["steps"] == 0 and sb["status_bits"] & 4
+    assert seg.seg_get_stats(a)["steps"] == 8
+    assert np.array_equal(seg.seg_get_u(a), seg.seg_get_u(alone))
+    seg.seg_batch_destroy(batch)
+
+
 def test_batch_rejects_mixed_classes(seg):
     xyz, tri = w.icosphere(2)
     a = make_state(seg, xyz, tri, 1e-3, 3, 0.1, 1)
@@ -110,6 +160,25 @@ def test_full_size_pair_batched_is_bitwise_the_pair_alone(seg):
         seg.seg_step(sb, 20)
         assert seg.seg_launch_info(sa) == seg.seg_launch_info(sb)
     b = seg.seg_batch_create(batched)
+    seg.seg_batch_step(b, 40)
+    for sa, sb in zip(alone, batched):
+        assert np.array_equal(seg.seg_get_u(sa), seg.seg_get_u(sb))
+        ta, tb = seg.seg_get_stats(sa), seg.seg_get_stats(sb)
+        assert ta["cg_iterations"] == tb["cg_iterations"] and ta["steps"] == tb["steps"]
+
+
+def test_full_size_pair_persistent_is_bitwise_the_pair_alone(seg):
+    """The two full-size instances (torus 1024 x 512 and the level-8
+    ellipsoid, m = 12) stepped by the persistent kernel (one block per SM,
+    each member's virtual blocks in its own decomposition) for 40 steps after
+    20 alone: bitwise the 60 steps of each alone."""
+    _, alone = _pair(seg, 12)
+    _, batched = _pair(seg, 12)
+    for sa, sb in zip(alone, batched):
+        seg.seg_step(sa, 60)
+        seg.seg_step(sb, 20)
+    b = seg.seg_batch_create(batched)
+    seg.seg_batch_set_persistent(b, True)
     seg.seg_batch_step(b, 40)
     for sa, sb in zip(alone, batched):
         assert np.array_equal(seg.seg_get_u(sa), seg.seg_get_u(sb))
