@@ -912,6 +912,18 @@ def batched_section(a):
     t_batch = time.perf_counter() - t0
     e_batch = [seg.seg_energy(st)["total"] for st in states]
     it_batch = [seg.seg_get_stats(st)["cg_iterations"] for st in states]
+    # the same batch in the persistent mode: one cooperative launch for all
+    # the steps
+    seg.seg_batch_set_persistent(batch, True)
+    seg.seg_batch_step(batch, 3)  # warm-up
+    for st, ck in zip(states, cks):
+        seg.seg_set_checkpoint(st, ck)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    seg.seg_batch_step(batch, steps)
+    t_persist = time.perf_counter() - t0
+    e_persist = [seg.seg_energy(st)["total"] for st in states]
+    it_persist = [seg.seg_get_stats(st)["cg_iterations"] for st in states]
     del batch
     for st, ck in zip(states, cks):
         seg.seg_step(st, 3)  # warm-up (builds the member's own graph)
@@ -927,9 +939,57 @@ def batched_section(a):
             "steps": steps, "value": dof * steps / t_batch, "unit": "DoF-steps/s",
             "alone_one_after_the_other": dof * steps / t_alone, "batch_over_alone": t_alone / t_batch,
             "same_results": e_batch == e_alone and it_batch == it_alone,
+            "persistent": {"value": dof * steps / t_persist, "persistent_over_alone": t_alone / t_persist,
+                           "same_results": e_persist == e_alone and it_persist == it_alone},
+            "small_instances": small_batch_arms(seg, torch),
             "cg_iterations_per_step": [(i - c) / steps for i, c in zip(it_batch, it0)],
-            "timing": "host clock around synchronous calls, both arms from the same checkpoint of the members "
+            "timing": "host clock around synchronous calls, every arm from the same checkpoint of the members "
                       "after 20 set-up steps and the autotuner, energy check every step"}
+
+
+def small_batch_arms(seg, torch, level=4, n=8, m=8, steps=400):
+    """Eight small instances (level-4 spheres, N = 2562, m = 8, eps = 2e-2,
+    tau = 1e-4, seeds 50..57, mixed): ms per step of the batch's step graph,
+    of its persistent kernel and of the instances stepped one after the
+    other, all from the same checkpoints."""
+    import workload as w
+
+    xyz, tri = w.icosphere(level)
+    prob = seg.seg_assemble(seg.seg_create_mesh(xyz, tri), 1e-4, seg.SEG_MIXED_FP32)
+    prm = seg.seg_params()
+    prm.check_every = 1
+    prm.energy_tol = -1.0
+    states = [seg.seg_state_create(prob, m, 2e-2, seg.SEG_INIT_UNIFORM, 50 + k, prm) for k in range(n)]
+    for st in states:
+        seg.seg_step(st, 20)
+    cks = [seg.seg_get_checkpoint(st) for st in states]
+    out, finals = {}, {}
+    batch = seg.seg_batch_create(states)
+    for arm in ("graph", "persistent", "alone"):
+        if arm == "persistent":
+            seg.seg_batch_set_persistent(batch, True)
+        for st, ck in zip(states, cks):
+            seg.seg_set_checkpoint(st, ck)
+        if arm == "alone":
+            for st in states:
+                seg.seg_step(st, 3)
+        else:
+            seg.seg_batch_step(batch, 3)
+        for st, ck in zip(states, cks):
+            seg.seg_set_checkpoint(st, ck)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if arm == "alone":
+            for st in states:
+                seg.seg_step(st, steps)
+        else:
+            seg.seg_batch_step(batch, steps)
+        out[arm + "_ms_per_step"] = (time.perf_counter() - t0) / steps * 1e3
+        finals[arm] = [seg.seg_energy(st)["total"] for st in states]
+    del batch
+    out["same_results"] = finals["graph"] == finals["alone"] and finals["persistent"] == finals["alone"]
+    out["workload"] = f"{n} x sphere level {level} (N = {xyz.shape[0]}), m = {m}, eps = 2e-2, tau = 1e-4, mixed, {steps} steps"
+    return out
 
 
 def serving_section(a):
