@@ -39,7 +39,7 @@ HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e, nominal
 # dram__bytes_write.sum of the bench's own kernel timing launches (selected by
 # their NVTX range), mean of the second and third launch; valid only for the
 # kernel versions captured.
-TRAFFIC = {"k_start": 196.3e6, "k_cg_a_first": 97.2e6, "k_cg_b": 90.6e6, "k_cg_b_first": 113.8e6,
+TRAFFIC = {"k_start": 196.1e6, "k_cg_a_first": 97.0e6, "k_cg_b": 90.6e6, "k_cg_b_first": 113.8e6,
            "k_finish_one": 279.5e6, "k_energy_check": 63.0e6}
 KERNEL_ROLE = {
     "k_start": "start pass: r0 = -tau K X - A y for the predicted correction y, z0 = D^-1 r0, norms "
