@@ -113,9 +113,12 @@ typedef struct {
   int64_t checks;           /* number of stop-rule checks evaluated */
   int64_t kernel_launches;  /* hot-path kernel launches on this state (start, CG passes A and B
                                including those that returned at once after the loop ended,
-                               finish, energy passes) */
+                               finish, energy passes); in a persistent batch, the phases of its
+                               launch that ran this state's passes */
   int32_t graph_peel;       /* CG iterations the step graph (launch_mode 0) runs as plain nodes
-                               before its loop node: the autotuner sets it to the latest step's
+                               before its loop node (their passes A, and the passes B of all but
+                               the last, whose pass B follows the loop condition): the autotuner
+                               sets it to the latest step's
                                count; reviews after 3 or more steps (at seg_sync / seg_step, and
                                every 16 steps inside a long seg_step) set it to their mean per
                                step rounded up if that is larger, or smaller by 2 or more (the
