@@ -180,3 +180,32 @@ def test_noalloc_wrapper_rejects_bad_arguments_before_any_call(seg):
             seg.seg_s_eps_noalloc(args["u"], args["xyz"], args["tri"], 0.1, args["out"])
         assert err.value.status == seg.SEG_ERR_ARG
         assert words in str(err.value), (key, str(err.value))
+
+
+HANDLE_CALLS = [
+    "seg_mesh_info", "seg_mesh_get", "seg_problem_info", "seg_state_bytes", "seg_set_u", "seg_get_u",
+    "seg_checkpoint_size", "seg_get_checkpoint", "seg_set_checkpoint", "seg_set_wait_limit", "seg_set_wait_stall",
+    "seg_step_async", "seg_sync", "seg_step", "seg_substep", "seg_batch_step_async", "seg_batch_sync",
+    "seg_batch_step", "seg_batch_set_persistent", "seg_energy", "seg_eigenvalue_estimates", "seg_energy_p",
+    "seg_prolong", "seg_labels", "seg_get_stats", "seg_stats_enqueue", "seg_stats_wait", "seg_time_kernel",
+    "seg_autotune", "seg_launch_info", "seg_server_submit", "seg_server_tick", "seg_server_info",
+    "seg_server_result",
+]
+
+
+@pytest.mark.parametrize("name", HANDLE_CALLS)
+def test_null_handle_is_refused_without_touching_the_gpu(seg, name):
+    """Every entry point that takes a mesh, problem, state, batch or server
+    handle first returns SEG_ERR_ARG for a NULL handle (with a message), before
+    any other work -- so also on a machine without a GPU."""
+    fn = getattr(seg.lib, name)
+    args = []
+    for t in fn.argtypes:
+        if t in (C.c_int32, C.c_int64, C.c_uint64, C.c_int):
+            args.append(0)
+        elif t is C.c_double:
+            args.append(0.0)
+        else:
+            args.append(None)  # the handle and every pointer
+    assert fn(*args) == seg.SEG_ERR_ARG, name
+    assert seg.seg_last_error()
