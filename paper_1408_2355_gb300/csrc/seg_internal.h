@@ -173,6 +173,9 @@ struct PersistArgs {
   long long nsteps;
   unsigned long long wait_ns;  // limit of one barrier wait
 };
+// (kernel parameters: at most 32 764 bytes per launch)
+static_assert(sizeof(PersistArgs<double>) <= 32764 && sizeof(BatchArgs<double>) <= 32764,
+              "batched arguments exceed the kernel parameter space");
 
 // Function table of one (precision, lanes-per-row) specialisation.
 struct KernelSet {
